@@ -1,0 +1,170 @@
+/*
+ * chfsi.h -- C ABI of a GB300-native Chebyshev filtered subspace iteration (ChFSI) for
+ * sequences of dense complex Hermitian generalized eigenproblems  H x = lambda S x
+ * (Berljafa & Di Napoli, "A Parallel and Scalable Iterative Solver for Sequences of Dense
+ * Eigenproblems Arising in FLAPW", arXiv:1305.5120).
+ *
+ * Conventions (all entry points):
+ *  - Matrices are complex128 with interleaved (re, im) doubles, COLUMN-MAJOR, leading
+ *    dimension = number of rows (n for n x n and n x k blocks, k for k x k).
+ *  - Every matrix/vector pointer is a DEVICE pointer on the context's device, unless the
+ *    comment says "host".  The caller owns all pointers it passes; the library keeps none
+ *    of them after a call returns.  The context owns its workspaces and the sequence state.
+ *  - Work is ordered on the context's CUDA stream; every call returns after its work has
+ *    completed (the host needs residuals to decide locking and termination).
+ *  - Errors are returned as chfsi_status.  Outputs are unspecified on error, except that
+ *    CHFSI_ERR_NO_CONV still fills the converged prefix and `info`.  After CHFSI_ERR_CUDA
+ *    the context must be destroyed; after any other error it stays usable.
+ *  - One context = one sequence = one stream.  Contexts are independent; a context must not
+ *    be used by two host threads at once.
+ */
+#ifndef CHFSI_H
+#define CHFSI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct chfsi_ctx chfsi_ctx;
+
+typedef enum {
+  CHFSI_OK = 0,
+  CHFSI_ERR_ARG = 1,       /* invalid argument (sizes, NULL pointers, tolerances) */
+  CHFSI_ERR_NOT_HPD = 2,   /* S is not Hermitian positive definite (Cholesky pivot <= 0) */
+  CHFSI_ERR_NO_CONV = 3,   /* max_iter outer iterations without nev locked pairs, or the
+                              reduced eigensolver did not converge */
+  CHFSI_ERR_OOM = 4,       /* device allocation failed */
+  CHFSI_ERR_CUDA = 5,      /* a CUDA runtime call failed (context unusable) */
+  CHFSI_ERR_TIMEOUT = 6,   /* a bounded device-side wait ran out (kernel returned early) */
+  CHFSI_ERR_STATE = 7,     /* call out of order (e.g. next_in_sequence before solve) */
+  CHFSI_ERR_NUMERIC = 8    /* NaN/Inf met in a residual or a filtered block */
+} chfsi_status;
+
+enum {
+  CHFSI_PREC_FP64 = 0,     /* every filter product in FP64 (DFMA) */
+  CHFSI_PREC_MIXED = 1     /* filter products on the tensor cores in split-BF16 (FP32-equivalent)
+                              while residuals are large, then FP64; Cholesky, transform, QR,
+                              Rayleigh-Ritz, residuals and Lanczos always FP64 */
+};
+
+typedef struct {
+  int degree;              /* filter degree m when per_vector_degree == 0 (default 20) */
+  int degree_min;          /* per-vector degree range (default 10 .. 25) */
+  int degree_max;
+  int per_vector_degree;   /* 0: one degree for the block; 1: degree chosen per vector */
+  int max_iter;            /* outer iterations of Algorithm 1 (default 50) */
+  int lanczos_steps;       /* Lanczos steps of the spectral bound (default 20, <= 256) */
+  int precision;           /* CHFSI_PREC_* (default FP64) */
+  double mixed_switch;     /* MIXED: low-precision filter while the smallest active relative
+                              residual exceeds this (default 1e-5) */
+  unsigned long long seed; /* SplitMix64 seed of the Lanczos start vectors and of the random
+                              start block (default 0) */
+} chfsi_params;
+
+typedef struct {
+  int iterations;          /* outer iterations of the last solve */
+  int locked;              /* pairs locked */
+  long long filter_col_steps;       /* sum over filter launches of (columns x degree) */
+  long long filter_col_steps_lowp;  /* of which on the low-precision tensor-core path */
+  double max_resid;        /* largest relative residual ||H'y - lam y|| / ||H'y|| returned */
+  double kappa_L;          /* upper estimate of cond_2(L), S = L L^H */
+  double bounds[3];        /* (a, b, a0) of the last filter: damped interval [a, b], scale point a0 */
+  double ms_stage[8];      /* device time per stage: 0 reduce (Cholesky, inverse, H'), 1 Lanczos,
+                              2 filter, 3 QR, 4 Rayleigh-Ritz, 5 residual+locking,
+                              6 back-transform, 7 whole call */
+} chfsi_info;
+
+/* Fills *p with the defaults listed above. */
+chfsi_status chfsi_default_params(chfsi_params *p);
+
+/* Creates a context on `device` whose work runs on `cuda_stream` (a cudaStream_t, NULL =
+ * the legacy default stream).  p may be NULL (defaults).  Allocates nothing on the device
+ * until the first solve. */
+chfsi_status chfsi_create(chfsi_ctx **out, int device, void *cuda_stream, const chfsi_params *p);
+
+/*
+ * First problem of a sequence (Algorithm 1 of the paper, preceded by the reduction to
+ * standard form of Section 3):
+ *   S = L L^H, H' = L^{-1} H L^{-H}, Lanczos bound, then repeat [Chebyshev filter, QR,
+ *   Rayleigh-Ritz, residuals, deflation and locking] until nev pairs are locked.
+ * H, S: n x n Hermitian (S positive definite).  X0: n x (nev+nex) start block in the space
+ * of x (the library uses Y0 = L^H X0), or NULL for a SplitMix64 random block.  A pair locks
+ * when ||H'y - lam y|| / ||H'y|| < tol / kappa_L, which bounds the generalized relative
+ * residual ||H x - lam S x|| / ||H x|| by tol.  degree <= 0 takes params.degree.
+ * Outputs: evals[nev] ascending (device), X (n x nev, device) S-orthonormal eigenvectors.
+ * info may be NULL.
+ */
+chfsi_status chfsi_solve(chfsi_ctx *c, const void *H, const void *S, int n, int nev, int nex,
+                         const void *X0, double tol, int degree, double *evals, void *X,
+                         chfsi_info *info);
+
+/*
+ * Next problem of the sequence (Section 2: each P^(l) is seeded with the solution of
+ * P^(l-1); Algorithm 1 Require: previous eigenvectors and eigenvalues).  Uses the stored
+ * Ritz block (nev + nex vectors) as start block and the stored lowest/highest Ritz values
+ * as filter bounds; re-runs Lanczos for the upper bound.  S_next == NULL keeps S (and L).
+ * Same n, nev, nex, tol and degree as the previous solve.
+ */
+chfsi_status chfsi_next_in_sequence(chfsi_ctx *c, const void *H_next, const void *S_next,
+                                    double *evals, void *X, chfsi_info *info);
+
+void chfsi_destroy(chfsi_ctx *c);
+const char *chfsi_status_string(chfsi_status s);
+
+/* ---- Stage entry points (each step of the solve on its own; device pointers) -------- */
+
+/* a1. S = L L^H (Section 3).  L: n x n lower triangular output (upper part zeroed). */
+chfsi_status chfsi_cholesky(chfsi_ctx *c, int n, const void *S, void *L);
+
+/* a2. H' = L^{-1} H L^{-H}, Hermitian part (Section 3 standard form).  L from chfsi_cholesky. */
+chfsi_status chfsi_reduce(chfsi_ctx *c, int n, const void *H, const void *L, void *Hs);
+
+/* a3. `steps`-step Lanczos on Hermitian Hs from v0 (n vector, normalised internally; NULL =
+ * SplitMix64 stream 0 of params.seed).  alpha[steps], beta[steps]: recurrence coefficients
+ * (device).  bounds[4] (device): b_sup = max Ritz value + |beta_last| (Algorithm 1 line 1),
+ * a = first-solve lower end of the damped interval, a0 = smallest Ritz value, max Ritz value.
+ * k = block size used for a. */
+chfsi_status chfsi_lanczos(chfsi_ctx *c, int n, const void *Hs, int steps, int k, const void *v0,
+                           double *alpha, double *beta, double *bounds);
+
+/* a4 / a4m. Chebyshev filter (Algorithm 1 line 3, Eq. (3term) scaled and shifted):
+ * Y <- T_m((H' - cI)/e) Y / T_m((a0 - c)/e), e = (b - a)/2, c = (b + a)/2.
+ * Y: n x k, overwritten.  precision: CHFSI_PREC_FP64 or CHFSI_PREC_MIXED (tensor cores). */
+chfsi_status chfsi_filter(chfsi_ctx *c, int n, int k, const void *Hs, void *Y, int m, double a,
+                          double b, double a0, int precision);
+
+/* a10 (filter part). Column i filtered with its own degree deg[i] (host array, non-increasing). */
+chfsi_status chfsi_filter_degrees(chfsi_ctx *c, int n, int k, const void *Hs, void *Y, const int *deg,
+                                  double a, double b, double a0, int precision);
+
+/* a5. Orthonormal basis of Y (n x k, overwritten) orthogonal to the nl orthonormal columns
+ * Ylocked (n x nl, may be NULL when nl == 0): two block Gram-Schmidt passes against Ylocked,
+ * then CholQR2 (shifted CholQR first when the Gram matrix is too ill-conditioned).  The
+ * result equals the Q of a QR factorisation with positive real diagonal R. */
+chfsi_status chfsi_orthonormalize(chfsi_ctx *c, int n, int nl, const void *Ylocked, int k, void *Y);
+
+/* a6-a8. Rayleigh-Ritz (Algorithm 1 lines 5-7): G = Y^H H' Y, G W = W Lambda (ascending),
+ * Y <- Y W, Z <- H' Y.  Y: n x k orthonormal in, Ritz vectors out; lam[k]; Z: n x k out. */
+chfsi_status chfsi_rayleigh_ritz(chfsi_ctx *c, int n, int k, const void *Hs, void *Y, double *lam, void *Z);
+
+/* a7 alone. All eigenpairs of the k x k Hermitian G (parallel Jacobi): lam ascending, W. */
+chfsi_status chfsi_reduced_eig(chfsi_ctx *c, int k, const void *G, double *lam, void *W);
+
+/* a9. res[j] = ||Z_j - lam_j Y_j|| / ||Z_j|| (Algorithm 1, Res), Z = H' Y. */
+chfsi_status chfsi_residuals(chfsi_ctx *c, int n, int k, const void *Z, const void *Y, const double *lam,
+                             double *res);
+
+/* a10. Per-vector degree m_i = clamp(ceil(ln(tol/r_i)/ln rho_i), m_min, m_max),
+ * rho_i = 1/(|t_i| + sqrt(t_i^2 - 1)), t_i = (lam_i - c)/e.  deg: device int[k]. */
+chfsi_status chfsi_degrees(chfsi_ctx *c, int k, const double *lam, const double *res, double a, double b,
+                           double tol, int m_min, int m_max, int *deg);
+
+/* a11. X = L^{-H} Y (back-transform to eigenvectors of the pencil).  Y: n x k. */
+chfsi_status chfsi_back_transform(chfsi_ctx *c, int n, int k, const void *L, const void *Y, void *X);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHFSI_H */

@@ -1,0 +1,899 @@
+// C ABI and host orchestration of Chebyshev filtered subspace iteration with locking
+// (Algorithm 1 of the paper), preceded by the reduction to standard form (Section 3) and
+// followed by the back-transform.  Every arithmetic step runs in this library's kernels;
+// the host only sequences launches, reads k residuals per outer iteration and takes the
+// locking/termination decisions.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "dense.cuh"
+#include "filter_tc.cuh"
+#include "jacobi.cuh"
+#include "lanczos.cuh"
+
+chfsi_status chfsi_cuda_error(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) return CHFSI_ERR_OOM;
+  if (getenv("CHFSI_VERBOSE")) fprintf(stderr, "chfsi: CUDA error %s in %s\n", cudaGetErrorString(e), what);
+  return CHFSI_ERR_CUDA;
+}
+
+namespace {
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Arena {
+  std::vector<std::pair<const char*, Buf>> bufs;
+  cudaError_t get(const char* name, size_t bytes, void** out) {
+    for (auto& b : bufs) {
+      if (strcmp(b.first, name) == 0) {
+        if (b.second.bytes >= bytes) {
+          *out = b.second.p;
+          return cudaSuccess;
+        }
+        cudaFree(b.second.p);
+        b.second = Buf{};
+        cudaError_t e = cudaMalloc(&b.second.p, bytes);
+        if (e != cudaSuccess) return e;
+        b.second.bytes = bytes;
+        *out = b.second.p;
+        return cudaSuccess;
+      }
+    }
+    Buf nb;
+    cudaError_t e = cudaMalloc(&nb.p, bytes ? bytes : 16);
+    if (e != cudaSuccess) return e;
+    nb.bytes = bytes;
+    bufs.push_back({name, nb});
+    *out = nb.p;
+    return cudaSuccess;
+  }
+  void release() {
+    for (auto& b : bufs) cudaFree(b.second.p);
+    bufs.clear();
+  }
+};
+
+}  // namespace
+
+struct chfsi_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  chfsi_params prm{};
+  Arena arena;
+  TcFilter* tc = nullptr;   // tensor-core filter state (lazy)
+  // pinned host mirrors
+  double* h_d = nullptr;    // 4 * kcap doubles
+  int* h_i = nullptr;       // 2 * kcap ints
+  int kcap = 0;
+  // device scalars
+  int* d_err = nullptr;
+  int* d_sweeps = nullptr;
+  // sequence state
+  bool have_seq = false;
+  int n = 0, nev = 0, nex = 0, degree = 20;
+  double tol = 1e-10, kappa_L = 1.0;
+  std::vector<double> block_lam;   // ascending Ritz values of the stored block
+  cudaEvent_t ev[16] = {};
+};
+
+namespace {
+
+inline chfsi_status cu(cudaError_t e, const char* what) {
+  return e == cudaSuccess ? CHFSI_OK : chfsi_cuda_error(e, what);
+}
+#define TRY(x)                        \
+  do {                                \
+    chfsi_status _s = (x);            \
+    if (_s != CHFSI_OK) return _s;    \
+  } while (0)
+#define CU(x) TRY(cu((x), #x))
+
+template <typename T>
+chfsi_status buf(chfsi_ctx* c, const char* name, size_t count, T** out) {
+  void* p = nullptr;
+  cudaError_t e = c->arena.get(name, count * sizeof(T), &p);
+  if (e != cudaSuccess) return chfsi_cuda_error(e, name);
+  *out = (T*)p;
+  return CHFSI_OK;
+}
+
+chfsi_status ensure_host(chfsi_ctx* c, int k) {
+  if (k <= c->kcap) return CHFSI_OK;
+  if (c->h_d) cudaFreeHost(c->h_d);
+  if (c->h_i) cudaFreeHost(c->h_i);
+  c->h_d = nullptr;
+  c->h_i = nullptr;
+  CU(cudaMallocHost((void**)&c->h_d, sizeof(double) * 4 * (size_t)k));
+  CU(cudaMallocHost((void**)&c->h_i, sizeof(int) * 2 * (size_t)k));
+  c->kcap = k;
+  return CHFSI_OK;
+}
+
+chfsi_status read_err(chfsi_ctx* c, int* dev_err) {
+  int h = 0;
+  CU(cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  *dev_err = h;
+  return CHFSI_OK;
+}
+
+chfsi_status map_dev_err(int e) {
+  switch (e) {
+    case DEV_OK: return CHFSI_OK;
+    case DEV_ERR_TIMEOUT: return CHFSI_ERR_TIMEOUT;
+    case DEV_ERR_NOT_HPD: return CHFSI_ERR_NOT_HPD;
+    case DEV_ERR_NO_CONV: return CHFSI_ERR_NO_CONV;
+    default: return CHFSI_ERR_NUMERIC;
+  }
+}
+
+// GEMM with a split-K factor chosen for the grid (deterministic reduction) --------------
+chfsi_status gemm(chfsi_ctx* c, GemmArgs g) {
+  const long tiles = (long)((g.M + 63) / 64) * ((g.N + 31) / 32);
+  int splits = 1;
+  if (g.K >= 512 && tiles < 2 * 152) {
+    splits = (int)std::min<long>(16, (2 * 152 + tiles - 1) / tiles);
+    splits = std::max(1, std::min(splits, g.K / 128));
+  }
+  g.splits = splits;
+  g.work = nullptr;
+  if (splits > 1) TRY(buf(c, "splitk", (size_t)splits * g.M * g.N, &g.work));
+  CU(zgemm_launch(g, c->stream));
+  return CHFSI_OK;
+}
+
+GemmArgs gemm_args(int M, int N, int K, int opA, const cplx* A, long lda, int opB, const cplx* B, long ldb,
+                   cplx* C, long ldc, cplx alpha, cplx beta, int tri = TRI_NONE) {
+  GemmArgs g{};
+  g.M = M; g.N = N; g.K = K;
+  g.opA = opA; g.opB = opB; g.tri = tri;
+  g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
+  g.alpha = alpha; g.beta = beta;
+  g.epi = EPI_GEMM;
+  g.splits = 1;
+  return g;
+}
+const cplx ONE = {1.0, 0.0}, ZERO = {0.0, 0.0}, MONE = {-1.0, 0.0};
+
+// a1 + inverse: L and Linv from S --------------------------------------------------------
+chfsi_status factor_S(chfsi_ctx* c, int n, const cplx* S, cplx* L, cplx* Linv) {
+  CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  CU(cudaMemcpyAsync(L, S, sizeof(cplx) * (size_t)n * n, cudaMemcpyDeviceToDevice, c->stream));
+  CU(chol_lower(c->stream, n, L, n, c->d_err));
+  if (Linv) CU(trtri_lower(c->stream, n, L, n, Linv, n, c->d_err));
+  int e = 0;
+  TRY(read_err(c, &e));
+  return map_dev_err(e);
+}
+
+// a2: Hs = Linv H Linv^H --------------------------------------------------------------------
+chfsi_status transform(chfsi_ctx* c, int n, const cplx* H, const cplx* Linv, cplx* Hs) {
+  cplx* W;
+  TRY(buf(c, "tmp_nn", (size_t)n * n, &W));
+  TRY(gemm(c, gemm_args(n, n, n, OP_N, Linv, n, OP_N, H, n, W, n, ONE, ZERO, TRI_A_LOWER)));
+  TRY(gemm(c, gemm_args(n, n, n, OP_N, W, n, OP_C, Linv, n, Hs, n, ONE, ZERO, TRI_B_UPPER)));
+  CU(hermitize(c->stream, n, Hs, n));
+  return CHFSI_OK;
+}
+
+// a3: Lanczos with a generic operator w = Op(v) ----------------------------------------------
+template <typename Op>
+chfsi_status lanczos_run(chfsi_ctx* c, int n, int steps, int k, const cplx* v0, unsigned long long stream_id, Op op,
+                         double* alpha, double* beta, double* bounds) {
+  steps = std::min(steps, n);
+  if (steps < 2) return CHFSI_ERR_ARG;
+  cplx *v, *vp, *w;
+  TRY(buf(c, "lz_v", n, &v));
+  TRY(buf(c, "lz_vp", n, &vp));
+  TRY(buf(c, "lz_w", n, &w));
+  if (v0) CU(cudaMemcpyAsync(v, v0, sizeof(cplx) * n, cudaMemcpyDeviceToDevice, c->stream));
+  else CU(splitmix_block(c->stream, n, 1, c->prm.seed, stream_id, v, n));
+  CU(normalize_vec(c->stream, n, v));
+  CU(cudaMemsetAsync(vp, 0, sizeof(cplx) * n, c->stream));
+  for (int j = 0; j < steps; ++j) {
+    TRY(op(v, w));
+    CU(lanczos_step(c->stream, n, j, v, vp, w, alpha, beta));
+  }
+  CU(lanczos_bounds(c->stream, steps, n, k, alpha, beta, bounds));
+  return CHFSI_OK;
+}
+
+chfsi_status lanczos_H(chfsi_ctx* c, int n, const cplx* Hs, int steps, int k, const cplx* v0, double* alpha,
+                       double* beta, double* bounds) {
+  auto op = [&](const cplx* v, cplx* w) -> chfsi_status {
+    CU(herm_gemv(c->stream, n, Hs, n, v, w));
+    return CHFSI_OK;
+  };
+  return lanczos_run(c, n, steps, k, v0, 0, op, alpha, beta, bounds);
+}
+
+// cond_2(L) <= sqrt(b(S) b(S^{-1})) from two Lanczos runs (start: SplitMix64 stream 1)
+chfsi_status kappa_L(chfsi_ctx* c, int n, const cplx* S, const cplx* Linv, double* out) {
+  double *al, *be, *bd;
+  cplx* t;
+  TRY(buf(c, "lz_alpha", 256, &al));
+  TRY(buf(c, "lz_beta", 256, &be));
+  TRY(buf(c, "lz_bounds", 16, &bd));
+  TRY(buf(c, "lz_t", n, &t));
+  const int steps = std::min(c->prm.lanczos_steps, n);
+  auto opS = [&](const cplx* v, cplx* w) -> chfsi_status {
+    CU(herm_gemv(c->stream, n, S, n, v, w));
+    return CHFSI_OK;
+  };
+  TRY(lanczos_run(c, n, steps, 1, nullptr, 1, opS, al, be, bd));
+  auto opSi = [&](const cplx* v, cplx* w) -> chfsi_status {
+    TRY(gemm(c, gemm_args(n, 1, n, OP_N, Linv, n, OP_N, v, n, t, n, ONE, ZERO, TRI_A_LOWER)));
+    TRY(gemm(c, gemm_args(n, 1, n, OP_C, Linv, n, OP_N, t, n, w, n, ONE, ZERO, TRI_A_UPPER)));
+    return CHFSI_OK;
+  };
+  TRY(lanczos_run(c, n, steps, 1, nullptr, 1, opSi, al, be, bd + 4));
+  double h[8];
+  CU(cudaMemcpyAsync(h, bd, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  *out = sqrt(h[0] * h[4]);
+  if (!(*out >= 1.0) || !isfinite(*out)) *out = std::max(1.0, isfinite(*out) ? *out : 1.0);
+  return CHFSI_OK;
+}
+
+// a4: filter coefficients of Y_j = fa_j H Y_{j-1} + fb_j Y_{j-1} + fg_j Y_{j-2} -------------
+void filter_coefs(int m, double a, double b, double a0, std::vector<double>& fa, std::vector<double>& fb,
+                  std::vector<double>& fg) {
+  const double e = 0.5 * (b - a), cc = 0.5 * (b + a);
+  const double s1 = e / (a0 - cc);
+  double sg = s1;
+  fa.assign(m + 1, 0.0);
+  fb.assign(m + 1, 0.0);
+  fg.assign(m + 1, 0.0);
+  fa[1] = s1 / e;
+  fb[1] = -cc * s1 / e;
+  fg[1] = 0.0;
+  for (int j = 2; j <= m; ++j) {
+    const double sn = 1.0 / (2.0 / s1 - sg);
+    fa[j] = 2.0 * sn / e;
+    fb[j] = -2.0 * sn * cc / e;
+    fg[j] = -sg * sn;
+    sg = sn;
+  }
+}
+
+__global__ void copy_odd_columns_kernel(int n, const int* deg, const cplx* src, cplx* dst) {
+  const int j = blockIdx.y;
+  if ((deg[j] & 1) == 0) return;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+    dst[r + (long)j * n] = src[r + (long)j * n];
+}
+
+// Filter on Y (n x k, ld n) with non-increasing degrees deg[0..k) (host), FP64 or tensor cores.
+chfsi_status run_filter(chfsi_ctx* c, int n, int k, const cplx* Hs, cplx* Y, const int* deg, double a, double b,
+                        double a0, int precision, long long* col_steps) {
+  if (k <= 0) return CHFSI_OK;
+  const int mmax = deg[0];
+  if (mmax <= 0) return CHFSI_OK;
+  for (int i = 1; i < k; ++i)
+    if (deg[i] > deg[i - 1] || deg[i] < 0) return CHFSI_ERR_ARG;
+  if (!(b > a) || !(a0 < a)) return CHFSI_ERR_ARG;
+  std::vector<double> fa, fb, fg;
+  filter_coefs(mmax, a, b, a0, fa, fb, fg);
+  std::vector<int> cnt(mmax + 1, 0);
+  for (int j = 1; j <= mmax; ++j) {
+    int q = 0;
+    while (q < k && deg[q] >= j) ++q;
+    cnt[j] = q;
+  }
+  long long steps = 0;
+  for (int j = 1; j <= mmax; ++j) steps += cnt[j];
+  if (col_steps) *col_steps += steps;
+  cplx* Y2;
+  TRY(buf(c, "filter_y2", (size_t)n * k, &Y2));
+  cplx* bufs[2] = {Y, Y2};
+  if (precision == CHFSI_PREC_MIXED) {
+    TRY(tc_filter_run(c->tc ? c->tc : (c->tc = tc_filter_new()), c->stream, n, Hs, bufs, cnt.data(), mmax,
+                      fa.data(), fb.data(), fg.data()));
+  } else {
+    for (int j = 1; j <= mmax; ++j) {
+      GemmArgs g = gemm_args(n, cnt[j], n, OP_N, Hs, n, OP_N, bufs[(j - 1) & 1], n, bufs[j & 1], n, ONE, ZERO);
+      g.epi = EPI_FILTER;
+      g.Ycur = bufs[(j - 1) & 1];
+      g.ldy = n;
+      g.fa = fa[j];
+      g.fb = fb[j];
+      g.fg = (j >= 2) ? fg[j] : 0.0;
+      TRY(gemm(c, g));
+    }
+  }
+  // columns with odd degree ended in Y2
+  bool uniform = deg[k - 1] == mmax;
+  if (uniform) {
+    if (mmax & 1) CU(copy_block(c->stream, n, k, Y2, n, Y, n));
+  } else {
+    int* d_deg;
+    TRY(buf(c, "deg_dev", k, &d_deg));
+    CU(cudaMemcpyAsync(d_deg, deg, sizeof(int) * k, cudaMemcpyHostToDevice, c->stream));
+    dim3 grid((unsigned)std::min((n + 255) / 256, 32), (unsigned)k);
+    copy_odd_columns_kernel<<<grid, 256, 0, c->stream>>>(n, d_deg, Y2, Y);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(c->stream));   // deg is a caller-owned host array
+  }
+  return CHFSI_OK;
+}
+
+// a5: CGS2 against locked vectors, then CholQR2 (shifted CholQR first on breakdown) --------
+__global__ void add_shift_kernel(int k, int n, cplx* G) {
+  // s = 11 (n k + k (k + 1)) u ||Y||_F^2, ||Y||_F^2 = trace(G)  (shifted CholeskyQR3, Fukaya et al.)
+  __shared__ double sh[32];
+  double t = 0.0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) t += G[i + (long)i * k].x;
+  t = block_sum(t, sh);
+  const double s = 11.0 * ((double)n * k + (double)k * (k + 1)) * 1.1102230246251565e-16 * t;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) G[i + (long)i * k].x += s;
+}
+
+chfsi_status cholqr_pass(chfsi_ctx* c, int n, int k, cplx* Y, bool shifted, bool* ok) {
+  cplx *G, *Ri, *T;
+  TRY(buf(c, "qr_G", (size_t)k * k, &G));
+  TRY(buf(c, "qr_Ri", (size_t)k * k, &Ri));
+  TRY(buf(c, "qr_T", (size_t)n * k, &T));
+  TRY(gemm(c, gemm_args(k, k, n, OP_C, Y, n, OP_N, Y, n, G, k, ONE, ZERO)));
+  CU(hermitize(c->stream, k, G, k));
+  if (shifted) {
+    add_shift_kernel<<<1, 256, 0, c->stream>>>(k, n, G);
+    CU(cudaGetLastError());
+  }
+  CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  CU(chol_lower(c->stream, k, G, k, c->d_err));
+  int e = 0;
+  TRY(read_err(c, &e));
+  if (e != DEV_OK) {
+    *ok = false;
+    return CHFSI_OK;
+  }
+  CU(trtri_lower(c->stream, k, G, k, Ri, k, c->d_err));
+  // Y <- Y R^{-1}, R = Lg^H  =>  R^{-1} = (Lg^{-1})^H (upper triangular)
+  TRY(gemm(c, gemm_args(n, k, k, OP_N, Y, n, OP_C, Ri, k, T, n, ONE, ZERO, TRI_B_UPPER)));
+  CU(copy_block(c->stream, n, k, T, n, Y, n));
+  *ok = true;
+  return CHFSI_OK;
+}
+
+chfsi_status orthonormalize(chfsi_ctx* c, int n, int nl, const cplx* Yl, int k, cplx* Y) {
+  if (k <= 0) return CHFSI_OK;
+  if (nl > 0) {
+    cplx* Cm;
+    TRY(buf(c, "qr_C", (size_t)nl * k, &Cm));
+    for (int pass = 0; pass < 2; ++pass) {
+      TRY(gemm(c, gemm_args(nl, k, n, OP_C, Yl, n, OP_N, Y, n, Cm, nl, ONE, ZERO)));
+      TRY(gemm(c, gemm_args(n, k, nl, OP_N, Yl, n, OP_N, Cm, nl, Y, n, MONE, ONE)));
+    }
+  }
+  bool ok = false;
+  TRY(cholqr_pass(c, n, k, Y, false, &ok));
+  if (!ok) {
+    TRY(cholqr_pass(c, n, k, Y, true, &ok));
+    if (!ok) return CHFSI_ERR_NUMERIC;
+    TRY(cholqr_pass(c, n, k, Y, false, &ok));
+    if (!ok) return CHFSI_ERR_NUMERIC;
+  }
+  TRY(cholqr_pass(c, n, k, Y, false, &ok));
+  if (!ok) return CHFSI_ERR_NUMERIC;
+  return CHFSI_OK;
+}
+
+// a7 ---------------------------------------------------------------------------------------
+chfsi_status reduced_eig(chfsi_ctx* c, int k, cplx* G, double* lam, cplx* W) {
+  char* work;
+  TRY(buf(c, "jac_work", jacobi_work_bytes(k), &work));
+  CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  CU(jacobi_eig(c->stream, k, G, lam, W, work, c->d_err, c->d_sweeps));
+  return CHFSI_OK;
+}
+
+// a6-a8: Z = H Y; G = Y^H Z; eig; Y <- Y W; Z <- Z W ----------------------------------------
+chfsi_status rayleigh_ritz(chfsi_ctx* c, int n, int k, const cplx* Hs, cplx* Y, double* lam, cplx* Z) {
+  cplx *G, *W, *T;
+  TRY(buf(c, "rr_G", (size_t)k * k, &G));
+  TRY(buf(c, "rr_W", (size_t)k * k, &W));
+  TRY(buf(c, "rr_T", (size_t)n * k, &T));
+  TRY(gemm(c, gemm_args(n, k, n, OP_N, Hs, n, OP_N, Y, n, Z, n, ONE, ZERO)));
+  TRY(gemm(c, gemm_args(k, k, n, OP_C, Y, n, OP_N, Z, n, G, k, ONE, ZERO)));
+  CU(hermitize(c->stream, k, G, k));
+  TRY(reduced_eig(c, k, G, lam, W));
+  TRY(gemm(c, gemm_args(n, k, k, OP_N, Y, n, OP_N, W, k, T, n, ONE, ZERO)));
+  CU(copy_block(c->stream, n, k, T, n, Y, n));
+  TRY(gemm(c, gemm_args(n, k, k, OP_N, Z, n, OP_N, W, k, T, n, ONE, ZERO)));
+  CU(copy_block(c->stream, n, k, T, n, Z, n));
+  return CHFSI_OK;
+}
+
+struct Timer {
+  chfsi_ctx* c;
+  double* acc;
+  int idx = 0;
+  int stage[8];
+  void start() { idx = 0; }
+  void mark(int s) {
+    if (idx < 15) {
+      cudaEventRecord(c->ev[idx], c->stream);
+      stage[idx] = s;
+      ++idx;
+    }
+  }
+  // after a sync: add elapsed time between consecutive marks to the stage of the later mark
+  void flush() {
+    for (int i = 1; i < idx && i < 8; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, c->ev[i - 1], c->ev[i]) == cudaSuccess) acc[stage[i]] += ms;
+    }
+    idx = 0;
+  }
+};
+
+// The iteration of Algorithm 1 on the stored standard-form problem.  Y (n x k) holds the
+// start block; on return Y holds the whole block sorted by Ritz value.
+chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, double a0, double* evals, cplx* Xout,
+                     const cplx* Linv, chfsi_info* info) {
+  const int n = c->n, nev = c->nev, k = nev + c->nex;
+  const double tol_lock = c->tol / c->kappa_L;
+  cplx *Z, *Y2;
+  double *lam, *res, *resabs;
+  int* perm;
+  TRY(buf(c, "it_Z", (size_t)n * k, &Z));
+  TRY(buf(c, "it_Y2", (size_t)n * k, &Y2));
+  TRY(buf(c, "it_lam", k, &lam));
+  TRY(buf(c, "it_res", k, &res));
+  TRY(buf(c, "it_resabs", k, &resabs));
+  TRY(buf(c, "it_perm", k, &perm));
+  TRY(ensure_host(c, k));
+  double* h_lam = c->h_d;
+  double* h_res = c->h_d + k;
+  double* h_lam2 = c->h_d + 2 * k;
+  int* h_perm = c->h_i;
+  int* h_deg = c->h_i + k;
+
+  std::vector<double> lam_locked;
+  std::vector<int> deg(k, c->degree);
+  int nl = 0, ka = k, it = 0;
+  double ms[8] = {0};
+  Timer tm{c, ms};
+  chfsi_status status = CHFSI_OK;
+  long long colsteps = 0, colsteps_lowp = 0;
+  double min_res = INFINITY, max_res_locked = 0.0;
+  std::vector<double> lam_active;
+  for (;;) {
+    ++it;
+    cplx* Ya = Y + (size_t)nl * n;
+    tm.start();
+    tm.mark(0);
+    // line 3: filter (mixed precision while every active residual is above the switch)
+    int prec = CHFSI_PREC_FP64;
+    if (c->prm.precision == CHFSI_PREC_MIXED && min_res > c->prm.mixed_switch) prec = CHFSI_PREC_MIXED;
+    long long cs = 0;
+    TRY(run_filter(c, n, ka, Hs, Ya, deg.data(), a, b, a0, prec, &cs));
+    colsteps += cs;
+    if (prec == CHFSI_PREC_MIXED) colsteps_lowp += cs;
+    tm.mark(2);
+    // line 4: QR against the locked vectors
+    TRY(orthonormalize(c, n, nl, Y, ka, Ya));
+    tm.mark(3);
+    // lines 5-7: Rayleigh-Ritz
+    TRY(rayleigh_ritz(c, n, ka, Hs, Ya, lam, Z));
+    tm.mark(4);
+    // residuals
+    CU(residual_norms(c->stream, n, ka, Z, n, Ya, n, lam, res, resabs));
+    CU(cudaMemcpyAsync(h_lam, lam, sizeof(double) * ka, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(h_res, res, sizeof(double) * ka, cudaMemcpyDeviceToHost, c->stream));
+    int h_err = 0;
+    CU(cudaMemcpyAsync(&h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    tm.mark(5);
+    CU(cudaStreamSynchronize(c->stream));
+    tm.flush();
+    if (h_err != DEV_OK) return map_dev_err(h_err);
+    for (int i = 0; i < ka; ++i)
+      if (!isfinite(h_res[i]) || !isfinite(h_lam[i])) return CHFSI_ERR_NUMERIC;
+    // lines 8-12: deflation and locking, i = converged .. nev
+    std::vector<int> lockv, rest;
+    for (int i = 0; i < ka; ++i) {
+      if (i < nev - nl && h_res[i] < tol_lock) lockv.push_back(i);
+      else rest.push_back(i);
+    }
+    // bounds of the next filter: a = largest Ritz value of the block, a0 = smallest seen
+    a = h_lam[ka - 1];
+    a0 = std::min(a0, h_lam[0]);
+    min_res = INFINITY;
+    for (int i : rest) min_res = std::min(min_res, h_res[i]);
+    for (int i : lockv) max_res_locked = std::max(max_res_locked, h_res[i]);
+    if (c->prm.per_vector_degree && !rest.empty()) {
+      // a10: degrees for the next filter, from the updated bounds (device kernel)
+      CU(vector_degrees(c->stream, ka, lam, res, a, b, tol_lock, c->prm.degree_min, c->prm.degree_max, perm));
+      CU(cudaMemcpyAsync(h_deg, perm, sizeof(int) * ka, cudaMemcpyDeviceToHost, c->stream));
+      CU(cudaStreamSynchronize(c->stream));
+    }
+    // new order of the active block: locked first, then the rest (by degree when per-vector)
+    std::vector<int> order;
+    order.insert(order.end(), lockv.begin(), lockv.end());
+    std::vector<int> rest_sorted = rest;
+    if (c->prm.per_vector_degree)
+      std::stable_sort(rest_sorted.begin(), rest_sorted.end(), [&](int x, int y) { return h_deg[x] > h_deg[y]; });
+    order.insert(order.end(), rest_sorted.begin(), rest_sorted.end());
+    for (int i : lockv) lam_locked.push_back(h_lam[i]);
+    lam_active.clear();
+    for (int i : rest_sorted) lam_active.push_back(h_lam[i]);
+    for (size_t q = 0; q < rest_sorted.size(); ++q)
+      deg[q] = c->prm.per_vector_degree ? h_deg[rest_sorted[q]] : c->degree;
+    bool identity = true;
+    for (int i = 0; i < ka; ++i) {
+      h_perm[i] = order[i];
+      identity = identity && order[i] == i;
+    }
+    if (!identity) {
+      CU(cudaMemcpyAsync(perm, h_perm, sizeof(int) * ka, cudaMemcpyHostToDevice, c->stream));
+      CU(gather_columns(c->stream, n, ka, perm, Ya, n, Y2, n));
+      CU(copy_block(c->stream, n, ka, Y2, n, Ya, n));
+    }
+    nl += (int)lockv.size();
+    ka -= (int)lockv.size();
+    if (nl >= nev || it >= c->prm.max_iter || ka == 0) break;
+  }
+  if (nl < nev) status = CHFSI_ERR_NO_CONV;
+  tm.start();
+  tm.mark(0);
+  // outputs: locked pairs by ascending eigenvalue (then the lowest active ones on NO_CONV)
+  std::vector<double> all_lam(lam_locked);
+  all_lam.insert(all_lam.end(), lam_active.begin(), lam_active.end());
+  std::vector<int> idx(k);
+  std::iota(idx.begin(), idx.begin() + nl, 0);
+  std::stable_sort(idx.begin(), idx.begin() + nl, [&](int x, int y) { return all_lam[x] < all_lam[y]; });
+  std::iota(idx.begin() + nl, idx.end(), nl);
+  std::stable_sort(idx.begin() + nl, idx.end(), [&](int x, int y) { return all_lam[x] < all_lam[y]; });
+  for (int i = 0; i < nev; ++i) {
+    h_perm[i] = idx[i];
+    h_lam2[i] = all_lam[idx[i]];
+  }
+  CU(cudaMemcpyAsync(perm, h_perm, sizeof(int) * nev, cudaMemcpyHostToDevice, c->stream));
+  CU(gather_columns(c->stream, n, nev, perm, Y, n, Y2, n));
+  CU(cudaMemcpyAsync(evals, h_lam2, sizeof(double) * nev, cudaMemcpyHostToDevice, c->stream));
+  // a11: X = L^{-H} Y
+  TRY(gemm(c, gemm_args(n, nev, n, OP_C, Linv, n, OP_N, Y2, n, (cplx*)Xout, n, ONE, ZERO, TRI_A_UPPER)));
+  tm.mark(6);
+  // sequence state: the whole block sorted by Ritz value
+  std::vector<int> all(k);
+  std::iota(all.begin(), all.end(), 0);
+  std::stable_sort(all.begin(), all.end(), [&](int x, int y) { return all_lam[x] < all_lam[y]; });
+  c->block_lam.resize(k);
+  for (int i = 0; i < k; ++i) {
+    h_perm[i] = all[i];
+    c->block_lam[i] = all_lam[all[i]];
+  }
+  CU(cudaMemcpyAsync(perm, h_perm, sizeof(int) * k, cudaMemcpyHostToDevice, c->stream));
+  CU(gather_columns(c->stream, n, k, perm, Y, n, Y2, n));
+  CU(copy_block(c->stream, n, k, Y2, n, Y, n));
+  CU(cudaStreamSynchronize(c->stream));
+  tm.flush();
+  if (info) {
+    info->iterations = it;
+    info->locked = nl;
+    info->filter_col_steps = colsteps;
+    info->filter_col_steps_lowp = colsteps_lowp;
+    info->max_resid = max_res_locked;
+    info->kappa_L = c->kappa_L;
+    info->bounds[0] = a;
+    info->bounds[1] = b;
+    info->bounds[2] = a0;
+    for (int s = 0; s < 7; ++s) info->ms_stage[s] += ms[s];
+  }
+  return status;
+}
+
+bool valid_ptrs(std::initializer_list<const void*> ps) {
+  for (auto p : ps)
+    if (!p) return false;
+  return true;
+}
+
+chfsi_status setup_device(chfsi_ctx* c) {
+  CU(cudaSetDevice(c->device));
+  return CHFSI_OK;
+}
+
+chfsi_status solve_common(chfsi_ctx* c, const cplx* H, const cplx* S, const cplx* X0, bool seeded, double* evals,
+                          void* X, chfsi_info* info) {
+  const int n = c->n, k = c->nev + c->nex;
+  cudaEvent_t t0 = c->ev[14], t1 = c->ev[15];
+  CU(cudaEventRecord(t0, c->stream));
+  cplx *L, *Linv, *Hs, *Y;
+  TRY(buf(c, "L", (size_t)n * n, &L));
+  TRY(buf(c, "Linv", (size_t)n * n, &Linv));
+  TRY(buf(c, "Hs", (size_t)n * n, &Hs));
+  TRY(buf(c, "Y", (size_t)n * k, &Y));
+  double *al, *be, *bd;
+  TRY(buf(c, "lz_alpha", 256, &al));
+  TRY(buf(c, "lz_beta", 256, &be));
+  TRY(buf(c, "lz_bounds", 16, &bd));
+  if (info) memset(info, 0, sizeof(*info));
+  cudaEvent_t r0 = c->ev[12], r1 = c->ev[13];
+  CU(cudaEventRecord(r0, c->stream));
+  if (S) {
+    if (seeded) {
+      // S changes inside a sequence: carry the block over as X = L_old^{-H} Y, Y_new = L_new^H X
+      cplx* T;
+      TRY(buf(c, "tmp_nk", (size_t)n * k, &T));
+      TRY(gemm(c, gemm_args(n, k, n, OP_C, Linv, n, OP_N, Y, n, T, n, ONE, ZERO, TRI_A_UPPER)));
+      TRY(factor_S(c, n, S, L, Linv));
+      TRY(gemm(c, gemm_args(n, k, n, OP_C, L, n, OP_N, T, n, Y, n, ONE, ZERO, TRI_A_UPPER)));
+    } else {
+      TRY(factor_S(c, n, S, L, Linv));
+    }
+    TRY(kappa_L(c, n, S, Linv, &c->kappa_L));
+  }
+  TRY(transform(c, n, H, Linv, Hs));
+  if (!seeded) {
+    if (X0) {
+      // Y0 = L^H X0
+      TRY(gemm(c, gemm_args(n, k, n, OP_C, L, n, OP_N, X0, n, Y, n, ONE, ZERO, TRI_A_UPPER)));
+    } else {
+      CU(splitmix_block(c->stream, n, k, c->prm.seed, 2, Y, n));
+    }
+  }
+  CU(cudaEventRecord(r1, c->stream));
+  // line 1: Lanczos
+  TRY(lanczos_H(c, n, Hs, c->prm.lanczos_steps, k, nullptr, al, be, bd));
+  double h[4];
+  CU(cudaMemcpyAsync(h, bd, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  float ms_reduce = 0.f, ms_lanczos = 0.f;
+  cudaEventElapsedTime(&ms_reduce, r0, r1);
+  double b = h[0], a = h[1], a0 = h[2];
+  if (seeded && !c->block_lam.empty()) {
+    a = c->block_lam.back();
+    a0 = std::min(c->block_lam.front(), h[2]);
+  }
+  if (!(a < b) || !(a0 < a)) {
+    // degenerate bounds (e.g. a spectrum narrower than the block): widen around the Lanczos values
+    a = 0.5 * (h[2] + h[3]);
+    a0 = std::min(a0, h[2]);
+    if (!(a < b) || !(a0 < a)) return CHFSI_ERR_NUMERIC;
+  }
+  cudaEvent_t l1 = c->ev[11];
+  CU(cudaEventRecord(l1, c->stream));
+  CU(cudaEventSynchronize(l1));
+  cudaEventElapsedTime(&ms_lanczos, r1, l1);
+  chfsi_status st = iterate(c, Hs, Y, a, b, a0, evals, (cplx*)X, Linv, info);
+  CU(cudaEventRecord(t1, c->stream));
+  CU(cudaEventSynchronize(t1));
+  if (info) {
+    float tot = 0.f;
+    cudaEventElapsedTime(&tot, t0, t1);
+    info->ms_stage[0] += ms_reduce;
+    info->ms_stage[1] += ms_lanczos;
+    info->ms_stage[7] = tot;
+  }
+  if (st == CHFSI_OK || st == CHFSI_ERR_NO_CONV) c->have_seq = true;
+  return st;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+extern "C" {
+
+const char* chfsi_status_string(chfsi_status s) {
+  switch (s) {
+    case CHFSI_OK: return "ok";
+    case CHFSI_ERR_ARG: return "invalid argument";
+    case CHFSI_ERR_NOT_HPD: return "S is not Hermitian positive definite";
+    case CHFSI_ERR_NO_CONV: return "not converged";
+    case CHFSI_ERR_OOM: return "device out of memory";
+    case CHFSI_ERR_CUDA: return "CUDA error";
+    case CHFSI_ERR_TIMEOUT: return "device wait timed out";
+    case CHFSI_ERR_STATE: return "call out of order";
+    case CHFSI_ERR_NUMERIC: return "non-finite value or breakdown";
+  }
+  return "unknown status";
+}
+
+chfsi_status chfsi_default_params(chfsi_params* p) {
+  if (!p) return CHFSI_ERR_ARG;
+  memset(p, 0, sizeof(*p));
+  p->degree = 20;
+  p->degree_min = 10;
+  p->degree_max = 25;
+  p->per_vector_degree = 0;
+  p->max_iter = 50;
+  p->lanczos_steps = 20;
+  p->precision = CHFSI_PREC_FP64;
+  p->mixed_switch = 1e-5;
+  p->seed = 0;
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_create(chfsi_ctx** out, int device, void* cuda_stream, const chfsi_params* p) {
+  if (!out) return CHFSI_ERR_ARG;
+  *out = nullptr;
+  chfsi_params prm;
+  if (p) prm = *p;
+  else chfsi_default_params(&prm);
+  if (prm.degree < 1 || prm.max_iter < 1 || prm.lanczos_steps < 2 || prm.lanczos_steps > 256 ||
+      prm.degree_min < 1 || prm.degree_max < prm.degree_min ||
+      (prm.precision != CHFSI_PREC_FP64 && prm.precision != CHFSI_PREC_MIXED))
+    return CHFSI_ERR_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return CHFSI_ERR_ARG;
+  chfsi_ctx* c = new chfsi_ctx();
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->prm = prm;
+  c->degree = prm.degree;
+  chfsi_status s = setup_device(c);
+  if (s == CHFSI_OK) s = cu(cudaMalloc(&c->d_err, 2 * sizeof(int)), "err");
+  if (s == CHFSI_OK) {
+    c->d_sweeps = c->d_err + 1;
+    s = cu(cudaMemset(c->d_err, 0, 2 * sizeof(int)), "err");
+  }
+  for (int i = 0; i < 16 && s == CHFSI_OK; ++i) s = cu(cudaEventCreate(&c->ev[i]), "event");
+  if (s != CHFSI_OK) {
+    chfsi_destroy(c);
+    return s;
+  }
+  *out = c;
+  return CHFSI_OK;
+}
+
+void chfsi_destroy(chfsi_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  c->arena.release();
+  if (c->tc) tc_filter_free(c->tc);
+  if (c->d_err) cudaFree(c->d_err);
+  if (c->h_d) cudaFreeHost(c->h_d);
+  if (c->h_i) cudaFreeHost(c->h_i);
+  for (int i = 0; i < 16; ++i)
+    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  delete c;
+}
+
+chfsi_status chfsi_solve(chfsi_ctx* c, const void* H, const void* S, int n, int nev, int nex, const void* X0,
+                         double tol, int degree, double* evals, void* X, chfsi_info* info) {
+  if (!c || !valid_ptrs({H, S, evals, X})) return CHFSI_ERR_ARG;
+  if (n < 2 || nev < 1 || nex < 0 || nev + nex > n || !(tol > 0.0)) return CHFSI_ERR_ARG;
+  TRY(setup_device(c));
+  c->n = n;
+  c->nev = nev;
+  c->nex = nex;
+  c->tol = tol;
+  c->degree = degree > 0 ? degree : c->prm.degree;
+  c->have_seq = false;
+  c->block_lam.clear();
+  return solve_common(c, (const cplx*)H, (const cplx*)S, (const cplx*)X0, false, evals, X, info);
+}
+
+chfsi_status chfsi_next_in_sequence(chfsi_ctx* c, const void* H_next, const void* S_next, double* evals, void* X,
+                                    chfsi_info* info) {
+  if (!c || !valid_ptrs({H_next, evals, X})) return CHFSI_ERR_ARG;
+  if (!c->have_seq) return CHFSI_ERR_STATE;
+  TRY(setup_device(c));
+  return solve_common(c, (const cplx*)H_next, (const cplx*)S_next, nullptr, true, evals, X, info);
+}
+
+// ---- stage entry points ----------------------------------------------------------------
+chfsi_status chfsi_cholesky(chfsi_ctx* c, int n, const void* S, void* L) {
+  if (!c || !valid_ptrs({S, L}) || n < 1) return CHFSI_ERR_ARG;
+  TRY(setup_device(c));
+  return factor_S(c, n, (const cplx*)S, (cplx*)L, nullptr);
+}
+
+chfsi_status chfsi_reduce(chfsi_ctx* c, int n, const void* H, const void* L, void* Hs) {
+  if (!c || !valid_ptrs({H, L, Hs}) || n < 1) return CHFSI_ERR_ARG;
+  TRY(setup_device(c));
+  cplx* Linv;
+  TRY(buf(c, "Linv_stage", (size_t)n * n, &Linv));
+  CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  CU(trtri_lower(c->stream, n, (const cplx*)L, n, Linv, n, c->d_err));
+  TRY(transform(c, n, (const cplx*)H, Linv, (cplx*)Hs));
+  int e = 0;
+  TRY(read_err(c, &e));
+  return map_dev_err(e);
+}
+
+chfsi_status chfsi_lanczos(chfsi_ctx* c, int n, const void* Hs, int steps, int k, const void* v0, double* alpha,
+                           double* beta, double* bounds) {
+  if (!c || !valid_ptrs({Hs, alpha, beta, bounds}) || n < 2 || steps < 2 || steps > 256 || steps > n || k < 1)
+    return CHFSI_ERR_ARG;
+  TRY(setup_device(c));
+  TRY(lanczos_H(c, n, (const cplx*)Hs, steps, k, (const cplx*)v0, alpha, beta, bounds));
+  CU(cudaStreamSynchronize(c->stream));
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_filter(chfsi_ctx* c, int n, int k, const void* Hs, void* Y, int m, double a, double b, double a0,
+                          int precision) {
+  if (!c || !valid_ptrs({Hs, Y}) || n < 1 || k < 1 || m < 1) return CHFSI_ERR_ARG;
+  if (precision != CHFSI_PREC_FP64 && precision != CHFSI_PREC_MIXED) return CHFSI_ERR_ARG;
+  TRY(setup_device(c));
+  std::vector<int> deg(k, m);
+  TRY(run_filter(c, n, k, (const cplx*)Hs, (cplx*)Y, deg.data(), a, b, a0, precision, nullptr));
+  CU(cudaStreamSynchronize(c->stream));
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_filter_degrees(chfsi_ctx* c, int n, int k, const void* Hs, void* Y, const int* deg, double a,
+                                  double b, double a0, int precision) {
+  if (!c || !valid_ptrs({Hs, Y, deg}) || n < 1 || k < 1) return CHFSI_ERR_ARG;
+  if (precision != CHFSI_PREC_FP64 && precision != CHFSI_PREC_MIXED) return CHFSI_ERR_ARG;
+  TRY(setup_device(c));
+  TRY(run_filter(c, n, k, (const cplx*)Hs, (cplx*)Y, deg, a, b, a0, precision, nullptr));
+  CU(cudaStreamSynchronize(c->stream));
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_orthonormalize(chfsi_ctx* c, int n, int nl, const void* Ylocked, int k, void* Y) {
+  if (!c || !Y || n < 1 || k < 1 || nl < 0 || nl + k > n || (nl > 0 && !Ylocked)) return CHFSI_ERR_ARG;
+  TRY(setup_device(c));
+  TRY(orthonormalize(c, n, nl, (const cplx*)Ylocked, k, (cplx*)Y));
+  CU(cudaStreamSynchronize(c->stream));
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_rayleigh_ritz(chfsi_ctx* c, int n, int k, const void* Hs, void* Y, double* lam, void* Z) {
+  if (!c || !valid_ptrs({Hs, Y, lam, Z}) || n < 1 || k < 1 || k > n) return CHFSI_ERR_ARG;
+  TRY(setup_device(c));
+  TRY(rayleigh_ritz(c, n, k, (const cplx*)Hs, (cplx*)Y, lam, (cplx*)Z));
+  int e = 0;
+  TRY(read_err(c, &e));
+  return map_dev_err(e);
+}
+
+chfsi_status chfsi_reduced_eig(chfsi_ctx* c, int k, const void* G, double* lam, void* W) {
+  if (!c || !valid_ptrs({G, lam, W}) || k < 1) return CHFSI_ERR_ARG;
+  TRY(setup_device(c));
+  cplx* Gc;
+  TRY(buf(c, "eig_G", (size_t)k * k, &Gc));
+  CU(cudaMemcpyAsync(Gc, G, sizeof(cplx) * (size_t)k * k, cudaMemcpyDeviceToDevice, c->stream));
+  TRY(reduced_eig(c, k, Gc, lam, (cplx*)W));
+  int e = 0;
+  TRY(read_err(c, &e));
+  return map_dev_err(e);
+}
+
+chfsi_status chfsi_residuals(chfsi_ctx* c, int n, int k, const void* Z, const void* Y, const double* lam,
+                             double* res) {
+  if (!c || !valid_ptrs({Z, Y, lam, res}) || n < 1 || k < 1) return CHFSI_ERR_ARG;
+  TRY(setup_device(c));
+  double* ra;
+  TRY(buf(c, "res_abs", k, &ra));
+  CU(residual_norms(c->stream, n, k, (const cplx*)Z, n, (const cplx*)Y, n, lam, res, ra));
+  CU(cudaStreamSynchronize(c->stream));
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_degrees(chfsi_ctx* c, int k, const double* lam, const double* res, double a, double b, double tol,
+                           int m_min, int m_max, int* deg) {
+  if (!c || !valid_ptrs({lam, res, deg}) || k < 1 || m_min < 1 || m_max < m_min || !(b > a)) return CHFSI_ERR_ARG;
+  TRY(setup_device(c));
+  CU(vector_degrees(c->stream, k, lam, res, a, b, tol, m_min, m_max, deg));
+  CU(cudaStreamSynchronize(c->stream));
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_back_transform(chfsi_ctx* c, int n, int k, const void* L, const void* Y, void* X) {
+  if (!c || !valid_ptrs({L, Y, X}) || n < 1 || k < 1) return CHFSI_ERR_ARG;
+  TRY(setup_device(c));
+  cplx* Linv;
+  TRY(buf(c, "Linv_stage", (size_t)n * n, &Linv));
+  CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  CU(trtri_lower(c->stream, n, (const cplx*)L, n, Linv, n, c->d_err));
+  TRY(gemm(c, gemm_args(n, k, n, OP_C, Linv, n, OP_N, (const cplx*)Y, n, (cplx*)X, n, ONE, ZERO, TRI_A_UPPER)));
+  int e = 0;
+  TRY(read_err(c, &e));
+  return map_dev_err(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,25 @@
+// FP64 dense factorisations and small kernels used around the filter.
+#pragma once
+#include "zgemm.cuh"
+
+// In-place blocked Cholesky A = L L^H of an n x n Hermitian matrix (lower triangle used;
+// the strictly upper triangle is zeroed on exit).  A non-positive or non-finite pivot sets
+// *err = DEV_ERR_NOT_HPD; later blocks are then skipped by the kernels.
+cudaError_t chol_lower(cudaStream_t s, int n, cplx* A, long lda, int* err);
+// X = L^{-1} for lower-triangular L (X fully written, upper triangle zero).
+cudaError_t trtri_lower(cudaStream_t s, int n, const cplx* L, long ldl, cplx* X, long ldx, int* err);
+// A <- (A + A^H) / 2 (diagonal made real).
+cudaError_t hermitize(cudaStream_t s, int n, cplx* A, long lda);
+// dst[:, j] = src[:, perm[j]] for j < cnt (n rows); and lam_dst[j] = lam_src[perm[j]].
+cudaError_t gather_columns(cudaStream_t s, int n, int cnt, const int* perm, const cplx* src, long lds,
+                           cplx* dst, long ldd);
+cudaError_t gather_values(cudaStream_t s, int cnt, const int* perm, const double* src, double* dst);
+// Column-wise relative residuals res[j] = ||Z_j - lam_j Y_j|| / ||Z_j||, and abs[j] the numerator.
+cudaError_t residual_norms(cudaStream_t s, int n, int k, const cplx* Z, long ldz, const cplx* Y, long ldy,
+                           const double* lam, double* res, double* resabs);
+// SplitMix64 complex block: element (i, j) = u(2(j n + i)) + i u(2(j n + i) + 1), u in [-0.5, 0.5),
+// counter offset stream * 2^40 (the same definition the oracle uses).
+cudaError_t splitmix_block(cudaStream_t s, int n, int k, unsigned long long seed, unsigned long long stream,
+                           cplx* Y, long ldy);
+// Copy an n x k block between leading dimensions.
+cudaError_t copy_block(cudaStream_t s, int n, int k, const cplx* src, long lds, cplx* dst, long ldd);

@@ -1,0 +1,201 @@
+// Reduced eigenproblem of Rayleigh-Ritz (Algorithm 1: "Solving reduced problem G w = lam w";
+// the paper used the parallel MRRR solver of its library).  On the GPU a parallel cyclic
+// Jacobi is used instead: in each round the k/2 disjoint index pairs of a round-robin
+// schedule rotate at once, and since the combined transform U is block diagonal over the
+// pairs, every 2 x 2 block (P, R) of G is updated independently as U_P^H G_PR U_R, so one
+// pass over G per round suffices.  Rounds are separated by a bounded grid barrier inside a
+// single cooperative launch.  Near-diagonal G (later outer iterations and sequence solves)
+// converges in one or two sweeps.
+#include <math.h>
+#include "jacobi.cuh"
+
+namespace {
+
+struct Rot {
+  cplx upp, upq, uqp, uqq;   // U restricted to (p, q): column p = (upp, uqp), column q = (upq, uqq)
+  int p, q, on;
+  int pad;
+};
+
+struct JacobiArgs {
+  int k, kk;
+  cplx* A;
+  cplx* V;
+  Rot* rot;
+  int* rot_count;     // per sweep
+  double* fro;
+  GridBarrier bar;
+  int* err;
+  int* sweeps;
+  int max_sweeps;
+};
+
+__device__ __forceinline__ int rr_slot(int x, int r, int kk) { return x == 0 ? 0 : 1 + (x - 1 + r) % (kk - 1); }
+
+__global__ void fro_kernel(int k, const cplx* A, double* out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (long e = threadIdx.x; e < (long)k * k; e += blockDim.x) s += cabs2(A[e]);
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) *out = sqrt(s);
+}
+
+__global__ void __launch_bounds__(256) jacobi_kernel(JacobiArgs g) {
+  const int k = g.k, kk = g.kk, np = kk / 2;
+  const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const long nth = (long)gridDim.x * blockDim.x;
+  const double thresh = 2.220446049250313e-16 * (*g.fro);
+  for (long e = tid; e < (long)k * k; e += nth) g.V[e] = cmk((e % k) == (e / k) ? 1.0 : 0.0, 0.0);
+  int sweep = 0;
+  bool converged = false;
+  for (; sweep < g.max_sweeps && !converged; ++sweep) {
+    for (int r = 0; r < kk - 1; ++r) {
+      // phase 1: rotation of each pair from the current 2 x 2 diagonal block
+      for (long j = tid; j < np; j += nth) {
+        int p = rr_slot((int)j, r, kk), q = rr_slot(kk - 1 - (int)j, r, kk);
+        if (p > q) { int t = p; p = q; q = t; }
+        Rot R;
+        R.p = p; R.q = q; R.on = 0;
+        R.upp = cmk(1, 0); R.uqq = cmk(1, 0); R.upq = cmk(0, 0); R.uqp = cmk(0, 0);
+        if (q < k) {
+          cplx apq = g.A[p + (long)q * k];
+          double ar = sqrt(cabs2(apq));
+          if (ar > thresh) {
+            double app = g.A[p + (long)p * k].x, aqq = g.A[q + (long)q * k].x;
+            cplx ph = cmk(apq.x / ar, apq.y / ar);
+            double tau = (aqq - app) / (2.0 * ar);
+            double t = (tau < 0.0 ? -1.0 : 1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+            R.upp = cmk(c, 0.0);
+            R.uqp = cmk(-s * ph.x, s * ph.y);     // -s conj(ph)
+            R.upq = cmk(s, 0.0);
+            R.uqq = cmk(c * ph.x, -c * ph.y);     // c conj(ph)
+            R.on = 1;
+            atomicAdd(&g.rot_count[sweep], 1);
+          }
+        }
+        g.rot[j] = R;
+      }
+      if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
+      // phase 2: G_PR <- U_P^H G_PR U_R for all block pairs, and V_R <- V_R U_R
+      const long nblk = (long)np * np;
+      for (long e = tid; e < nblk + (long)k * np; e += nth) {
+        if (e < nblk) {
+          const Rot P = g.rot[e % np], R = g.rot[e / np];
+          if (!P.on && !R.on) continue;
+          const bool pq_ok = P.q < k, rs_ok = R.q < k;
+          cplx b00 = g.A[P.p + (long)R.p * k];
+          cplx b01 = rs_ok ? g.A[P.p + (long)R.q * k] : cmk(0, 0);
+          cplx b10 = pq_ok ? g.A[P.q + (long)R.p * k] : cmk(0, 0);
+          cplx b11 = (pq_ok && rs_ok) ? g.A[P.q + (long)R.q * k] : cmk(0, 0);
+          // T = B U_R
+          cplx t00 = cadd(cmul(b00, R.upp), cmul(b01, R.uqp));
+          cplx t01 = cadd(cmul(b00, R.upq), cmul(b01, R.uqq));
+          cplx t10 = cadd(cmul(b10, R.upp), cmul(b11, R.uqp));
+          cplx t11 = cadd(cmul(b10, R.upq), cmul(b11, R.uqq));
+          // N = U_P^H T
+          cplx n00 = cadd(cmul(cconj(P.upp), t00), cmul(cconj(P.uqp), t10));
+          cplx n01 = cadd(cmul(cconj(P.upp), t01), cmul(cconj(P.uqp), t11));
+          cplx n10 = cadd(cmul(cconj(P.upq), t00), cmul(cconj(P.uqq), t10));
+          cplx n11 = cadd(cmul(cconj(P.upq), t01), cmul(cconj(P.uqq), t11));
+          if (e % np == e / np && P.on) {   // diagonal block: exactly diagonal afterwards
+            n00.y = 0.0; n11.y = 0.0; n01 = cmk(0, 0); n10 = cmk(0, 0);
+          }
+          g.A[P.p + (long)R.p * k] = n00;
+          if (rs_ok) g.A[P.p + (long)R.q * k] = n01;
+          if (pq_ok) g.A[P.q + (long)R.p * k] = n10;
+          if (pq_ok && rs_ok) g.A[P.q + (long)R.q * k] = n11;
+        } else {
+          const long f = e - nblk;
+          const int i = (int)(f % k);
+          const Rot R = g.rot[f / k];
+          if (!R.on) continue;
+          cplx x = g.V[i + (long)R.p * k], y = g.V[i + (long)R.q * k];
+          g.V[i + (long)R.p * k] = cadd(cmul(x, R.upp), cmul(y, R.uqp));
+          g.V[i + (long)R.q * k] = cadd(cmul(x, R.upq), cmul(y, R.uqq));
+        }
+      }
+      if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
+    }
+    converged = (*(volatile int*)&g.rot_count[sweep]) == 0;
+  }
+  if (tid == 0) {
+    *g.sweeps = sweep;
+    if (!converged) atomicExch(g.err, DEV_ERR_NO_CONV);
+  }
+}
+
+// rank sort of the diagonal; W = V permuted, lam ascending (ties by index)
+__global__ void jacobi_sort_kernel(int k, const cplx* A, const cplx* V, double* lam, cplx* W) {
+  for (int i = blockIdx.x; i < k; i += gridDim.x) {
+    const double li = A[i + (long)i * k].x;
+    __shared__ int rank_sh;
+    if (threadIdx.x == 0) rank_sh = 0;
+    __syncthreads();
+    int cnt = 0;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+      double lj = A[j + (long)j * k].x;
+      if (lj < li || (lj == li && j < i)) ++cnt;
+    }
+    atomicAdd(&rank_sh, cnt);
+    __syncthreads();
+    const int rk = rank_sh;
+    if (threadIdx.x == 0) lam[rk] = li;
+    for (int r = threadIdx.x; r < k; r += blockDim.x) W[r + (long)rk * k] = V[r + (long)i * k];
+    __syncthreads();
+  }
+}
+
+int coop_blocks(int needed) {
+  static int cap = 0;
+  if (cap == 0) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_kernel, 256, 0);
+    cap = sms * (occ < 1 ? 1 : (occ > 2 ? 2 : occ));
+  }
+  return needed < cap ? (needed < 1 ? 1 : needed) : cap;
+}
+}  // namespace
+
+size_t jacobi_work_bytes(int k) {
+  const int kk = k + (k & 1);
+  const int max_sweeps = 64;
+  return sizeof(cplx) * (size_t)k * k + sizeof(Rot) * (size_t)(kk / 2) + sizeof(int) * max_sweeps +
+         sizeof(double) * 2 + sizeof(unsigned) * 4 + 256;
+}
+
+cudaError_t jacobi_eig(cudaStream_t s, int k, cplx* G, double* lam, cplx* W, void* work, int* err, int* sweeps) {
+  if (k <= 0) return cudaSuccess;
+  const int kk = k + (k & 1);
+  const int max_sweeps = 64;
+  char* w = (char*)work;
+  JacobiArgs g{};
+  g.k = k;
+  g.kk = kk;
+  g.A = G;
+  g.V = (cplx*)w;                 w += sizeof(cplx) * (size_t)k * k;
+  g.rot = (Rot*)w;                w += sizeof(Rot) * (size_t)(kk / 2);
+  g.rot_count = (int*)w;          w += sizeof(int) * max_sweeps;
+  g.fro = (double*)w;             w += sizeof(double) * 2;
+  unsigned* bar = (unsigned*)w;
+  g.bar.count = bar;
+  g.bar.gen = bar + 1;
+  g.err = err;
+  g.sweeps = sweeps;
+  g.max_sweeps = max_sweeps;
+  cudaError_t e = cudaMemsetAsync(g.rot_count, 0, sizeof(int) * max_sweeps + sizeof(double) * 2 + sizeof(unsigned) * 4, s);
+  if (e != cudaSuccess) return e;
+  fro_kernel<<<1, 1024, 0, s>>>(k, G, g.fro);
+  if (kk < 2) {
+    // 1 x 1: nothing to rotate
+  }
+  const long work_items = (long)(kk / 2) * (kk / 2) + (long)k * (kk / 2);
+  int blocks = coop_blocks((int)((work_items + 255) / 256));
+  void* args[] = {&g};
+  e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(blocks), dim3(256), args, 0, s);
+  if (e != cudaSuccess) return e;
+  jacobi_sort_kernel<<<k < 1024 ? k : 1024, 128, 0, s>>>(k, G, (const cplx*)g.V, lam, W);
+  return cudaGetLastError();
+}

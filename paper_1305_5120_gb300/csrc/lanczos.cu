@@ -1,0 +1,172 @@
+// Lanczos estimate of the spectral upper bound (Algorithm 1, line 1; the estimator of Zhou &
+// Li 2011 cited in Section 3): memory-bound Hermitian GEMV plus single-CTA vector updates,
+// and Sturm-sequence bisection on the small tridiagonal T.
+#include <math.h>
+#include "lanczos.cuh"
+
+namespace {
+
+__global__ void herm_gemv_kernel(int n, const cplx* __restrict__ H, long ldh, const cplx* __restrict__ v,
+                                 cplx* __restrict__ w) {
+  const int lane = threadIdx.x & 31;
+  const long col = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
+  if (col >= n) return;
+  const cplx* hc = H + col * ldh;
+  double re = 0.0, im = 0.0;
+  for (long r = lane; r < n; r += 32) {
+    cplx h = __ldg(hc + r), x = __ldg(v + r);
+    // conj(h) * x
+    re = fma(h.x, x.x, re);
+    re = fma(h.y, x.y, re);
+    im = fma(h.x, x.y, im);
+    im = fma(-h.y, x.x, im);
+  }
+  re = warp_sum(re);
+  im = warp_sum(im);
+  if (lane == 0) w[col] = cmk(re, im);
+}
+
+__global__ void normalize_kernel(int n, cplx* v) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += cabs2(v[i]);
+  s = block_sum(s, sh);
+  const double inv = 1.0 / sqrt(s);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = cscale(v[i], inv);
+}
+
+__global__ void lanczos_step_kernel(int n, int j, cplx* v, cplx* vp, cplx* w, double* alpha, double* beta) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    cplx a = v[i], b = w[i];
+    s += a.x * b.x + a.y * b.y;     // Re(conj(v) w)
+  }
+  const double al = block_sum(s, sh);
+  const double bp = (j > 0) ? beta[j - 1] : 0.0;
+  double t = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    cplx x = w[i], a = v[i], p = vp[i];
+    x.x -= al * a.x + bp * p.x;
+    x.y -= al * a.y + bp * p.y;
+    w[i] = x;
+    t += cabs2(x);
+  }
+  const double be = sqrt(block_sum(t, sh));
+  const double inv = be > 0.0 ? 1.0 / be : 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    vp[i] = v[i];
+    v[i] = cscale(w[i], inv);
+  }
+  if (threadIdx.x == 0) {
+    alpha[j] = al;
+    beta[j] = be;
+  }
+}
+
+// number of eigenvalues of tridiag(beta, alpha, beta) below x (Sturm sequence / LDL^T pivots)
+__device__ int sturm_count(int m, const double* al, const double* be, double x) {
+  int cnt = 0;
+  double q = 1.0;
+  for (int i = 0; i < m; ++i) {
+    double b2 = (i > 0) ? be[i - 1] * be[i - 1] : 0.0;
+    q = al[i] - x - ((i > 0) ? b2 / q : 0.0);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// index-th smallest eigenvalue (0-based) by bisection on the Gershgorin interval
+__device__ double tridiag_eig_bisect(int m, const double* al, const double* be, int index) {
+  double lo = al[0], hi = al[0];
+  for (int i = 0; i < m; ++i) {
+    double r = ((i > 0) ? fabs(be[i - 1]) : 0.0) + ((i + 1 < m) ? fabs(be[i]) : 0.0);
+    lo = fmin(lo, al[i] - r);
+    hi = fmax(hi, al[i] + r);
+  }
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_count(m, al, be, mid) <= index) lo = mid;
+    else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+__global__ void lanczos_bounds_kernel(int steps, int n, int k, const double* alpha, const double* beta,
+                                      double* out) {
+  __shared__ double al[256], be[256];
+  const int m = steps;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    al[i] = alpha[i];
+    be[i] = beta[i];
+  }
+  __syncthreads();
+  // j = max(1, ceil(m k / n)) + 1 (1-based), at most m - 1
+  long prod = (long)m * k;
+  int j = (int)((prod + n - 1) / n);
+  if (j < 1) j = 1;
+  j += 1;
+  if (j > m - 1) j = m - 1;
+  if (j < 1) j = 1;
+  if (threadIdx.x == 0) {
+    double mu_max = tridiag_eig_bisect(m, al, be, m - 1);
+    out[0] = mu_max + fabs(be[m - 1]);
+    out[3] = mu_max;
+  } else if (threadIdx.x == 1) {
+    out[1] = tridiag_eig_bisect(m, al, be, j - 1);
+  } else if (threadIdx.x == 2) {
+    out[2] = tridiag_eig_bisect(m, al, be, 0);
+  }
+}
+
+__global__ void vector_degrees_kernel(int k, const double* lam, const double* res, double a, double b, double tol,
+                                      int m_min, int m_max, int* deg) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= k) return;
+  const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+  const double t = fabs((lam[i] - c) / e), r = res[i];
+  int m;
+  if (r <= tol) m = m_min;
+  else if (t <= 1.0) m = m_max;
+  else {
+    double rho = 1.0 / (t + sqrt(t * t - 1.0));
+    double need = log(tol / r) / log(rho);
+    double mc = ceil(need);
+    m = mc < m_min ? m_min : (mc > m_max ? m_max : (int)mc);
+  }
+  deg[i] = m;
+}
+}  // namespace
+
+cudaError_t herm_gemv(cudaStream_t s, int n, const cplx* H, long ldh, const cplx* v, cplx* w) {
+  const long threads = 32L * n;
+  herm_gemv_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(n, H, ldh, v, w);
+  return cudaGetLastError();
+}
+
+cudaError_t normalize_vec(cudaStream_t s, int n, cplx* v) {
+  normalize_kernel<<<1, 1024, 0, s>>>(n, v);
+  return cudaGetLastError();
+}
+
+cudaError_t lanczos_step(cudaStream_t s, int n, int j, cplx* v, cplx* v_prev, cplx* w, double* alpha,
+                         double* beta) {
+  lanczos_step_kernel<<<1, 1024, 0, s>>>(n, j, v, v_prev, w, alpha, beta);
+  return cudaGetLastError();
+}
+
+cudaError_t lanczos_bounds(cudaStream_t s, int steps, int n, int k, const double* alpha, const double* beta,
+                           double* out) {
+  if (steps < 2 || steps > 256) return cudaErrorInvalidValue;
+  lanczos_bounds_kernel<<<1, 32, 0, s>>>(steps, n, k, alpha, beta, out);
+  return cudaGetLastError();
+}
+
+cudaError_t vector_degrees(cudaStream_t s, int k, const double* lam, const double* res, double a, double b,
+                           double tol, int m_min, int m_max, int* deg) {
+  if (k <= 0) return cudaSuccess;
+  vector_degrees_kernel<<<(k + 127) / 128, 128, 0, s>>>(k, lam, res, a, b, tol, m_min, m_max, deg);
+  return cudaGetLastError();
+}

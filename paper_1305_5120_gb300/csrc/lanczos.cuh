@@ -1,0 +1,22 @@
+// Lanczos spectral-bound estimator (Algorithm 1, line 1) and the per-vector degree rule.
+#pragma once
+#include "common.cuh"
+
+// w = H v for Hermitian H (column-major): w_i = sum_r conj(H[r, i]) v_r, one warp per column
+// (each warp streams one contiguous column with 16-byte loads).
+cudaError_t herm_gemv(cudaStream_t s, int n, const cplx* H, long ldh, const cplx* v, cplx* w);
+// v <- v / ||v||   (single CTA)
+cudaError_t normalize_vec(cudaStream_t s, int n, cplx* v);
+// One Lanczos recurrence step on (v, v_prev, w = Op v):  alpha_j = Re(v^H w);
+// w -= alpha_j v + beta_{j-1} v_prev; beta_j = ||w||; v_prev <- v; v <- w / beta_j.
+cudaError_t lanczos_step(cudaStream_t s, int n, int j, cplx* v, cplx* v_prev, cplx* w, double* alpha,
+                         double* beta);
+// From T = tridiag(beta, alpha, beta) of `steps` steps: out[0] = b_sup = mu_max + |beta_last|,
+// out[1] = a = mu_j (j = max(1, ceil(steps*k/n)) + 1, 1-based, at most steps-1), out[2] = a0 = mu_min,
+// out[3] = mu_max.  Eigenvalues of T by Sturm-count bisection.
+cudaError_t lanczos_bounds(cudaStream_t s, int steps, int n, int k, const double* alpha, const double* beta,
+                           double* out);
+// m_i = clamp(ceil(ln(tol / r_i) / ln(rho_i)), m_min, m_max), rho_i = 1 / (|t_i| + sqrt(t_i^2 - 1)),
+// t_i = (lam_i - c) / e; m_min for converged vectors, m_max inside the damped interval.
+cudaError_t vector_degrees(cudaStream_t s, int k, const double* lam, const double* res, double a, double b,
+                           double tol, int m_min, int m_max, int* deg);
