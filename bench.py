@@ -1,0 +1,367 @@
+"""Benchmark: ChFSI eigenproblems/s at residual <= 1e-10 on a correlated sequence of dense
+complex Hermitian generalized eigenproblems (n = 2000, 20 SCF steps, nev = 200, nex = 40,
+degree 20; S fixed, each solve seeded with the previous Ritz block).
+
+One benchmark step = one whole sequence (20 eigenproblems: Cholesky of S once, then per
+problem the transform, Lanczos and Algorithm 1 to convergence, back-transform).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed] [--impl ours|reference]
+
+Prints one JSON line.  For N > 1 (torchrun) every rank solves its own sequence (replicas,
+no collective on the data path); the value is all ranks' eigenproblems over the slowest
+rank's time.  --impl reference times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ChFSI eigenproblems/s at resid<=1e-10"
+UNIT = "eigenproblems/s"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, max clock, throttle reasons)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1305_5120_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, when it was taken
+    on the current kernel sources (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        if t.get("source_hash") != kernel_source_hash():
+            return None
+        return t["kernels"].get(kernel)
+    except Exception:
+        return None
+
+
+def make_inputs(w, seed):
+    from paper_1305_5120_gb300 import synth
+    seq = list(synth.sequence(w.n, w.n_low, w.high, w.steps, seed))
+    S = seq[0][1].S
+    Hs = [p.H for _, p in seq]
+    X0 = synth.start_block(w.n, w.nev + w.nex, seed)
+    return Hs, S, X0
+
+
+# ----------------------------------------------------------------------------------------
+def oracle_sample(w, seed=0):
+    """Bounded CPU sample of the workload with the FP64 oracle as it stands: Cholesky of S,
+    then for problem 1 the reduction to standard form, Lanczos and ONE outer iteration of
+    Algorithm 1 (degree-m filter of the whole block, QR, Rayleigh-Ritz, residuals).
+    Rate = problems / (t_chol + problems * (t_reduce + t_lanczos + t_iteration)): an upper
+    bound on the oracle's rate, since every problem needs at least one outer iteration."""
+    from oracle import chfsi as O2
+    from oracle import direct as O1
+    from paper_1305_5120_gb300 import synth
+    gen = synth.sequence(w.n, w.n_low, w.high, 2, seed)
+    _, p0 = next(gen)
+    _, p1 = next(gen)
+    k = w.nev + w.nex
+    t = time.perf_counter()
+    L = O1.cholesky(p0.S)
+    t_chol = time.perf_counter() - t
+    t = time.perf_counter()
+    Hs = O1.reduce_to_standard(p1.H, L)
+    t_red = time.perf_counter() - t
+    t = time.perf_counter()
+    v0 = O2.splitmix_complex_block(seed, w.n, 1, stream=0)[:, 0]
+    al, be = O2.lanczos(Hs, v0, 20)
+    b, a, a0 = O2.lanczos_bounds(al, be, w.n, k)
+    t_lz = time.perf_counter() - t
+    Y0 = synth.start_block(w.n, k, seed)
+    t = time.perf_counter()
+    Y = O2.chebyshev_filter(Hs, Y0, w.degree, a, b, a0)
+    Q = O2.orthonormalize(None, Y)
+    lam, Yr, Z = O2.rayleigh_ritz(Hs, Q)
+    O2.residual_norms(Z, Yr, lam)
+    t_it = time.perf_counter() - t
+    P = w.steps
+    rate = P / (t_chol + P * (t_red + t_lz + t_it))
+    return rate, {"t_cholesky_s": t_chol, "t_reduce_s": t_red, "t_lanczos_s": t_lz, "t_iteration_s": t_it}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    from paper_1305_5120_gb300 import synth
+    w = synth.SEQ_N2000
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_sample(w)
+    rates, parts = [], None
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r, parts = oracle_sample(w)
+        rates.append(r)
+    wall = time.perf_counter() - t0
+    value = float(np.mean(rates))
+    cores = os.cpu_count()
+    sample = ("oracle O2 (numpy/C, FP64): Cholesky + reduction + Lanczos + one outer iteration on problem 1 "
+              f"of the n={w.n} sequence; rate = 20/(t_chol + 20*(t_red+t_lz+t_iter)), an upper bound")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(w, "fp64"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "parts": parts},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(w, precision):
+    return {"workload": w.name, "n": w.n, "nev": w.nev, "nex": w.nex, "problems_per_step": w.steps,
+            "degree": w.degree, "tol": w.tol, "precision": precision, "seed": w.seed,
+            "l2": "inputs larger than L2: 20 distinct H (1.3 GB) resident, each read by its own solve",
+            "parallelism": "replicas (one sequence per GPU, no collectives)"}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1305_5120_gb300 import chfsi, synth
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    w = synth.SEQ_N2000
+    prec = chfsi.CHFSI_PREC_MIXED if args.precision == "mixed" else chfsi.CHFSI_PREC_FP64
+    seed = w.seed + rank
+    Hs, S, X0 = make_inputs(w, seed)
+    n, nev, nex, k = w.n, w.nev, w.nex, w.nev + w.nex
+    dev = [chfsi.colmajor(H) for H in Hs]
+    S_d = chfsi.colmajor(S)
+    X0_d = chfsi.colmajor(X0)
+    evals = torch.empty(nev, dtype=torch.float64, device="cuda")
+    X = torch.empty((nev, n), dtype=torch.complex128, device="cuda")
+    ctx = chfsi.Context(device=local, precision=prec)
+    stream = ctx.stream
+
+    def one_sequence(Hlist, Sd, infos):
+        st, *_ , info = ctx.solve(Hlist[0], Sd, n, nev, nex, X0_d, w.tol, w.degree, evals, X)
+        infos.append((st, info))
+        for l in range(1, len(Hlist)):
+            st, *_ , info = ctx.next_in_sequence(Hlist[l], None, evals, X)
+            infos.append((st, info))
+
+    for _ in range(args.warmup):
+        one_sequence(dev, S_d, [])
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = chfsi.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    infos = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        one_sequence(dev, S_d, infos)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = chfsi.kernel_launches() - launches0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    bad = [st for st, _ in infos if st != 0]
+    # accuracy of the last problem, checked in FP64 on the host
+    lam = evals.cpu().numpy()
+    Xh = chfsi.to_numpy(X)
+    HX = Hs[-1] @ Xh
+    resid = float((np.linalg.norm(HX - (S @ Xh) * lam[None, :], axis=0) / np.linalg.norm(HX, axis=0)).max())
+    t_max = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms = float(t_max.item())
+    problems = args.steps * w.steps * world
+    value = problems / (ms / 1000.0)
+
+    # per-kernel accounting from the library's stream-ordered CUDA events
+    f_lowp_ms = sum(i.ms_filter_lowp for _, i in infos)
+    f_all_ms = sum(i.ms_stage[2] for _, i in infos)
+    f64_ms = f_all_ms - f_lowp_ms
+    cs_all = sum(i.filter_col_steps for _, i in infos)
+    cs_low = sum(i.filter_col_steps_lowp for _, i in infos)
+    flop_per_colstep = 8.0 * n * n
+    pk, pk_kind = peaks()
+    fp64_peak = pk["bf16_tflops"] * (1.25 / 2250.0)
+    kernels = {}
+    if f64_ms > 0:
+        ach = flop_per_colstep * (cs_all - cs_low) / (f64_ms / 1000.0) / 1e12
+        kernels["zgemm_kernel (FP64 filter)"] = {"bound": "tensor", "achieved": ach, "peak": fp64_peak,
+                                                 "unit": "TFLOP/s", "frac": ach / fp64_peak, "ms": f64_ms,
+                                                 "peak_note": f"FP64 = {pk_kind} bf16 burst x 1.25/2250 (nominal ratio)"}
+    if f_lowp_ms > 0:
+        ach = 6.0 * flop_per_colstep * cs_low / (f_lowp_ms / 1000.0) / 1e12
+        kernels["tc_filter_kernel (split-BF16)"] = {"bound": "tensor", "achieved": ach,
+                                                    "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                                                    "frac": ach / pk["bf16_tflops_sustained"], "ms": f_lowp_ms,
+                                                    "peak_note": f"{pk_kind} bf16 sustained; 6 slice products"}
+    dom = max(kernels, key=lambda k_: kernels[k_]["ms"]) if kernels else None
+    roof = dict(kernels[dom]) if dom else None
+    if roof:
+        roof["kernel"] = dom
+        roof["traffic"] = traffic_for(dom.split()[0])
+        roof.pop("ms")
+    stages = np.sum([list(i.ms_stage) for _, i in infos], axis=0).tolist()
+
+    # end to end through the public API with host buffers: per problem H2D of H_l (pinned),
+    # solve, D2H of eigenvalues and eigenvectors; S uploaded once per sequence
+    e2e = None
+    if not args.no_e2e:
+        Hh = [torch.from_numpy(np.ascontiguousarray(H.T)).pin_memory() for H in Hs]
+        Sh = torch.from_numpy(np.ascontiguousarray(S.T)).pin_memory()
+        Hd = torch.empty_like(dev[0])
+        Sd2 = torch.empty_like(S_d)
+        ev_h = torch.empty(nev, dtype=torch.float64).pin_memory()
+        X_h = torch.empty((nev, n), dtype=torch.complex128).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(args.steps):
+            Sd2.copy_(Sh, non_blocking=True)
+            for l in range(w.steps):
+                Hd.copy_(Hh[l], non_blocking=True)
+                if l == 0:
+                    ctx.solve(Hd, Sd2, n, nev, nex, X0_d, w.tol, w.degree, evals, X)
+                else:
+                    ctx.next_in_sequence(Hd, None, evals, X)
+                ev_h.copy_(evals, non_blocking=True)
+                X_h.copy_(X, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = e0.elapsed_time(e1)
+        h2d = (Hh[0].numel() * 16) * w.steps + Sh.numel() * 16
+        d2h = (nev * 8 + nev * n * 16) * w.steps
+        e2e = {"value": problems / (ms_e2e / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "wall_s": time.perf_counter() - t0}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, parts = oracle_sample(w)
+        cpu = {"value": r, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "Cholesky + reduction + Lanczos + one outer iteration of problem 1 (FP64 oracle, "
+                         "numpy BLAS threads = all cores); rate = 20/(t_chol + 20*(t_red+t_lz+t_iter)), "
+                         "an upper bound", "parts": parts}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64" if prec == chfsi.CHFSI_PREC_FP64 else "bf16x6+f64",
+                "data": "synthetic", "config": config_dict(w, args.precision), "roofline": roof,
+                "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+                "stages_ms": dict(zip(["reduce", "lanczos", "filter", "qr", "rayleigh_ritz", "residual_lock",
+                                       "back_transform", "total"], stages)),
+                "iterations": int(sum(i.iterations for _, i in infos)), "failed_solves": len(bad),
+                "last_problem_max_resid": resid,
+                "filter_col_steps": int(cs_all), "filter_col_steps_lowp": int(cs_low)}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0 if not bad else 1
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -45,7 +45,7 @@ typedef enum {
 enum {
   CHFSI_PREC_FP64 = 0,     /* every filter product in FP64 (DFMA) */
   CHFSI_PREC_MIXED = 1     /* filter products on the tensor cores in split-BF16 (FP32-equivalent)
-                              while residuals are large, then FP64; Cholesky, transform, QR,
+                              while residuals are large (see mixed_switch), then FP64; Cholesky, transform, QR,
                               Rayleigh-Ritz, residuals and Lanczos always FP64 */
 };
 
@@ -57,8 +57,9 @@ typedef struct {
   int max_iter;            /* outer iterations of Algorithm 1 (default 50) */
   int lanczos_steps;       /* Lanczos steps of the spectral bound (default 20, <= 256) */
   int precision;           /* CHFSI_PREC_* (default FP64) */
-  double mixed_switch;     /* MIXED: low-precision filter while the smallest active relative
-                              residual exceeds this (default 1e-5) */
+  double mixed_switch;     /* MIXED: tensor-core filter while the smallest active absolute residual
+                              exceeds mixed_switch * max(|a0|, |b|) and still drops at least 10x
+                              per pass (default 1e-6) */
   unsigned long long seed; /* SplitMix64 seed of the Lanczos start vectors and of the random
                               start block (default 0) */
 } chfsi_params;
@@ -74,6 +75,7 @@ typedef struct {
   double ms_stage[8];      /* device time per stage: 0 reduce (Cholesky, inverse, H'), 1 Lanczos,
                               2 filter, 3 QR, 4 Rayleigh-Ritz, 5 residual+locking,
                               6 back-transform, 7 whole call */
+  double ms_filter_lowp;   /* part of ms_stage[2] spent in tensor-core (low-precision) filter passes */
 } chfsi_info;
 
 /* Fills *p with the defaults listed above. */
@@ -112,6 +114,10 @@ chfsi_status chfsi_next_in_sequence(chfsi_ctx *c, const void *H_next, const void
 
 void chfsi_destroy(chfsi_ctx *c);
 const char *chfsi_status_string(chfsi_status s);
+
+/* Number of CUDA kernels this library has launched in this process (all contexts).  A
+ * diagnostic for benchmarks; the paper has no counterpart. */
+unsigned long long chfsi_kernel_launches(void);
 
 /* ---- Stage entry points (each step of the solve on its own; device pointers) -------- */
 

@@ -39,12 +39,14 @@ class Params(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("locked", ctypes.c_int), ("filter_col_steps", ctypes.c_longlong),
                 ("filter_col_steps_lowp", ctypes.c_longlong), ("max_resid", ctypes.c_double),
-                ("kappa_L", ctypes.c_double), ("bounds", ctypes.c_double * 3), ("ms_stage", ctypes.c_double * 8)]
+                ("kappa_L", ctypes.c_double), ("bounds", ctypes.c_double * 3), ("ms_stage", ctypes.c_double * 8),
+                ("ms_filter_lowp", ctypes.c_double)]
 
     def as_dict(self):
         return {"iterations": self.iterations, "locked": self.locked, "filter_col_steps": self.filter_col_steps,
                 "filter_col_steps_lowp": self.filter_col_steps_lowp, "max_resid": self.max_resid,
-                "kappa_L": self.kappa_L, "bounds": list(self.bounds), "ms_stage": list(self.ms_stage)}
+                "kappa_L": self.kappa_L, "bounds": list(self.bounds), "ms_stage": list(self.ms_stage),
+                "ms_filter_lowp": self.ms_filter_lowp}
 
 
 _lib = None
@@ -59,6 +61,7 @@ _SIGS = {
     "chfsi_next_in_sequence": [_P, _P, _P, _P, _P, ctypes.POINTER(Info)],
     "chfsi_destroy": [_P],
     "chfsi_status_string": [_I],
+    "chfsi_kernel_launches": [],
     "chfsi_cholesky": [_P, _I, _P, _P],
     "chfsi_reduce": [_P, _I, _P, _P, _P],
     "chfsi_lanczos": [_P, _I, _P, _I, _I, _P, _P, _P, _P],
@@ -71,6 +74,10 @@ _SIGS = {
     "chfsi_degrees": [_P, _I, _P, _P, _D, _D, _D, _I, _I, _P],
     "chfsi_back_transform": [_P, _I, _I, _P, _P, _P],
 }
+
+
+def kernel_launches() -> int:
+    return int(load().chfsi_kernel_launches())
 
 
 def exported_names():
@@ -93,7 +100,8 @@ def load(build_if_missing: bool = True):
     for name, args in _SIGS.items():
         f = getattr(lib, name)
         f.argtypes = args
-        f.restype = ctypes.c_char_p if name == "chfsi_status_string" else (None if name == "chfsi_destroy" else _I)
+        f.restype = {"chfsi_status_string": ctypes.c_char_p, "chfsi_destroy": None,
+                     "chfsi_kernel_launches": ctypes.c_ulonglong}.get(name, _I)
     _lib = lib
     return lib
 

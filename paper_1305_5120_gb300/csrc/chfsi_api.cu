@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -15,6 +16,13 @@
 #include "filter_tc.cuh"
 #include "jacobi.cuh"
 #include "lanczos.cuh"
+
+static unsigned long long g_launches = 0;   // host-side count; launches are issued from host threads
+static std::mutex g_launch_mu;
+void count_launch(unsigned long long n) {
+  std::lock_guard<std::mutex> lk(g_launch_mu);
+  g_launches += n;
+}
 
 chfsi_status chfsi_cuda_error(cudaError_t e, const char* what) {
   if (e == cudaErrorMemoryAllocation) return CHFSI_ERR_OOM;
@@ -318,7 +326,7 @@ chfsi_status run_filter(chfsi_ctx* c, int n, int k, const cplx* Hs, cplx* Y, con
     TRY(buf(c, "deg_dev", k, &d_deg));
     CU(cudaMemcpyAsync(d_deg, deg, sizeof(int) * k, cudaMemcpyHostToDevice, c->stream));
     dim3 grid((unsigned)std::min((n + 255) / 256, 32), (unsigned)k);
-    copy_odd_columns_kernel<<<grid, 256, 0, c->stream>>>(n, d_deg, Y2, Y);
+    copy_odd_columns_kernel<<<grid, 256, 0, c->stream>>>(n, d_deg, Y2, Y); count_launch();
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(c->stream));   // deg is a caller-owned host array
   }
@@ -344,7 +352,7 @@ chfsi_status cholqr_pass(chfsi_ctx* c, int n, int k, cplx* Y, bool shifted, bool
   TRY(gemm(c, gemm_args(k, k, n, OP_C, Y, n, OP_N, Y, n, G, k, ONE, ZERO)));
   CU(hermitize(c->stream, k, G, k));
   if (shifted) {
-    add_shift_kernel<<<1, 256, 0, c->stream>>>(k, n, G);
+    add_shift_kernel<<<1, 256, 0, c->stream>>>(k, n, G); count_launch();
     CU(cudaGetLastError());
   }
   CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
@@ -416,10 +424,10 @@ struct Timer {
   chfsi_ctx* c;
   double* acc;
   int idx = 0;
-  int stage[8];
+  int stage[16];
   void start() { idx = 0; }
   void mark(int s) {
-    if (idx < 15) {
+    if (idx < 10) {   // events 0..9; 11..15 are used by solve_common
       cudaEventRecord(c->ev[idx], c->stream);
       stage[idx] = s;
       ++idx;
@@ -427,7 +435,7 @@ struct Timer {
   }
   // after a sync: add elapsed time between consecutive marks to the stage of the later mark
   void flush() {
-    for (int i = 1; i < idx && i < 8; ++i) {
+    for (int i = 1; i < idx; ++i) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, c->ev[i - 1], c->ev[i]) == cudaSuccess) acc[stage[i]] += ms;
     }
@@ -460,11 +468,15 @@ chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, 
   std::vector<double> lam_locked;
   std::vector<int> deg(k, c->degree);
   int nl = 0, ka = k, it = 0;
-  double ms[8] = {0};
+  double ms[9] = {0};   // index 8: low-precision filter passes
   Timer tm{c, ms};
   chfsi_status status = CHFSI_OK;
   long long colsteps = 0, colsteps_lowp = 0;
   double min_res = INFINITY, max_res_locked = 0.0;
+  double min_res_abs = INFINITY, prev_min_res_abs = INFINITY;
+  bool last_lowp = false;
+  const double hnorm = std::max(fabs(a0), fabs(b));
+  double* h_resabs = c->h_d + 3 * k;
   std::vector<double> lam_active;
   for (;;) {
     ++it;
@@ -472,13 +484,20 @@ chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, 
     tm.start();
     tm.mark(0);
     // line 3: filter (mixed precision while every active residual is above the switch)
+    // precision ladder: the tensor-core filter while the smallest active absolute residual is
+    // above mixed_switch * ||H'|| and the previous low-precision pass still made progress
+    // (an FP32-equivalent filter stalls near 2^-24 ||H'||)
     int prec = CHFSI_PREC_FP64;
-    if (c->prm.precision == CHFSI_PREC_MIXED && min_res > c->prm.mixed_switch) prec = CHFSI_PREC_MIXED;
+    if (c->prm.precision == CHFSI_PREC_MIXED && min_res_abs > c->prm.mixed_switch * hnorm &&
+        !(last_lowp && min_res_abs > 0.1 * prev_min_res_abs))
+      prec = CHFSI_PREC_MIXED;
+    last_lowp = prec == CHFSI_PREC_MIXED;
+    prev_min_res_abs = min_res_abs;
     long long cs = 0;
     TRY(run_filter(c, n, ka, Hs, Ya, deg.data(), a, b, a0, prec, &cs));
     colsteps += cs;
     if (prec == CHFSI_PREC_MIXED) colsteps_lowp += cs;
-    tm.mark(2);
+    tm.mark(prec == CHFSI_PREC_MIXED ? 8 : 2);
     // line 4: QR against the locked vectors
     TRY(orthonormalize(c, n, nl, Y, ka, Ya));
     tm.mark(3);
@@ -489,6 +508,7 @@ chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, 
     CU(residual_norms(c->stream, n, ka, Z, n, Ya, n, lam, res, resabs));
     CU(cudaMemcpyAsync(h_lam, lam, sizeof(double) * ka, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaMemcpyAsync(h_res, res, sizeof(double) * ka, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(h_resabs, resabs, sizeof(double) * ka, cudaMemcpyDeviceToHost, c->stream));
     int h_err = 0;
     CU(cudaMemcpyAsync(&h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     tm.mark(5);
@@ -507,7 +527,11 @@ chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, 
     a = h_lam[ka - 1];
     a0 = std::min(a0, h_lam[0]);
     min_res = INFINITY;
-    for (int i : rest) min_res = std::min(min_res, h_res[i]);
+    min_res_abs = INFINITY;
+    for (int i : rest) {
+      min_res = std::min(min_res, h_res[i]);
+      min_res_abs = std::min(min_res_abs, h_resabs[i]);
+    }
     for (int i : lockv) max_res_locked = std::max(max_res_locked, h_res[i]);
     if (c->prm.per_vector_degree && !rest.empty()) {
       // a10: degrees for the next filter, from the updated bounds (device kernel)
@@ -587,6 +611,8 @@ chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, 
     info->bounds[1] = b;
     info->bounds[2] = a0;
     for (int s = 0; s < 7; ++s) info->ms_stage[s] += ms[s];
+    info->ms_stage[2] += ms[8];
+    info->ms_filter_lowp += ms[8];
   }
   return status;
 }
@@ -683,6 +709,11 @@ chfsi_status solve_common(chfsi_ctx* c, const cplx* H, const cplx* S, const cplx
 // ---------------------------------------------------------------------------------------
 extern "C" {
 
+unsigned long long chfsi_kernel_launches(void) {
+  std::lock_guard<std::mutex> lk(g_launch_mu);
+  return g_launches;
+}
+
 const char* chfsi_status_string(chfsi_status s) {
   switch (s) {
     case CHFSI_OK: return "ok";
@@ -708,7 +739,7 @@ chfsi_status chfsi_default_params(chfsi_params* p) {
   p->max_iter = 50;
   p->lanczos_steps = 20;
   p->precision = CHFSI_PREC_FP64;
-  p->mixed_switch = 1e-5;
+  p->mixed_switch = 1e-6;
   p->seed = 0;
   return CHFSI_OK;
 }

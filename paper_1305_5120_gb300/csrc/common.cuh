@@ -113,3 +113,6 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier b, unsigned int nblocks
   } while (0)
 
 chfsi_status chfsi_cuda_error(cudaError_t e, const char* what);
+
+// Number of kernels this library has launched (process-wide); chfsi_kernel_launches() reads it.
+void count_launch(unsigned long long n = 1);

@@ -209,11 +209,11 @@ cudaError_t chol_lower(cudaStream_t s, int n, cplx* A, long lda, int* err) {
       cudaError_t e = zgemm_launch(g, s);
       if (e != cudaSuccess) return e;
     }
-    potrf_diag_kernel<<<1, 256, 0, s>>>(A, lda, j0, jb, err);
+    potrf_diag_kernel<<<1, 256, 0, s>>>(A, lda, j0, jb, err); count_launch();
     const int rows = n - j0 - jb;
-    if (rows > 0) potrf_panel_kernel<<<(rows + 127) / 128, 128, 0, s>>>(A, lda, n, j0, jb, err);
+    if (rows > 0) potrf_panel_kernel<<<(rows + 127) / 128, 128, 0, s>>>(A, lda, n, j0, jb, err); count_launch();
   }
-  zero_upper_kernel<<<grid_for((long)n * n), 256, 0, s>>>(n, A, lda);
+  zero_upper_kernel<<<grid_for((long)n * n), 256, 0, s>>>(n, A, lda); count_launch();
   return cudaGetLastError();
 }
 
@@ -236,13 +236,13 @@ cudaError_t trtri_lower(cudaStream_t s, int n, const cplx* L, long ldl, cplx* X,
       if (e != cudaSuccess) return e;
     }
     const int cols = i0 + jb;
-    trtri_rows_kernel<<<(cols + 127) / 128, 128, 0, s>>>(L, ldl, X, ldx, i0, jb, err);
+    trtri_rows_kernel<<<(cols + 127) / 128, 128, 0, s>>>(L, ldl, X, ldx, i0, jb, err); count_launch();
   }
   return cudaGetLastError();
 }
 
 cudaError_t hermitize(cudaStream_t s, int n, cplx* A, long lda) {
-  hermitize_kernel<<<grid_for((long)n * n), 256, 0, s>>>(n, A, lda);
+  hermitize_kernel<<<grid_for((long)n * n), 256, 0, s>>>(n, A, lda); count_launch();
   return cudaGetLastError();
 }
 
@@ -250,31 +250,31 @@ cudaError_t gather_columns(cudaStream_t s, int n, int cnt, const int* perm, cons
                            long ldd) {
   if (cnt <= 0) return cudaSuccess;
   dim3 grid((unsigned)min((n + 255) / 256, 64), (unsigned)cnt);
-  gather_columns_kernel<<<grid, 256, 0, s>>>(n, cnt, perm, src, lds, dst, ldd);
+  gather_columns_kernel<<<grid, 256, 0, s>>>(n, cnt, perm, src, lds, dst, ldd); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t gather_values(cudaStream_t s, int cnt, const int* perm, const double* src, double* dst) {
   if (cnt <= 0) return cudaSuccess;
-  gather_values_kernel<<<(cnt + 255) / 256, 256, 0, s>>>(cnt, perm, src, dst);
+  gather_values_kernel<<<(cnt + 255) / 256, 256, 0, s>>>(cnt, perm, src, dst); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t residual_norms(cudaStream_t s, int n, int k, const cplx* Z, long ldz, const cplx* Y, long ldy,
                            const double* lam, double* res, double* resabs) {
   if (k <= 0) return cudaSuccess;
-  residual_kernel<<<k, 256, 0, s>>>(n, Z, ldz, Y, ldy, lam, res, resabs);
+  residual_kernel<<<k, 256, 0, s>>>(n, Z, ldz, Y, ldy, lam, res, resabs); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t splitmix_block(cudaStream_t s, int n, int k, unsigned long long seed, unsigned long long stream,
                            cplx* Y, long ldy) {
-  splitmix_block_kernel<<<grid_for((long)n * k), 256, 0, s>>>(n, k, seed, stream << 40, Y, ldy);
+  splitmix_block_kernel<<<grid_for((long)n * k), 256, 0, s>>>(n, k, seed, stream << 40, Y, ldy); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t copy_block(cudaStream_t s, int n, int k, const cplx* src, long lds, cplx* dst, long ldd) {
   if (n <= 0 || k <= 0) return cudaSuccess;
-  copy_block_kernel<<<grid_for((long)n * k), 256, 0, s>>>(n, k, src, lds, dst, ldd);
+  copy_block_kernel<<<grid_for((long)n * k), 256, 0, s>>>(n, k, src, lds, dst, ldd); count_launch();
   return cudaGetLastError();
 }

@@ -1,8 +1,435 @@
+// Chebyshev filter step on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// One step of the scaled three-term recurrence (Eq. (3term) with shift and scale, Section 3)
+//     Y_{j+1} = fa * H' Y_j + fb * Y_j + fg * Y_{j-1}
+// is one launch.  The complex product H' Y_j runs as a real GEMM through the embedding
+//     [Re H' | Im H'] (K interleaved)  x  [[Re Y, Im Y], [-Im Y, Re Y]] (columns interleaved),
+// so M = n, N = 2k, K = 2n.  Each FP64 operand is split into three BF16 slices
+// (x = s0 + s1 + s2 + O(2^-24 |x|)) and the six slice products with s + t <= 2 accumulate in
+// one FP32 TMEM accumulator: an FP32-equivalent product on the BF16 tensor pipe.
+//
+// Per CTA (one 128 x BN output tile): warp 0 issues TMA loads of the A and B slice tiles
+// (128-byte swizzle) into a 3-stage shared-memory ring; warp 1 owns the TMEM accumulator and
+// issues tcgen05.mma; warps 2-5 drain TMEM, apply the recurrence in FP64 against Y_j and
+// Y_{j-1}, store Y_{j+1} (FP64) and write its BF16 slices in the B layout of the next step.
+// Every mbarrier wait is bounded: on timeout the kernel records DEV_ERR_TIMEOUT and leaves.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
 #include "filter_tc.cuh"
-struct TcFilter { int dummy; };
+
+void count_launch(unsigned long long n);
+
+namespace {
+
+constexpr int BM = 128;          // tcgen05 M (cta_group::1)
+constexpr int BN = 64;           // real output columns per tile (32 complex)
+constexpr int BK = 64;           // bf16 per 128-byte swizzle row
+constexpr int STAGES = 3;
+constexpr int NSLICE = 3;
+constexpr int A_TILE = BM * BK * 2;            // bytes per A slice tile (16 KB)
+constexpr int B_TILE = BN * BK * 2;            // bytes per B slice tile (8 KB)
+constexpr int STAGE_BYTES = NSLICE * (A_TILE + B_TILE);
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int TMEM_COLS = BN;    // fp32 accumulator columns
+constexpr int NTHREADS = 192;
+constexpr long WAIT_LIMIT = 1L << 24;
+
+static_assert(STAGE_BYTES % 1024 == 0, "stage alignment");
+
+struct StepArgs {
+  int n, mtiles;                 // rows, row tiles
+  int ncols;                     // complex columns this step (cnt[j])
+  int kblocks;                   // K_pad / BK
+  long ldb_next;                 // K_pad (elements per B row)
+  long nslice_rows_b;            // N_pad (rows per B slice)
+  const cplx* Ycur;              // n x ncols, ld n
+  cplx* Yout;                    // in: Y_{j-1} (if fg != 0), out: Y_{j+1}
+  __nv_bfloat16* Bnext;          // next step's B slices (NULL on the last step)
+  double fa, fb, fg;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; false (and the error word set) when the limit ran out or another role failed
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+  for (long i = 0; i < WAIT_LIMIT; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 255) == 255 && *(volatile int*)err != DEV_OK) return false;
+  }
+  atomicExch(err, DEV_ERR_TIMEOUT);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          dst),
+      "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major operand, 128-byte swizzle, 8-row atoms 1024 B apart
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);           // start address
+  d |= (uint64_t)1 << 16;                            // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;                  // stride byte offset
+  d |= (uint64_t)1 << 46;                            // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;                            // SWIZZLE_128B
+  return d;
+}
+
+// instruction descriptor: kind::f16, A/B bf16, D f32, both K-major, M = 128, N = BN
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// three-way BF16 split: x ~= s0 + s1 + s2 (each rounded to nearest)
+__device__ __forceinline__ void split3(double x, __nv_bfloat16& s0, __nv_bfloat16& s1, __nv_bfloat16& s2) {
+  s0 = __double2bfloat16(x);
+  double r = x - (double)__bfloat162float(s0);
+  s1 = __double2bfloat16(r);
+  r -= (double)__bfloat162float(s1);
+  s2 = __double2bfloat16(r);
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    tc_filter_step_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                          StepArgs g) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* base_ptr = smem_raw + (base - raw);
+  const uint32_t bars = base + STAGES * STAGE_BYTES;          // full[S], empty[S], accum
+  uint64_t* bar_ptr = (uint64_t*)(base_ptr + STAGES * STAGE_BYTES);
+  uint32_t* tmem_slot = (uint32_t*)(bar_ptr + 2 * STAGES + 1);
+  auto full = [&](int s) { return bars + 8u * s; };
+  auto empty = [&](int s) { return bars + 8u * (STAGES + s); };
+  const uint32_t accum = bars + 8u * (2 * STAGES);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM;
+  const int n0 = blockIdx.y * BN;   // real column offset
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(accum, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *(volatile uint32_t*)tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: A slice s at rows s*mtiles*BM + m0, B slice t at rows t*N_pad + n0
+      for (int kb = 0; kb < g.kblocks; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (!mbar_wait(empty(s), ph ^ 1, g.err)) break;
+        mbar_expect_tx(full(s), STAGE_BYTES);
+        const uint32_t st = base + s * STAGE_BYTES;
+        for (int q = 0; q < NSLICE; ++q)
+          tma_load_2d(st + q * A_TILE, &tmA, full(s), kb * BK, q * g.mtiles * BM + m0);
+        for (int q = 0; q < NSLICE; ++q)
+          tma_load_2d(st + NSLICE * A_TILE + q * B_TILE, &tmB, full(s), kb * BK, (int)(q * g.nslice_rows_b) + n0);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer: six slice products per 16-wide K step into one accumulator
+      const int prod_a[6] = {0, 0, 1, 0, 1, 2};
+      const int prod_b[6] = {0, 1, 0, 2, 1, 0};
+      bool ok = true;
+      for (int kb = 0; kb < g.kblocks && ok; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (!mbar_wait(full(s), ph, g.err)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st = base + s * STAGE_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+#pragma unroll
+          for (int p = 0; p < 6; ++p) {
+            const uint64_t da = umma_desc(st + prod_a[p] * A_TILE + kk * 32);
+            const uint64_t db = umma_desc(st + NSLICE * A_TILE + prod_b[p] * B_TILE + kk * 32);
+            umma_bf16(tmem, da, db, (kb | kk | p) != 0);
+          }
+        }
+        umma_commit(empty(s));   // frees the stage once these MMAs have read it
+      }
+      umma_commit(accum);        // accumulator complete (or abandoned on error)
+    }
+  } else {
+    // epilogue: warps 2..5 -> TMEM lane quarter (warp % 4)
+    const int q = warp & 3;
+    const int row = m0 + q * 32 + lane;
+    bool ok = mbar_wait(accum, 0, g.err);
+    ok = __all_sync(0xffffffffu, ok && *(volatile int*)g.err == DEV_OK);   // warp-uniform
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      float acc[BN];
+#pragma unroll
+      for (int c = 0; c < BN; c += 16) tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + c, acc + c);
+      if (row < g.n) {
+#pragma unroll 4
+        for (int jj = 0; jj < BN / 2; ++jj) {
+          const int j = n0 / 2 + jj;     // complex column
+          if (j >= g.ncols) break;
+          const long e = (long)j * g.n + row;
+          const cplx y = g.Ycur[e];
+          cplx o = cmk(g.fa * (double)acc[2 * jj] + g.fb * y.x, g.fa * (double)acc[2 * jj + 1] + g.fb * y.y);
+          if (g.fg != 0.0) {
+            const cplx p = g.Yout[e];
+            o.x += g.fg * p.x;
+            o.y += g.fg * p.y;
+          }
+          g.Yout[e] = o;
+          if (g.Bnext) {
+            __nv_bfloat16 xr[3], xi[3];
+            split3(o.x, xr[0], xr[1], xr[2]);
+            split3(o.y, xi[0], xi[1], xi[2]);
+#pragma unroll
+            for (int t = 0; t < NSLICE; ++t) {
+              __nv_bfloat16* rowRe = g.Bnext + (t * g.nslice_rows_b + 2L * j) * g.ldb_next;
+              __nv_bfloat16* rowIm = rowRe + g.ldb_next;
+              __nv_bfloat162 v0, v1;
+              v0.x = xr[t]; v0.y = __hneg(xi[t]);   // row 2j:   ( Re y, -Im y)
+              v1.x = xi[t]; v1.y = xr[t];           // row 2j+1: ( Im y,  Re y)
+              *(__nv_bfloat162*)(rowRe + 2L * row) = v0;
+              *(__nv_bfloat162*)(rowIm + 2L * row) = v1;
+            }
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (*(volatile int*)g.err != DEV_OK) __nanosleep(200000);   // let abandoned copies land
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+}
+
+// H' (column-major, Hermitian) -> A slices: A_s[r][2c] = s_s(Re H'[r,c]), A_s[r][2c+1] = s_s(Im H'[r,c]),
+// read through the Hermitian symmetry (row r of H' = conj of column r, contiguous).  Padding zero.
+__global__ void slice_H_kernel(int n, long kpad, long mpad, const cplx* __restrict__ H, __nv_bfloat16* __restrict__ A) {
+  const long r = blockIdx.y;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < kpad / 2; c += (long)gridDim.x * blockDim.x) {
+    __nv_bfloat16 re[3], im[3];
+    if (r < n && c < n) {
+      const cplx h = H[c + r * (long)n];   // H'[c, r] = conj(H'[r, c])
+      split3(h.x, re[0], re[1], re[2]);
+      split3(-h.y, im[0], im[1], im[2]);
+    } else {
+      for (int t = 0; t < 3; ++t) re[t] = im[t] = __float2bfloat16(0.f);
+    }
+    for (int t = 0; t < 3; ++t) {
+      __nv_bfloat162 v;
+      v.x = re[t];
+      v.y = im[t];
+      *(__nv_bfloat162*)(A + (t * mpad + r) * kpad + 2 * c) = v;
+    }
+  }
+}
+
+// Y (n x ncols, column-major) -> B slices (rows 2j, 2j+1 of each slice; K interleaved); padding zero.
+__global__ void slice_Y_kernel(int n, int ncols, long kpad, long npad, const cplx* __restrict__ Y,
+                               __nv_bfloat16* __restrict__ B) {
+  const long j = blockIdx.y;   // complex column, < npad / 2
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < kpad / 2; c += (long)gridDim.x * blockDim.x) {
+    __nv_bfloat16 xr[3], xi[3];
+    if (j < ncols && c < n) {
+      const cplx y = Y[c + j * (long)n];
+      split3(y.x, xr[0], xr[1], xr[2]);
+      split3(y.y, xi[0], xi[1], xi[2]);
+    } else {
+      for (int t = 0; t < 3; ++t) xr[t] = xi[t] = __float2bfloat16(0.f);
+    }
+    for (int t = 0; t < 3; ++t) {
+      __nv_bfloat16* rowRe = B + (t * npad + 2 * j) * kpad;
+      __nv_bfloat162 v0, v1;
+      v0.x = xr[t]; v0.y = __hneg(xi[t]);
+      v1.x = xi[t]; v1.y = xr[t];
+      *(__nv_bfloat162*)(rowRe + 2 * c) = v0;
+      *(__nv_bfloat162*)(rowRe + kpad + 2 * c) = v1;
+    }
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, void* ptr, long rows, long cols, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+long round_up(long x, long m) { return (x + m - 1) / m * m; }
+}  // namespace
+
+struct TcFilter {
+  int n = 0, k = 0;
+  long kpad = 0, mpad = 0, npad = 0;
+  __nv_bfloat16* A = nullptr;
+  __nv_bfloat16* B[2] = {nullptr, nullptr};
+  int* err = nullptr;
+  CUtensorMap mapA, mapB[2];
+  bool attr = false;
+};
+
 TcFilter* tc_filter_new() { return new TcFilter(); }
-void tc_filter_free(TcFilter* f) { delete f; }
-chfsi_status tc_filter_run(TcFilter*, cudaStream_t, int, const cplx*, cplx**, const int*, int, const double*,
-                           const double*, const double*) {
-  return CHFSI_ERR_ARG;
+
+void tc_filter_free(TcFilter* f) {
+  if (!f) return;
+  cudaFree(f->A);
+  cudaFree(f->B[0]);
+  cudaFree(f->B[1]);
+  cudaFree(f->err);
+  delete f;
+}
+
+static chfsi_status tc_ensure(TcFilter* f, int n, int k) {
+  if (n == f->n && k <= f->k && f->A) return CHFSI_OK;
+  cudaFree(f->A);
+  cudaFree(f->B[0]);
+  cudaFree(f->B[1]);
+  f->A = f->B[0] = f->B[1] = nullptr;
+  f->n = n;
+  f->k = k;
+  f->kpad = round_up(2L * n, BK);
+  f->mpad = round_up(n, BM);
+  f->npad = round_up(2L * k, BN);
+  CHFSI_CUDA_TRY(cudaMalloc(&f->A, sizeof(__nv_bfloat16) * 3 * f->mpad * f->kpad));
+  for (int i = 0; i < 2; ++i) {
+    CHFSI_CUDA_TRY(cudaMalloc(&f->B[i], sizeof(__nv_bfloat16) * 3 * f->npad * f->kpad));
+    CHFSI_CUDA_TRY(cudaMemset(f->B[i], 0, sizeof(__nv_bfloat16) * 3 * f->npad * f->kpad));
+  }
+  if (!f->err) CHFSI_CUDA_TRY(cudaMalloc(&f->err, sizeof(int)));
+  if (!make_map(&f->mapA, f->A, 3 * f->mpad, f->kpad, BM)) return CHFSI_ERR_CUDA;
+  for (int i = 0; i < 2; ++i)
+    if (!make_map(&f->mapB[i], f->B[i], 3 * f->npad, f->kpad, BN)) return CHFSI_ERR_CUDA;
+  if (!f->attr) {
+    CHFSI_CUDA_TRY(cudaFuncSetAttribute(tc_filter_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    f->attr = true;
+  }
+  return CHFSI_OK;
+}
+
+chfsi_status tc_filter_run(TcFilter* f, cudaStream_t s, int n, const cplx* H, cplx* bufs[2], const int* cnt, int mmax,
+                           const double* fa, const double* fb, const double* fg) {
+  if (mmax < 1 || cnt[1] < 1) return CHFSI_OK;
+  chfsi_status st = tc_ensure(f, n, cnt[1]);
+  if (st != CHFSI_OK) return st;
+  CHFSI_CUDA_TRY(cudaMemsetAsync(f->err, 0, sizeof(int), s));
+  {
+    dim3 grid((unsigned)((f->kpad / 2 + 255) / 256), (unsigned)f->mpad);
+    slice_H_kernel<<<grid, 256, 0, s>>>(n, f->kpad, f->mpad, H, f->A);
+    count_launch(1);
+    dim3 gy((unsigned)((f->kpad / 2 + 255) / 256), (unsigned)(f->npad / 2));
+    slice_Y_kernel<<<gy, 256, 0, s>>>(n, cnt[1], f->kpad, f->npad, bufs[0], f->B[0]);
+    count_launch(1);
+  }
+  for (int j = 1; j <= mmax; ++j) {
+    StepArgs g{};
+    g.n = n;
+    g.mtiles = (int)(f->mpad / BM);
+    g.ncols = cnt[j];
+    g.kblocks = (int)(f->kpad / BK);
+    g.ldb_next = f->kpad;
+    g.nslice_rows_b = f->npad;
+    g.Ycur = bufs[(j - 1) & 1];
+    g.Yout = bufs[j & 1];
+    g.Bnext = (j < mmax) ? f->B[j & 1] : nullptr;
+    g.fa = fa[j];
+    g.fb = fb[j];
+    g.fg = (j >= 2) ? fg[j] : 0.0;
+    g.err = f->err;
+    dim3 grid((unsigned)g.mtiles, (unsigned)((2L * cnt[j] + BN - 1) / BN));
+    tc_filter_step_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(f->mapA, f->mapB[(j - 1) & 1], g);
+    count_launch(1);
+    CHFSI_CUDA_TRY(cudaGetLastError());
+  }
+  int h = 0;
+  CHFSI_CUDA_TRY(cudaMemcpyAsync(&h, f->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CHFSI_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h == DEV_ERR_TIMEOUT) return CHFSI_ERR_TIMEOUT;
+  if (h != DEV_OK) return CHFSI_ERR_NUMERIC;
+  return CHFSI_OK;
 }

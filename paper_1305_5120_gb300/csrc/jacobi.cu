@@ -187,7 +187,7 @@ cudaError_t jacobi_eig(cudaStream_t s, int k, cplx* G, double* lam, cplx* W, voi
   g.max_sweeps = max_sweeps;
   cudaError_t e = cudaMemsetAsync(g.rot_count, 0, sizeof(int) * max_sweeps + sizeof(double) * 2 + sizeof(unsigned) * 4, s);
   if (e != cudaSuccess) return e;
-  fro_kernel<<<1, 1024, 0, s>>>(k, G, g.fro);
+  fro_kernel<<<1, 1024, 0, s>>>(k, G, g.fro); count_launch();
   if (kk < 2) {
     // 1 x 1: nothing to rotate
   }
@@ -195,7 +195,8 @@ cudaError_t jacobi_eig(cudaStream_t s, int k, cplx* G, double* lam, cplx* W, voi
   int blocks = coop_blocks((int)((work_items + 255) / 256));
   void* args[] = {&g};
   e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(blocks), dim3(256), args, 0, s);
+  count_launch();
   if (e != cudaSuccess) return e;
-  jacobi_sort_kernel<<<k < 1024 ? k : 1024, 128, 0, s>>>(k, G, (const cplx*)g.V, lam, W);
+  jacobi_sort_kernel<<<k < 1024 ? k : 1024, 128, 0, s>>>(k, G, (const cplx*)g.V, lam, W); count_launch();
   return cudaGetLastError();
 }

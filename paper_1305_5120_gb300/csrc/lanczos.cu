@@ -142,31 +142,31 @@ __global__ void vector_degrees_kernel(int k, const double* lam, const double* re
 
 cudaError_t herm_gemv(cudaStream_t s, int n, const cplx* H, long ldh, const cplx* v, cplx* w) {
   const long threads = 32L * n;
-  herm_gemv_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(n, H, ldh, v, w);
+  herm_gemv_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(n, H, ldh, v, w); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t normalize_vec(cudaStream_t s, int n, cplx* v) {
-  normalize_kernel<<<1, 1024, 0, s>>>(n, v);
+  normalize_kernel<<<1, 1024, 0, s>>>(n, v); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t lanczos_step(cudaStream_t s, int n, int j, cplx* v, cplx* v_prev, cplx* w, double* alpha,
                          double* beta) {
-  lanczos_step_kernel<<<1, 1024, 0, s>>>(n, j, v, v_prev, w, alpha, beta);
+  lanczos_step_kernel<<<1, 1024, 0, s>>>(n, j, v, v_prev, w, alpha, beta); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t lanczos_bounds(cudaStream_t s, int steps, int n, int k, const double* alpha, const double* beta,
                            double* out) {
   if (steps < 2 || steps > 256) return cudaErrorInvalidValue;
-  lanczos_bounds_kernel<<<1, 32, 0, s>>>(steps, n, k, alpha, beta, out);
+  lanczos_bounds_kernel<<<1, 32, 0, s>>>(steps, n, k, alpha, beta, out); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t vector_degrees(cudaStream_t s, int k, const double* lam, const double* res, double a, double b,
                            double tol, int m_min, int m_max, int* deg) {
   if (k <= 0) return cudaSuccess;
-  vector_degrees_kernel<<<(k + 127) / 128, 128, 0, s>>>(k, lam, res, a, b, tol, m_min, m_max, deg);
+  vector_degrees_kernel<<<(k + 127) / 128, 128, 0, s>>>(k, lam, res, a, b, tol, m_min, m_max, deg); count_launch();
   return cudaGetLastError();
 }

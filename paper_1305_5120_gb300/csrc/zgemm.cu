@@ -185,24 +185,21 @@ cudaError_t zgemm_launch(const GemmArgs& g0, cudaStream_t stream) {
   GemmArgs g = g0;
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
   if (g.splits < 1) g.splits = 1;
+  const long total = (long)g.M * g.N;
+  const unsigned rblocks = (unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
   if (g.K <= 0) {
-    // empty product: only the epilogue remains
-    g.splits = 1;
-    g.work = nullptr;
-  }
-  dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, g.splits);
-  if (g.K > 0) zgemm_kernel<<<grid, NT, 0, stream>>>(g);
-  else {
-    // K == 0: treat as a GEMM with zero product by launching the reduce with splits = 0
-    GemmArgs h = g;
-    h.splits = 0;
-    zgemm_splitk_reduce<<<(unsigned)(((long)g.M * g.N + 255) / 256 < 4096 ? ((long)g.M * g.N + 255) / 256 : 4096), 256, 0, stream>>>(h);
+    // empty product: only the epilogue remains (the reduce kernel with zero partials)
+    g.splits = 0;
+    zgemm_splitk_reduce<<<rblocks, 256, 0, stream>>>(g);
+    count_launch();
     return cudaGetLastError();
   }
+  dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, g.splits);
+  zgemm_kernel<<<grid, NT, 0, stream>>>(g);
+  count_launch();
   if (g.splits > 1) {
-    long total = (long)g.M * g.N;
-    unsigned blocks = (unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
-    zgemm_splitk_reduce<<<blocks, 256, 0, stream>>>(g);
+    zgemm_splitk_reduce<<<rblocks, 256, 0, stream>>>(g);
+    count_launch();
   }
   return cudaGetLastError();
 }

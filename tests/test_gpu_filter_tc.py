@@ -1,0 +1,76 @@
+"""The tensor-core (split-BF16, FP32-accumulate) Chebyshev filter against the oracle's FP64
+filter, element by element.
+
+Tolerance: each BF16 triple represents an FP64 entry to 2^-24 relative, and the FP32
+accumulation over K = 2n real terms adds about sqrt(K) * 2^-24 relative per product, i.e.
+<= 2e-6 for n <= 2000.  Errors injected at every one of the m recurrence steps survive
+(normalised) to the output, so the bound is m * 2e-6 relative to the largest entry: 1e-5 for
+m <= 2 and 1e-4 for m = 20 (tested with a factor-2 margin)."""
+import numpy as np
+import pytest
+
+from oracle import chfsi as O2
+from paper_1305_5120_gb300 import chfsi as lib
+from paper_1305_5120_gb300 import synth
+
+from gpu_util import rel_err, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch_cuda()
+    c = lib.Context(device=0)
+    yield c
+    c.close()
+
+
+def std_problem(n, seed, high=50.0):
+    lam = synth.prescribed_spectrum(n, max(4, n // 10), high, seed)
+    q = synth.haar_unitary(n, synth.rng_for(seed, 3))
+    return synth.hermitian_part((q * lam[None, :]) @ q.conj().T), lam
+
+
+def tol_for(m, n):
+    per_step = np.sqrt(2 * n) * 2.0 ** -24 * 2
+    return 2 * max(m, 1) * max(per_step, 1e-7) + 1e-6
+
+
+@pytest.mark.parametrize("n,k", [(128, 32), (200, 24), (333, 37), (512, 48), (130, 1), (1000, 121)])
+@pytest.mark.parametrize("m", [1, 2, 20])
+def test_filter_mixed_vs_oracle(ctx, n, k, m):
+    H, lam = std_problem(n, 51)
+    Y0 = synth.start_block(n, k, 51)
+    a, b, a0 = float(lam[min(n - 1, int(1.2 * k) + 2)]), float(lam[-1] * 1.05), float(lam[0] - 0.1)
+    Y = lib.colmajor(Y0)
+    ctx.filter(n, k, lib.colmajor(H), Y, m, a, b, a0, lib.CHFSI_PREC_MIXED)
+    ref = O2.chebyshev_filter(H, Y0, m, a, b, a0)
+    err = rel_err(lib.to_numpy(Y), ref)
+    assert err < tol_for(m, n), err
+
+
+def test_filter_mixed_per_vector_degree(ctx):
+    n, k = 300, 29
+    H, lam = std_problem(n, 52)
+    Y0 = synth.start_block(n, k, 52)
+    deg = sorted(np.random.default_rng(2).integers(3, 17, k).tolist(), reverse=True)
+    a, b, a0 = float(lam[40]), float(lam[-1] * 1.05), float(lam[0] - 0.1)
+    Y = lib.colmajor(Y0)
+    ctx.filter_degrees(n, k, lib.colmajor(H), Y, deg, a, b, a0, lib.CHFSI_PREC_MIXED)
+    ref = O2.chebyshev_filter_per_column(H, Y0, deg, a, b, a0)
+    assert rel_err(lib.to_numpy(Y), ref) < tol_for(16, n)
+
+
+def test_filter_mixed_matches_fp64_kernel_closely(ctx):
+    """Same inputs through both device paths: the mixed result sits within the FP32-equivalent
+    bound of the FP64 one (a check that does not depend on the oracle)."""
+    n, k, m = 700, 64, 10
+    H, lam = std_problem(n, 53)
+    Y0 = synth.start_block(n, k, 53)
+    a, b, a0 = float(lam[80]), float(lam[-1] * 1.05), float(lam[0] - 0.1)
+    Y1, Y2 = lib.colmajor(Y0), lib.colmajor(Y0)
+    Hd = lib.colmajor(H)
+    ctx.filter(n, k, Hd, Y1, m, a, b, a0, lib.CHFSI_PREC_FP64)
+    ctx.filter(n, k, Hd, Y2, m, a, b, a0, lib.CHFSI_PREC_MIXED)
+    assert rel_err(lib.to_numpy(Y2), lib.to_numpy(Y1)) < tol_for(m, n)

@@ -41,7 +41,7 @@ def solve_once(prec, w, p, X0=None, per_vector=False):
     return ctx, st, ev.cpu().numpy(), lib.to_numpy(X), info
 
 
-@pytest.mark.parametrize("prec", [lib.CHFSI_PREC_FP64])
+@pytest.mark.parametrize("prec", [lib.CHFSI_PREC_FP64, lib.CHFSI_PREC_MIXED])
 def test_single_n512(prec):
     w = synth.SINGLE_N512
     p = synth.prescribed_pencil(w.n, w.n_low, w.high, w.seed)
@@ -106,7 +106,7 @@ def load_golden_sequence():
     return rows
 
 
-@pytest.mark.parametrize("prec", [lib.CHFSI_PREC_FP64])
+@pytest.mark.parametrize("prec", [lib.CHFSI_PREC_FP64, lib.CHFSI_PREC_MIXED])
 def test_sequence_n2000_against_golden(prec):
     """The n = 2000, 20-step sequence (the benchmark workload): every step's eigenvalues
     against the oracle's direct solver (stored by tests/golden/make_sequence_evals.py),
