@@ -141,6 +141,15 @@ chfsi_status chfsi_lanczos(chfsi_ctx *c, int n, const void *Hs, int steps, int k
 chfsi_status chfsi_filter(chfsi_ctx *c, int n, int k, const void *Hs, void *Y, int m, double a,
                           double b, double a0, int precision);
 
+/* a4m, residual-corrected form for a Ritz block: Y (n x k) with Ritz values lam[k] (device)
+ * and Z = H' Y (n x k, device), as chfsi_rayleigh_ritz returns them.  Computes the same
+ * T_m((H' - cI)/e) Y / T_m((a0 - c)/e) as chfsi_filter, written as Y p_m(lam) + D_m with
+ * D_j = fa_j H' D_{j-1} + fb_j D_{j-1} + fg_j D_{j-2} + fa_j (Z - Y diag(lam)) p_{j-1}(lam):
+ * the tensor-core products act on D, whose size is proportional to the residual, so their
+ * rounding error shrinks with it instead of flooring the subspace accuracy. */
+chfsi_status chfsi_filter_ritz(chfsi_ctx *c, int n, int k, const void *Hs, void *Y, const double *lam,
+                               const void *Z, int m, double a, double b, double a0);
+
 /* a10 (filter part). Column i filtered with its own degree deg[i] (host array, non-increasing). */
 chfsi_status chfsi_filter_degrees(chfsi_ctx *c, int n, int k, const void *Hs, void *Y, const int *deg,
                                   double a, double b, double a0, int precision);

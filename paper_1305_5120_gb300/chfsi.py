@@ -67,6 +67,7 @@ _SIGS = {
     "chfsi_lanczos": [_P, _I, _P, _I, _I, _P, _P, _P, _P],
     "chfsi_filter": [_P, _I, _I, _P, _P, _I, _D, _D, _D, _I],
     "chfsi_filter_degrees": [_P, _I, _I, _P, _P, ctypes.POINTER(_I), _D, _D, _D, _I],
+    "chfsi_filter_ritz": [_P, _I, _I, _P, _P, _P, _P, _I, _D, _D, _D],
     "chfsi_orthonormalize": [_P, _I, _I, _P, _I, _P],
     "chfsi_rayleigh_ritz": [_P, _I, _I, _P, _P, _P, _P],
     "chfsi_reduced_eig": [_P, _I, _P, _P, _P],
@@ -207,6 +208,10 @@ class Context:
         arr = (ctypes.c_int * k)(*[int(d) for d in degrees])
         _check(self.lib.chfsi_filter_degrees(self.h, n, k, _ptr(Hs), _ptr(Y), arr, a, b, a0, precision),
                "chfsi_filter_degrees")
+
+    def filter_ritz(self, n, k, Hs, Y, lam, Z, m, a, b, a0):
+        _check(self.lib.chfsi_filter_ritz(self.h, n, k, _ptr(Hs), _ptr(Y), _ptr(lam), _ptr(Z), m, a, b, a0),
+               "chfsi_filter_ritz")
 
     def orthonormalize(self, n, nl, Ylocked, k, Y):
         _check(self.lib.chfsi_orthonormalize(self.h, n, nl, _ptr(Ylocked), k, _ptr(Y)), "chfsi_orthonormalize")

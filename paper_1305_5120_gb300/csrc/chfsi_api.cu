@@ -280,8 +280,14 @@ __global__ void copy_odd_columns_kernel(int n, const int* deg, const cplx* src, 
 }
 
 // Filter on Y (n x k, ld n) with non-increasing degrees deg[0..k) (host), FP64 or tensor cores.
+struct RitzData {
+  const cplx* Z;          // H' Y (device)
+  const double* lam_dev;  // Ritz values (device)
+  const double* lam_host; // the same values (host)
+};
+
 chfsi_status run_filter(chfsi_ctx* c, int n, int k, const cplx* Hs, cplx* Y, const int* deg, double a, double b,
-                        double a0, int precision, long long* col_steps) {
+                        double a0, int precision, long long* col_steps, const RitzData* ritz = nullptr) {
   if (k <= 0) return CHFSI_OK;
   const int mmax = deg[0];
   if (mmax <= 0) return CHFSI_OK;
@@ -303,8 +309,26 @@ chfsi_status run_filter(chfsi_ctx* c, int n, int k, const cplx* Hs, cplx* Y, con
   TRY(buf(c, "filter_y2", (size_t)n * k, &Y2));
   cplx* bufs[2] = {Y, Y2};
   if (precision == CHFSI_PREC_MIXED) {
-    TRY(tc_filter_run(c->tc ? c->tc : (c->tc = tc_filter_new()), c->stream, n, Hs, bufs, cnt.data(), mmax,
-                      fa.data(), fb.data(), fg.data()));
+    if (!c->tc) c->tc = tc_filter_new();
+    if (ritz) {
+      // p_j(lam_i), j = 0..mmax, by the scalar form of the same recurrence
+      std::vector<double> ptab((size_t)(mmax + 1) * k);
+      for (int i = 0; i < k; ++i) {
+        const double l = ritz->lam_host[i];
+        double pm2 = 0.0, pm1 = 1.0;
+        ptab[i] = 1.0;
+        for (int j = 1; j <= mmax; ++j) {
+          const double p = fa[j] * l * pm1 + fb[j] * pm1 + (j >= 2 ? fg[j] * pm2 : 0.0);
+          ptab[(size_t)j * k + i] = p;
+          pm2 = pm1;
+          pm1 = p;
+        }
+      }
+      TcRefine ref{ritz->Z, ritz->lam_dev, ptab.data(), deg};
+      TRY(tc_filter_run(c->tc, c->stream, n, Hs, bufs, cnt.data(), mmax, fa.data(), fb.data(), fg.data(), &ref));
+      return CHFSI_OK;   // result already in Y for every column
+    }
+    TRY(tc_filter_run(c->tc, c->stream, n, Hs, bufs, cnt.data(), mmax, fa.data(), fb.data(), fg.data()));
   } else {
     for (int j = 1; j <= mmax; ++j) {
       GemmArgs g = gemm_args(n, cnt[j], n, OP_N, Hs, n, OP_N, bufs[(j - 1) & 1], n, bufs[j & 1], n, ONE, ZERO);
@@ -446,15 +470,17 @@ struct Timer {
 // The iteration of Algorithm 1 on the stored standard-form problem.  Y (n x k) holds the
 // start block; on return Y holds the whole block sorted by Ritz value.
 chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, double a0, double* evals, cplx* Xout,
-                     const cplx* Linv, chfsi_info* info) {
+                     const cplx* Linv, chfsi_info* info, bool seeded) {
   const int n = c->n, nev = c->nev, k = nev + c->nex;
   const double tol_lock = c->tol / c->kappa_L;
   cplx *Z, *Y2;
   double *lam, *res, *resabs;
   int* perm;
+  double* lam_tmp;
   TRY(buf(c, "it_Z", (size_t)n * k, &Z));
   TRY(buf(c, "it_Y2", (size_t)n * k, &Y2));
   TRY(buf(c, "it_lam", k, &lam));
+  TRY(buf(c, "it_lam_tmp", k, &lam_tmp));
   TRY(buf(c, "it_res", k, &res));
   TRY(buf(c, "it_resabs", k, &resabs));
   TRY(buf(c, "it_perm", k, &perm));
@@ -478,9 +504,12 @@ chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, 
   const double hnorm = std::max(fabs(a0), fabs(b));
   double* h_resabs = c->h_d + 3 * k;
   std::vector<double> lam_active;
+  bool have_ritz = false;   // Z, lam (columns nl..k) hold H' Ya and the Ritz values of Ya
   for (;;) {
     ++it;
     cplx* Ya = Y + (size_t)nl * n;
+    cplx* Za = Z + (size_t)nl * n;
+    double* lama = lam + nl;
     tm.start();
     tm.mark(0);
     // line 3: filter (mixed precision while every active residual is above the switch)
@@ -494,7 +523,15 @@ chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, 
     last_lowp = prec == CHFSI_PREC_MIXED;
     prev_min_res_abs = min_res_abs;
     long long cs = 0;
-    TRY(run_filter(c, n, ka, Hs, Ya, deg.data(), a, b, a0, prec, &cs));
+    // a seeded mixed-precision solve starts with Rayleigh-Ritz of the seed block, so that
+    // every filter pass can use the residual-corrected tensor-core recurrence
+    const bool skip_filter = seeded && it == 1 && c->prm.precision == CHFSI_PREC_MIXED;
+    if (skip_filter) last_lowp = false;
+    if (!skip_filter) {
+      RitzData rd{Za, lama, lam_active.data()};
+      const bool use_ritz = prec == CHFSI_PREC_MIXED && have_ritz && (int)lam_active.size() == ka;
+      TRY(run_filter(c, n, ka, Hs, Ya, deg.data(), a, b, a0, prec, &cs, use_ritz ? &rd : nullptr));
+    }
     colsteps += cs;
     if (prec == CHFSI_PREC_MIXED) colsteps_lowp += cs;
     tm.mark(prec == CHFSI_PREC_MIXED ? 8 : 2);
@@ -502,11 +539,12 @@ chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, 
     TRY(orthonormalize(c, n, nl, Y, ka, Ya));
     tm.mark(3);
     // lines 5-7: Rayleigh-Ritz
-    TRY(rayleigh_ritz(c, n, ka, Hs, Ya, lam, Z));
+    TRY(rayleigh_ritz(c, n, ka, Hs, Ya, lama, Za));
+    have_ritz = true;
     tm.mark(4);
     // residuals
-    CU(residual_norms(c->stream, n, ka, Z, n, Ya, n, lam, res, resabs));
-    CU(cudaMemcpyAsync(h_lam, lam, sizeof(double) * ka, cudaMemcpyDeviceToHost, c->stream));
+    CU(residual_norms(c->stream, n, ka, Za, n, Ya, n, lama, res, resabs));
+    CU(cudaMemcpyAsync(h_lam, lama, sizeof(double) * ka, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaMemcpyAsync(h_res, res, sizeof(double) * ka, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaMemcpyAsync(h_resabs, resabs, sizeof(double) * ka, cudaMemcpyDeviceToHost, c->stream));
     int h_err = 0;
@@ -560,6 +598,10 @@ chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, 
       CU(cudaMemcpyAsync(perm, h_perm, sizeof(int) * ka, cudaMemcpyHostToDevice, c->stream));
       CU(gather_columns(c->stream, n, ka, perm, Ya, n, Y2, n));
       CU(copy_block(c->stream, n, ka, Y2, n, Ya, n));
+      CU(gather_columns(c->stream, n, ka, perm, Za, n, Y2, n));
+      CU(copy_block(c->stream, n, ka, Y2, n, Za, n));
+      CU(gather_values(c->stream, ka, perm, lama, lam_tmp));
+      CU(cudaMemcpyAsync(lama, lam_tmp, sizeof(double) * ka, cudaMemcpyDeviceToDevice, c->stream));
     }
     nl += (int)lockv.size();
     ka -= (int)lockv.size();
@@ -690,7 +732,7 @@ chfsi_status solve_common(chfsi_ctx* c, const cplx* H, const cplx* S, const cplx
   CU(cudaEventRecord(l1, c->stream));
   CU(cudaEventSynchronize(l1));
   cudaEventElapsedTime(&ms_lanczos, r1, l1);
-  chfsi_status st = iterate(c, Hs, Y, a, b, a0, evals, (cplx*)X, Linv, info);
+  chfsi_status st = iterate(c, Hs, Y, a, b, a0, evals, (cplx*)X, Linv, info, seeded);
   CU(cudaEventRecord(t1, c->stream));
   CU(cudaEventSynchronize(t1));
   if (info) {
@@ -861,6 +903,20 @@ chfsi_status chfsi_filter_degrees(chfsi_ctx* c, int n, int k, const void* Hs, vo
   if (precision != CHFSI_PREC_FP64 && precision != CHFSI_PREC_MIXED) return CHFSI_ERR_ARG;
   TRY(setup_device(c));
   TRY(run_filter(c, n, k, (const cplx*)Hs, (cplx*)Y, deg, a, b, a0, precision, nullptr));
+  CU(cudaStreamSynchronize(c->stream));
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_filter_ritz(chfsi_ctx* c, int n, int k, const void* Hs, void* Y, const double* lam, const void* Z,
+                               int m, double a, double b, double a0) {
+  if (!c || !valid_ptrs({Hs, Y, lam, Z}) || n < 1 || k < 1 || m < 1) return CHFSI_ERR_ARG;
+  TRY(setup_device(c));
+  std::vector<double> hl(k);
+  CU(cudaMemcpyAsync(hl.data(), lam, sizeof(double) * k, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  std::vector<int> deg(k, m);
+  RitzData rd{(const cplx*)Z, lam, hl.data()};
+  TRY(run_filter(c, n, k, (const cplx*)Hs, (cplx*)Y, deg.data(), a, b, a0, CHFSI_PREC_MIXED, nullptr, &rd));
   CU(cudaStreamSynchronize(c->stream));
   return CHFSI_OK;
 }

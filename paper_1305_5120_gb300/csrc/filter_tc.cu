@@ -17,6 +17,9 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "filter_tc.cuh"
 
 void count_launch(unsigned long long n);
@@ -32,7 +35,7 @@ constexpr int A_TILE = BM * BK * 2;            // bytes per A slice tile (16 KB)
 constexpr int B_TILE = BN * BK * 2;            // bytes per B slice tile (8 KB)
 constexpr int STAGE_BYTES = NSLICE * (A_TILE + B_TILE);
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
-constexpr int TMEM_COLS = BN;    // fp32 accumulator columns
+constexpr int TMEM_COLS = 2 * BN;  // fp32 accumulators: [0, BN) leading slice product, [BN, 2BN) corrections
 constexpr int NTHREADS = 192;
 constexpr long WAIT_LIMIT = 1L << 24;
 
@@ -48,6 +51,8 @@ struct StepArgs {
   cplx* Yout;                    // in: Y_{j-1} (if fg != 0), out: Y_{j+1}
   __nv_bfloat16* Bnext;          // next step's B slices (NULL on the last step)
   double fa, fb, fg;
+  const cplx* R;                 // corrected recurrence: R = H Yhat - Yhat diag(lam) (n x ncols)
+  const double* fcol;            // per column fa * p_{j-1}(lam_col); NULL for the plain recurrence
   int* err;
 };
 
@@ -206,7 +211,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           for (int p = 0; p < 6; ++p) {
             const uint64_t da = umma_desc(st + prod_a[p] * A_TILE + kk * 32);
             const uint64_t db = umma_desc(st + NSLICE * A_TILE + prod_b[p] * B_TILE + kk * 32);
-            umma_bf16(tmem, da, db, (kb | kk | p) != 0);
+            // the leading product s = t = 0 and the five corrections accumulate apart: the
+            // accumulator's per-instruction truncation then acts on each at its own scale
+            if (p == 0) umma_bf16(tmem, da, db, (kb | kk) != 0);
+            else umma_bf16(tmem + BN, da, db, (kb | kk | (p - 1)) != 0);
           }
         }
         umma_commit(empty(s));   // frees the stage once these MMAs have read it
@@ -222,21 +230,32 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
-      float acc[BN];
+      float acc[BN], cor[BN];
 #pragma unroll
-      for (int c = 0; c < BN; c += 16) tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + c, acc + c);
+      for (int c = 0; c < BN; c += 16) {
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + c, acc + c);
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + BN + c, cor + c);
+      }
       if (row < g.n) {
-#pragma unroll 4
+#pragma unroll
         for (int jj = 0; jj < BN / 2; ++jj) {
           const int j = n0 / 2 + jj;     // complex column
-          if (j >= g.ncols) break;
+          if (j >= g.ncols) continue;
           const long e = (long)j * g.n + row;
           const cplx y = g.Ycur[e];
-          cplx o = cmk(g.fa * (double)acc[2 * jj] + g.fb * y.x, g.fa * (double)acc[2 * jj + 1] + g.fb * y.y);
+          const double hr = (double)acc[2 * jj] + (double)cor[2 * jj];
+          const double hi = (double)acc[2 * jj + 1] + (double)cor[2 * jj + 1];
+          cplx o = cmk(g.fa * hr + g.fb * y.x, g.fa * hi + g.fb * y.y);
           if (g.fg != 0.0) {
             const cplx p = g.Yout[e];
             o.x += g.fg * p.x;
             o.y += g.fg * p.y;
+          }
+          if (g.fcol) {   // residual forcing of the corrected recurrence: + fa p_{j-1}(lam_j) R_j
+            const cplx r = g.R[e];
+            const double f = g.fcol[j];
+            o.x += f * r.x;
+            o.y += f * r.y;
           }
           g.Yout[e] = o;
           if (g.Bnext) {
@@ -313,6 +332,49 @@ __global__ void slice_Y_kernel(int n, int ncols, long kpad, long npad, const cpl
   }
 }
 
+// R = Z - Yhat diag(lam);  D_1 = fa1 * R; B slices of D_1 for the next product
+__global__ void refine_first_kernel(int n, int ncols, long kpad, long npad, const cplx* __restrict__ Z,
+                                    const cplx* __restrict__ Y, const double* __restrict__ lam, double fa1,
+                                    cplx* __restrict__ R, cplx* __restrict__ D1, __nv_bfloat16* __restrict__ B) {
+  const long j = blockIdx.y;
+  const double l = lam[j];
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
+    const long e = j * n + c;
+    const cplx z = Z[e], y = Y[e];
+    const cplx r = cmk(z.x - l * y.x, z.y - l * y.y);
+    R[e] = r;
+    const cplx d = cmk(fa1 * r.x, fa1 * r.y);
+    D1[e] = d;
+    if (B) {
+      __nv_bfloat16 xr[3], xi[3];
+      split3(d.x, xr[0], xr[1], xr[2]);
+      split3(d.y, xi[0], xi[1], xi[2]);
+      for (int t = 0; t < 3; ++t) {
+        __nv_bfloat16* rowRe = B + (t * npad + 2 * j) * kpad;
+        __nv_bfloat162 v0, v1;
+        v0.x = xr[t]; v0.y = __hneg(xi[t]);
+        v1.x = xi[t]; v1.y = xr[t];
+        *(__nv_bfloat162*)(rowRe + 2 * c) = v0;
+        *(__nv_bfloat162*)(rowRe + kpad + 2 * c) = v1;
+      }
+    }
+  }
+}
+
+// Yhat_j <- Yhat_j p_{m_j}(lam_j) + D_{m_j}, D_m in Dbuf[m & 1]
+__global__ void refine_combine_kernel(int n, cplx* __restrict__ Y, const cplx* __restrict__ D0,
+                                      const cplx* __restrict__ D1, const double* __restrict__ pm,
+                                      const int* __restrict__ deg) {
+  const long j = blockIdx.y;
+  const double p = pm[j];
+  const cplx* D = (deg[j] & 1) ? D1 : D0;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
+    const long e = j * n + c;
+    const cplx y = Y[e], d = D[e];
+    Y[e] = cmk(p * y.x + d.x, p * y.y + d.y);
+  }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -349,6 +411,11 @@ struct TcFilter {
   long kpad = 0, mpad = 0, npad = 0;
   __nv_bfloat16* A = nullptr;
   __nv_bfloat16* B[2] = {nullptr, nullptr};
+  cplx* D[2] = {nullptr, nullptr};   // corrected recurrence state
+  cplx* R = nullptr;
+  double* tab = nullptr;             // forcing scales per step and column, final p_m per column
+  int* deg = nullptr;
+  int tab_cap = 0;
   int* err = nullptr;
   CUtensorMap mapA, mapB[2];
   bool attr = false;
@@ -361,6 +428,11 @@ void tc_filter_free(TcFilter* f) {
   cudaFree(f->A);
   cudaFree(f->B[0]);
   cudaFree(f->B[1]);
+  cudaFree(f->D[0]);
+  cudaFree(f->D[1]);
+  cudaFree(f->R);
+  cudaFree(f->tab);
+  cudaFree(f->deg);
   cudaFree(f->err);
   delete f;
 }
@@ -370,7 +442,11 @@ static chfsi_status tc_ensure(TcFilter* f, int n, int k) {
   cudaFree(f->A);
   cudaFree(f->B[0]);
   cudaFree(f->B[1]);
+  cudaFree(f->D[0]);
+  cudaFree(f->D[1]);
+  cudaFree(f->R);
   f->A = f->B[0] = f->B[1] = nullptr;
+  f->D[0] = f->D[1] = f->R = nullptr;
   f->n = n;
   f->k = k;
   f->kpad = round_up(2L * n, BK);
@@ -381,6 +457,8 @@ static chfsi_status tc_ensure(TcFilter* f, int n, int k) {
     CHFSI_CUDA_TRY(cudaMalloc(&f->B[i], sizeof(__nv_bfloat16) * 3 * f->npad * f->kpad));
     CHFSI_CUDA_TRY(cudaMemset(f->B[i], 0, sizeof(__nv_bfloat16) * 3 * f->npad * f->kpad));
   }
+  for (int i = 0; i < 2; ++i) CHFSI_CUDA_TRY(cudaMalloc(&f->D[i], sizeof(cplx) * (size_t)n * k));
+  CHFSI_CUDA_TRY(cudaMalloc(&f->R, sizeof(cplx) * (size_t)n * k));
   if (!f->err) CHFSI_CUDA_TRY(cudaMalloc(&f->err, sizeof(int)));
   if (!make_map(&f->mapA, f->A, 3 * f->mpad, f->kpad, BM)) return CHFSI_ERR_CUDA;
   for (int i = 0; i < 2; ++i)
@@ -393,20 +471,47 @@ static chfsi_status tc_ensure(TcFilter* f, int n, int k) {
 }
 
 chfsi_status tc_filter_run(TcFilter* f, cudaStream_t s, int n, const cplx* H, cplx* bufs[2], const int* cnt, int mmax,
-                           const double* fa, const double* fb, const double* fg) {
+                           const double* fa, const double* fb, const double* fg, const TcRefine* ref) {
   if (mmax < 1 || cnt[1] < 1) return CHFSI_OK;
-  chfsi_status st = tc_ensure(f, n, cnt[1]);
+  const int k = cnt[1];
+  chfsi_status st = tc_ensure(f, n, k);
   if (st != CHFSI_OK) return st;
   CHFSI_CUDA_TRY(cudaMemsetAsync(f->err, 0, sizeof(int), s));
   {
     dim3 grid((unsigned)((f->kpad / 2 + 255) / 256), (unsigned)f->mpad);
     slice_H_kernel<<<grid, 256, 0, s>>>(n, f->kpad, f->mpad, H, f->A);
     count_launch(1);
+  }
+  const unsigned cgrid = (unsigned)std::min<long>((n + 255) / 256, 16);
+  std::vector<double> htab;
+  if (ref) {
+    // device table: rows j = 0..mmax of fa[j] p_{j-1}(lam_i) (row 0 unused), then p_{m_i}(lam_i)
+    const int rows = mmax + 2;
+    if (f->tab_cap < rows * k) {
+      cudaFree(f->tab);
+      cudaFree(f->deg);
+      f->tab = nullptr;
+      f->deg = nullptr;
+      CHFSI_CUDA_TRY(cudaMalloc(&f->tab, sizeof(double) * (size_t)rows * k));
+      CHFSI_CUDA_TRY(cudaMalloc(&f->deg, sizeof(int) * (size_t)k));
+      f->tab_cap = rows * k;
+    }
+    htab.assign((size_t)rows * k, 0.0);
+    for (int j = 1; j <= mmax; ++j)
+      for (int i = 0; i < k; ++i) htab[(size_t)j * k + i] = fa[j] * ref->ptab[(size_t)(j - 1) * k + i];
+    for (int i = 0; i < k; ++i) htab[(size_t)(mmax + 1) * k + i] = ref->ptab[(size_t)ref->deg[i] * k + i];
+    CHFSI_CUDA_TRY(cudaMemcpyAsync(f->tab, htab.data(), sizeof(double) * htab.size(), cudaMemcpyHostToDevice, s));
+    CHFSI_CUDA_TRY(cudaMemcpyAsync(f->deg, ref->deg, sizeof(int) * k, cudaMemcpyHostToDevice, s));
+    dim3 g1(cgrid, (unsigned)k);
+    refine_first_kernel<<<g1, 256, 0, s>>>(n, k, f->kpad, f->npad, ref->Z, bufs[0], ref->lam, fa[1], f->R, f->D[1],
+                                           mmax > 1 ? f->B[1] : nullptr);
+    count_launch(1);
+  } else {
     dim3 gy((unsigned)((f->kpad / 2 + 255) / 256), (unsigned)(f->npad / 2));
-    slice_Y_kernel<<<gy, 256, 0, s>>>(n, cnt[1], f->kpad, f->npad, bufs[0], f->B[0]);
+    slice_Y_kernel<<<gy, 256, 0, s>>>(n, k, f->kpad, f->npad, bufs[0], f->B[0]);
     count_launch(1);
   }
-  for (int j = 1; j <= mmax; ++j) {
+  for (int j = ref ? 2 : 1; j <= mmax; ++j) {
     StepArgs g{};
     g.n = n;
     g.mtiles = (int)(f->mpad / BM);
@@ -414,17 +519,30 @@ chfsi_status tc_filter_run(TcFilter* f, cudaStream_t s, int n, const cplx* H, cp
     g.kblocks = (int)(f->kpad / BK);
     g.ldb_next = f->kpad;
     g.nslice_rows_b = f->npad;
-    g.Ycur = bufs[(j - 1) & 1];
-    g.Yout = bufs[j & 1];
+    if (ref) {
+      g.Ycur = f->D[(j - 1) & 1];
+      g.Yout = f->D[j & 1];
+      g.fg = (j >= 3) ? fg[j] : 0.0;      // D_0 = 0
+      g.R = f->R;
+      g.fcol = f->tab + (size_t)j * k;
+    } else {
+      g.Ycur = bufs[(j - 1) & 1];
+      g.Yout = bufs[j & 1];
+      g.fg = (j >= 2) ? fg[j] : 0.0;
+    }
     g.Bnext = (j < mmax) ? f->B[j & 1] : nullptr;
     g.fa = fa[j];
     g.fb = fb[j];
-    g.fg = (j >= 2) ? fg[j] : 0.0;
     g.err = f->err;
     dim3 grid((unsigned)g.mtiles, (unsigned)((2L * cnt[j] + BN - 1) / BN));
     tc_filter_step_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(f->mapA, f->mapB[(j - 1) & 1], g);
     count_launch(1);
     CHFSI_CUDA_TRY(cudaGetLastError());
+  }
+  if (ref) {
+    dim3 g2(cgrid, (unsigned)k);
+    refine_combine_kernel<<<g2, 256, 0, s>>>(n, bufs[0], f->D[0], f->D[1], f->tab + (size_t)(mmax + 1) * k, f->deg);
+    count_launch(1);
   }
   int h = 0;
   CHFSI_CUDA_TRY(cudaMemcpyAsync(&h, f->err, sizeof(int), cudaMemcpyDeviceToHost, s));

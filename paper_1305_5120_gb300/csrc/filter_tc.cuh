@@ -6,7 +6,22 @@
 struct TcFilter;
 TcFilter* tc_filter_new();
 void tc_filter_free(TcFilter* f);
+
+// Residual-corrected form (used when the block is a Ritz block of H):  with H Yhat =
+// Yhat diag(lam) + R, the filtered block is Yhat p_m(lam) + D_m where D_0 = 0 and
+//     D_j = fa[j] H D_{j-1} + fb[j] D_{j-1} + fg[j] D_{j-2} + fa[j] R diag(p_{j-1}(lam)),
+// an exact rewriting of the recurrence in which the low-precision products act on D, whose
+// size is proportional to the residual, so their rounding no longer sets an accuracy floor.
+struct TcRefine {
+  const cplx* Z;        // H Yhat, n x k (device)
+  const double* lam;    // Ritz values, k (device)
+  const double* ptab;   // host, (mmax + 1) x k: ptab[j * k + i] = p_j(lam_i)
+  const int* deg;       // host, per-column degree (non-increasing)
+};
+
 // Runs mmax recurrence steps: Y_j = fa[j] H Y_{j-1} + fb[j] Y_{j-1} + fg[j] Y_{j-2} on the
-// first cnt[j] columns; Y_j lands in bufs[j & 1] (bufs[0] holds Y_0 on entry).
+// first cnt[j] columns; Y_j lands in bufs[j & 1] (bufs[0] holds Y_0 on entry).  With ref
+// the corrected form runs instead and the result replaces bufs[0] for every column.
 chfsi_status tc_filter_run(TcFilter* f, cudaStream_t s, int n, const cplx* H, cplx* bufs[2], const int* cnt,
-                           int mmax, const double* fa, const double* fb, const double* fg);
+                           int mmax, const double* fa, const double* fb, const double* fg,
+                           const TcRefine* ref = nullptr);
