@@ -505,6 +505,17 @@ chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, 
   double* h_resabs = c->h_d + 3 * k;
   std::vector<double> lam_active;
   bool have_ritz = false;   // Z, lam (columns nl..k) hold H' Ya and the Ritz values of Ya
+  if (seeded && c->prm.precision == CHFSI_PREC_MIXED) {
+    // the seed block (the previous problem's Ritz vectors) with its Rayleigh quotients for the
+    // new H': Z = H' Y, lam_i = y_i^H z_i.  The corrected recurrence is exact for any diagonal
+    // lam; with these the forcing R = Z - Y diag(lam) is as small as the change of H'.
+    TRY(gemm(c, gemm_args(n, k, n, OP_N, Hs, n, OP_N, Y, n, Z, n, ONE, ZERO)));
+    CU(rayleigh_quotients(c->stream, n, k, Y, n, Z, n, lam));
+    CU(cudaMemcpyAsync(h_lam, lam, sizeof(double) * k, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    lam_active.assign(h_lam, h_lam + k);
+    have_ritz = true;
+  }
   for (;;) {
     ++it;
     cplx* Ya = Y + (size_t)nl * n;
@@ -517,17 +528,15 @@ chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, 
     // above mixed_switch * ||H'|| and the previous low-precision pass still made progress
     // (an FP32-equivalent filter stalls near 2^-24 ||H'||)
     int prec = CHFSI_PREC_FP64;
-    if (c->prm.precision == CHFSI_PREC_MIXED && min_res_abs > c->prm.mixed_switch * hnorm &&
-        !(last_lowp && min_res_abs > 0.1 * prev_min_res_abs))
-      prec = CHFSI_PREC_MIXED;
+    if (c->prm.precision == CHFSI_PREC_MIXED) {
+      const bool stalled = last_lowp && min_res_abs > 0.1 * prev_min_res_abs;
+      if (have_ritz) prec = stalled ? CHFSI_PREC_FP64 : CHFSI_PREC_MIXED;   // corrected recurrence: no floor
+      else if (min_res_abs > c->prm.mixed_switch * hnorm && !stalled) prec = CHFSI_PREC_MIXED;
+    }
     last_lowp = prec == CHFSI_PREC_MIXED;
     prev_min_res_abs = min_res_abs;
     long long cs = 0;
-    // a seeded mixed-precision solve starts with Rayleigh-Ritz of the seed block, so that
-    // every filter pass can use the residual-corrected tensor-core recurrence
-    const bool skip_filter = seeded && it == 1 && c->prm.precision == CHFSI_PREC_MIXED;
-    if (skip_filter) last_lowp = false;
-    if (!skip_filter) {
+    {
       RitzData rd{Za, lama, lam_active.data()};
       const bool use_ritz = prec == CHFSI_PREC_MIXED && have_ritz && (int)lam_active.size() == ka;
       TRY(run_filter(c, n, ka, Hs, Ya, deg.data(), a, b, a0, prec, &cs, use_ritz ? &rd : nullptr));

@@ -161,6 +161,18 @@ __global__ void residual_kernel(int n, const cplx* Z, long ldz, const cplx* Y, l
   }
 }
 
+__global__ void rayleigh_quotient_kernel(int n, const cplx* Y, long ldy, const cplx* Z, long ldz, double* lam) {
+  __shared__ double sh[32];
+  const int j = blockIdx.x;
+  double acc = 0.0;
+  for (long r = threadIdx.x; r < n; r += blockDim.x) {
+    cplx y = Y[r + j * ldy], z = Z[r + j * ldz];
+    acc += y.x * z.x + y.y * z.y;   // Re(conj(y) z)
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) lam[j] = acc;
+}
+
 __device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed, unsigned long long i) {
   unsigned long long z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -264,6 +276,13 @@ cudaError_t residual_norms(cudaStream_t s, int n, int k, const cplx* Z, long ldz
                            const double* lam, double* res, double* resabs) {
   if (k <= 0) return cudaSuccess;
   residual_kernel<<<k, 256, 0, s>>>(n, Z, ldz, Y, ldy, lam, res, resabs); count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t rayleigh_quotients(cudaStream_t s, int n, int k, const cplx* Y, long ldy, const cplx* Z, long ldz,
+                               double* lam) {
+  if (k <= 0) return cudaSuccess;
+  rayleigh_quotient_kernel<<<k, 256, 0, s>>>(n, Y, ldy, Z, ldz, lam); count_launch();
   return cudaGetLastError();
 }
 

@@ -17,6 +17,9 @@ cudaError_t gather_values(cudaStream_t s, int cnt, const int* perm, const double
 // Column-wise relative residuals res[j] = ||Z_j - lam_j Y_j|| / ||Z_j||, and abs[j] the numerator.
 cudaError_t residual_norms(cudaStream_t s, int n, int k, const cplx* Z, long ldz, const cplx* Y, long ldy,
                            const double* lam, double* res, double* resabs);
+// lam[j] = Re(Y_j^H Z_j) (Rayleigh quotients when Z = H Y and ||Y_j|| = 1).
+cudaError_t rayleigh_quotients(cudaStream_t s, int n, int k, const cplx* Y, long ldy, const cplx* Z, long ldz,
+                               double* lam);
 // SplitMix64 complex block: element (i, j) = u(2(j n + i)) + i u(2(j n + i) + 1), u in [-0.5, 0.5),
 // counter offset stream * 2^40 (the same definition the oracle uses).
 cudaError_t splitmix_block(cudaStream_t s, int n, int k, unsigned long long seed, unsigned long long stream,
