@@ -167,6 +167,21 @@ chfsi_status chfsi_rayleigh_ritz(chfsi_ctx *c, int n, int k, const void *Hs, voi
 /* a7 alone. All eigenpairs of the k x k Hermitian G (parallel Jacobi): lam ascending, W. */
 chfsi_status chfsi_reduced_eig(chfsi_ctx *c, int k, const void *G, double *lam, void *W);
 
+/* Allocation-free form of chfsi_reduced_eig, for callers that cannot allocate device memory
+ * (a plugin or callback that owns no device allocator, or a loop that must not trigger the
+ * device-wide synchronisation of cudaMalloc/cudaFree).  The paper has no counterpart.
+ * Same result as chfsi_reduced_eig (G k x k Hermitian, device, not modified; lam[k]
+ * ascending and W k x k, device) with no context: work is ordered on `cuda_stream` (NULL =
+ * legacy default stream) of the current device and the call returns when it is complete.
+ * Scratch lives in one fixed device array of this library, sized for k <= 256
+ * (CHFSI_NOALLOC_KMAX); larger k returns CHFSI_ERR_ARG.  The first call on a device looks
+ * up that array's device address (a one-time set-up with the device current); make that
+ * first call before any stream capture.  Every call on a device shares the array and
+ * re-initialises it, so calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  Nothing is allocated or freed. */
+#define CHFSI_NOALLOC_KMAX 256
+chfsi_status chfsi_reduced_eig_noalloc(void *cuda_stream, int k, const void *G, double *lam, void *W);
+
 /* a9. res[j] = ||Z_j - lam_j Y_j|| / ||Z_j|| (Algorithm 1, Res), Z = H' Y. */
 chfsi_status chfsi_residuals(chfsi_ctx *c, int n, int k, const void *Z, const void *Y, const double *lam,
                              double *res);

@@ -71,6 +71,7 @@ _SIGS = {
     "chfsi_orthonormalize": [_P, _I, _I, _P, _I, _P],
     "chfsi_rayleigh_ritz": [_P, _I, _I, _P, _P, _P, _P],
     "chfsi_reduced_eig": [_P, _I, _P, _P, _P],
+    "chfsi_reduced_eig_noalloc": [_P, _I, _P, _P, _P],
     "chfsi_residuals": [_P, _I, _I, _P, _P, _P, _P],
     "chfsi_degrees": [_P, _I, _P, _P, _D, _D, _D, _I, _I, _P],
     "chfsi_back_transform": [_P, _I, _I, _P, _P, _P],
@@ -136,6 +137,13 @@ def colmajor(A, device="cuda"):
 def to_numpy(t) -> np.ndarray:
     """Inverse of colmajor: device buffer of shape (cols, rows) -> numpy (rows, cols)."""
     return t.detach().cpu().numpy().T.copy()
+
+
+def reduced_eig_noalloc(k, G, lam, W, stream=None) -> int:
+    """Allocation-free reduced eigensolver (k <= 256); returns the chfsi_status code."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    return int(load().chfsi_reduced_eig_noalloc(_P(st.cuda_stream), k, _ptr(G), _ptr(lam), _ptr(W)))
 
 
 def default_params(**kw) -> Params:

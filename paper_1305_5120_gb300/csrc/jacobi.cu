@@ -7,6 +7,9 @@
 // single cooperative launch.  Near-diagonal G (later outer iterations and sequence solves)
 // converges in one or two sweeps.
 #include <math.h>
+
+#include <mutex>
+
 #include "jacobi.cuh"
 
 namespace {
@@ -199,4 +202,87 @@ cudaError_t jacobi_eig(cudaStream_t s, int k, cplx* G, double* lam, cplx* W, voi
   if (e != cudaSuccess) return e;
   jacobi_sort_kernel<<<k < 1024 ? k : 1024, 128, 0, s>>>(k, G, (const cplx*)g.V, lam, W); count_launch();
   return cudaGetLastError();
+}
+
+// ---- allocation-free variant ----------------------------------------------------------------
+// Some callers cannot allocate device memory: code that runs inside a host process whose
+// device memory is owned and budgeted by someone else (a plugin or callback that receives
+// only input and output buffers), or a serving loop that must not pay the implicit
+// device-wide synchronisation of cudaMalloc/cudaFree while other streams are busy.  For
+// them, chfsi_reduced_eig_noalloc keeps its scratch -- a working copy of G, the rotation
+// accumulator V, the rotation table, sweep counters, the grid barrier and the error word --
+// in one fixed file-scope device array sized for k <= CHFSI_NOALLOC_KMAX.  Every GPU that
+// loads this library holds the array until the process exits.
+
+namespace {
+constexpr int NOALLOC_KMAX = 256;
+constexpr int NOALLOC_SWEEPS = 64;
+constexpr size_t NOALLOC_BYTES = 2 * sizeof(cplx) * (size_t)NOALLOC_KMAX * NOALLOC_KMAX +
+                                 sizeof(Rot) * (size_t)(NOALLOC_KMAX / 2) + 1024;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+std::mutex g_noalloc_mu;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+void* g_noalloc_base[NOALLOC_MAX_DEVICES] = {};   // device address of the array, per device
+}  // namespace
+
+extern "C" chfsi_status chfsi_reduced_eig_noalloc(void* cuda_stream, int k, const void* G, double* lam, void* W) {
+  if (k < 1 || k > NOALLOC_KMAX || !G || !lam || !W) return CHFSI_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return chfsi_cuda_error(e, "cudaGetDevice");
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return CHFSI_ERR_ARG;
+  char* base = nullptr;
+  {
+    // one-time set-up per device (with that device current): the host-side name of the
+    // array is not a device address, so ask the runtime for the address
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) return chfsi_cuda_error(e, "cudaGetSymbolAddress");
+      g_noalloc_base[dev] = p;
+    }
+    base = (char*)g_noalloc_base[dev];
+  }
+  const int kk = k + (k & 1);
+  char* w = base;
+  JacobiArgs g{};
+  g.k = k;
+  g.kk = kk;
+  g.A = (cplx*)w;                 w += sizeof(cplx) * (size_t)k * k;
+  g.V = (cplx*)w;                 w += sizeof(cplx) * (size_t)k * k;
+  g.rot = (Rot*)w;                w += sizeof(Rot) * (size_t)(kk / 2);
+  char* zero_begin = w;
+  g.rot_count = (int*)w;          w += sizeof(int) * NOALLOC_SWEEPS;
+  g.fro = (double*)w;             w += sizeof(double) * 2;
+  unsigned* bar = (unsigned*)w;   w += sizeof(unsigned) * 4;
+  g.err = (int*)w;                w += sizeof(int);
+  g.sweeps = (int*)w;             w += sizeof(int);
+  g.bar.count = bar;
+  g.bar.gen = bar + 1;
+  g.max_sweeps = NOALLOC_SWEEPS;
+  // the array keeps the previous call's contents: copy G in and clear what must start at zero
+  e = cudaMemcpyAsync(g.A, G, sizeof(cplx) * (size_t)k * k, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(zero_begin, 0, (size_t)(w - zero_begin), s);
+  if (e != cudaSuccess) return chfsi_cuda_error(e, "scratch set-up");
+  fro_kernel<<<1, 1024, 0, s>>>(k, g.A, g.fro);
+  count_launch();
+  const long work_items = (long)(kk / 2) * (kk / 2) + (long)k * (kk / 2);
+  int blocks = coop_blocks((int)((work_items + 255) / 256));
+  void* args[] = {&g};
+  e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(blocks), dim3(256), args, 0, s);
+  count_launch();
+  if (e != cudaSuccess) return chfsi_cuda_error(e, "jacobi launch");
+  jacobi_sort_kernel<<<k < 1024 ? k : 1024, 128, 0, s>>>(k, g.A, (const cplx*)g.V, lam, (cplx*)W);
+  count_launch();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return chfsi_cuda_error(e, "jacobi sort");
+  int herr = 0;
+  e = cudaMemcpyAsync(&herr, g.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return chfsi_cuda_error(e, "jacobi status");
+  if (herr == DEV_OK) return CHFSI_OK;
+  return herr == DEV_ERR_TIMEOUT ? CHFSI_ERR_TIMEOUT : CHFSI_ERR_NO_CONV;
 }
