@@ -121,6 +121,17 @@ unsigned long long chfsi_kernel_launches(void);
 
 /* ---- Stage entry points (each step of the solve on its own; device pointers) -------- */
 
+/* The dense complex product the stages are built from: C = alpha op(A) op(B) + beta C,
+ * op = 'N' (as stored) or 'C' (conjugate transpose); op(A) is M x K, op(B) K x N, all
+ * column-major with leading dimensions lda, ldb, ldc.  alpha, beta: host (re, im) pairs.
+ * CHFSI_PREC_FP64 runs it on the FP64 pipe; CHFSI_PREC_MIXED as an error-free expansion in
+ * BF16 digits on the tensor cores (13 digits of 5 bits per entry relative to its row or
+ * column scale, exact integer accumulation per significance level, levels combined in
+ * FP64: 65 bits of the row/column scale before the final FP64 rounding). */
+chfsi_status chfsi_gemm(chfsi_ctx *c, char opA, char opB, int M, int N, int K, const double *alpha,
+                        const void *A, int lda, const void *B, int ldb, const double *beta, void *C,
+                        int ldc, int precision);
+
 /* a1. S = L L^H (Section 3).  L: n x n lower triangular output (upper part zeroed). */
 chfsi_status chfsi_cholesky(chfsi_ctx *c, int n, const void *S, void *L);
 

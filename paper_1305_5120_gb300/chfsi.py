@@ -62,6 +62,8 @@ _SIGS = {
     "chfsi_destroy": [_P],
     "chfsi_status_string": [_I],
     "chfsi_kernel_launches": [],
+    "chfsi_gemm": [_P, ctypes.c_char, ctypes.c_char, _I, _I, _I, ctypes.POINTER(_D), _P, _I, _P, _I,
+                   ctypes.POINTER(_D), _P, _I, _I],
     "chfsi_cholesky": [_P, _I, _P, _P],
     "chfsi_reduce": [_P, _I, _P, _P, _P],
     "chfsi_lanczos": [_P, _I, _P, _I, _I, _P, _P, _P, _P],
@@ -199,6 +201,12 @@ class Context:
         return st, evals, X, info
 
     # --- stages -------------------------------------------------------------------------------
+    def gemm(self, opA, opB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, precision=CHFSI_PREC_FP64):
+        al = (_D * 2)(complex(alpha).real, complex(alpha).imag)
+        be = (_D * 2)(complex(beta).real, complex(beta).imag)
+        _check(self.lib.chfsi_gemm(self.h, opA.encode(), opB.encode(), M, N, K, al, _ptr(A), lda, _ptr(B), ldb, be,
+                                   _ptr(C), ldc, precision), "chfsi_gemm")
+
     def cholesky(self, n, S, L):
         _check(self.lib.chfsi_cholesky(self.h, n, _ptr(S), _ptr(L)), "chfsi_cholesky")
 

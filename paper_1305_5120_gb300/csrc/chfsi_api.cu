@@ -16,6 +16,7 @@
 #include "filter_tc.cuh"
 #include "jacobi.cuh"
 #include "lanczos.cuh"
+#include "ozaki.cuh"
 
 static unsigned long long g_launches = 0;   // host-side count; launches are issued from host threads
 static std::mutex g_launch_mu;
@@ -77,6 +78,7 @@ struct chfsi_ctx {
   chfsi_params prm{};
   Arena arena;
   TcFilter* tc = nullptr;   // tensor-core filter state (lazy)
+  OzakiGemm* oz = nullptr;  // FP64-accurate tensor-core GEMM state (lazy)
   // pinned host mirrors
   double* h_d = nullptr;    // 4 * kcap doubles
   int* h_i = nullptr;       // 2 * kcap ints
@@ -171,6 +173,18 @@ GemmArgs gemm_args(int M, int N, int K, int opA, const cplx* A, long lda, int op
 }
 const cplx ONE = {1.0, 0.0}, ZERO = {0.0, 0.0}, MONE = {-1.0, 0.0};
 
+// FP64-accurate product: in mixed-precision mode the large ones run as the error-free digit
+// expansion on the tensor cores (ozaki.cu); otherwise, and for small shapes, on the DFMA pipe.
+chfsi_status gemm64(chfsi_ctx* c, const GemmArgs& g) {
+  if (c->prm.precision == CHFSI_PREC_MIXED && g.epi == EPI_GEMM && g.N > 1 && g.M > 1 &&
+      (double)g.M * g.N * g.K >= 4.0e6) {
+    if (!c->oz) c->oz = ozaki_new();
+    CU(ozaki_gemm(c->oz, g, c->stream, c->d_err));
+    return CHFSI_OK;
+  }
+  return gemm(c, g);
+}
+
 // a1 + inverse: L and Linv from S --------------------------------------------------------
 chfsi_status factor_S(chfsi_ctx* c, int n, const cplx* S, cplx* L, cplx* Linv) {
   CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
@@ -186,8 +200,8 @@ chfsi_status factor_S(chfsi_ctx* c, int n, const cplx* S, cplx* L, cplx* Linv) {
 chfsi_status transform(chfsi_ctx* c, int n, const cplx* H, const cplx* Linv, cplx* Hs) {
   cplx* W;
   TRY(buf(c, "tmp_nn", (size_t)n * n, &W));
-  TRY(gemm(c, gemm_args(n, n, n, OP_N, Linv, n, OP_N, H, n, W, n, ONE, ZERO, TRI_A_LOWER)));
-  TRY(gemm(c, gemm_args(n, n, n, OP_N, W, n, OP_C, Linv, n, Hs, n, ONE, ZERO, TRI_B_UPPER)));
+  TRY(gemm64(c, gemm_args(n, n, n, OP_N, Linv, n, OP_N, H, n, W, n, ONE, ZERO, TRI_A_LOWER)));
+  TRY(gemm64(c, gemm_args(n, n, n, OP_N, W, n, OP_C, Linv, n, Hs, n, ONE, ZERO, TRI_B_UPPER)));
   CU(hermitize(c->stream, n, Hs, n));
   return CHFSI_OK;
 }
@@ -373,7 +387,7 @@ chfsi_status cholqr_pass(chfsi_ctx* c, int n, int k, cplx* Y, bool shifted, bool
   TRY(buf(c, "qr_G", (size_t)k * k, &G));
   TRY(buf(c, "qr_Ri", (size_t)k * k, &Ri));
   TRY(buf(c, "qr_T", (size_t)n * k, &T));
-  TRY(gemm(c, gemm_args(k, k, n, OP_C, Y, n, OP_N, Y, n, G, k, ONE, ZERO)));
+  TRY(gemm64(c, gemm_args(k, k, n, OP_C, Y, n, OP_N, Y, n, G, k, ONE, ZERO)));
   CU(hermitize(c->stream, k, G, k));
   if (shifted) {
     add_shift_kernel<<<1, 256, 0, c->stream>>>(k, n, G); count_launch();
@@ -389,7 +403,7 @@ chfsi_status cholqr_pass(chfsi_ctx* c, int n, int k, cplx* Y, bool shifted, bool
   }
   CU(trtri_lower(c->stream, k, G, k, Ri, k, c->d_err));
   // Y <- Y R^{-1}, R = Lg^H  =>  R^{-1} = (Lg^{-1})^H (upper triangular)
-  TRY(gemm(c, gemm_args(n, k, k, OP_N, Y, n, OP_C, Ri, k, T, n, ONE, ZERO, TRI_B_UPPER)));
+  TRY(gemm64(c, gemm_args(n, k, k, OP_N, Y, n, OP_C, Ri, k, T, n, ONE, ZERO, TRI_B_UPPER)));
   CU(copy_block(c->stream, n, k, T, n, Y, n));
   *ok = true;
   return CHFSI_OK;
@@ -401,8 +415,8 @@ chfsi_status orthonormalize(chfsi_ctx* c, int n, int nl, const cplx* Yl, int k, 
     cplx* Cm;
     TRY(buf(c, "qr_C", (size_t)nl * k, &Cm));
     for (int pass = 0; pass < 2; ++pass) {
-      TRY(gemm(c, gemm_args(nl, k, n, OP_C, Yl, n, OP_N, Y, n, Cm, nl, ONE, ZERO)));
-      TRY(gemm(c, gemm_args(n, k, nl, OP_N, Yl, n, OP_N, Cm, nl, Y, n, MONE, ONE)));
+      TRY(gemm64(c, gemm_args(nl, k, n, OP_C, Yl, n, OP_N, Y, n, Cm, nl, ONE, ZERO)));
+      TRY(gemm64(c, gemm_args(n, k, nl, OP_N, Yl, n, OP_N, Cm, nl, Y, n, MONE, ONE)));
     }
   }
   bool ok = false;
@@ -433,13 +447,13 @@ chfsi_status rayleigh_ritz(chfsi_ctx* c, int n, int k, const cplx* Hs, cplx* Y, 
   TRY(buf(c, "rr_G", (size_t)k * k, &G));
   TRY(buf(c, "rr_W", (size_t)k * k, &W));
   TRY(buf(c, "rr_T", (size_t)n * k, &T));
-  TRY(gemm(c, gemm_args(n, k, n, OP_N, Hs, n, OP_N, Y, n, Z, n, ONE, ZERO)));
-  TRY(gemm(c, gemm_args(k, k, n, OP_C, Y, n, OP_N, Z, n, G, k, ONE, ZERO)));
+  TRY(gemm64(c, gemm_args(n, k, n, OP_N, Hs, n, OP_N, Y, n, Z, n, ONE, ZERO)));
+  TRY(gemm64(c, gemm_args(k, k, n, OP_C, Y, n, OP_N, Z, n, G, k, ONE, ZERO)));
   CU(hermitize(c->stream, k, G, k));
   TRY(reduced_eig(c, k, G, lam, W));
-  TRY(gemm(c, gemm_args(n, k, k, OP_N, Y, n, OP_N, W, k, T, n, ONE, ZERO)));
+  TRY(gemm64(c, gemm_args(n, k, k, OP_N, Y, n, OP_N, W, k, T, n, ONE, ZERO)));
   CU(copy_block(c->stream, n, k, T, n, Y, n));
-  TRY(gemm(c, gemm_args(n, k, k, OP_N, Z, n, OP_N, W, k, T, n, ONE, ZERO)));
+  TRY(gemm64(c, gemm_args(n, k, k, OP_N, Z, n, OP_N, W, k, T, n, ONE, ZERO)));
   CU(copy_block(c->stream, n, k, T, n, Z, n));
   return CHFSI_OK;
 }
@@ -509,7 +523,7 @@ chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, 
     // the seed block (the previous problem's Ritz vectors) with its Rayleigh quotients for the
     // new H': Z = H' Y, lam_i = y_i^H z_i.  The corrected recurrence is exact for any diagonal
     // lam; with these the forcing R = Z - Y diag(lam) is as small as the change of H'.
-    TRY(gemm(c, gemm_args(n, k, n, OP_N, Hs, n, OP_N, Y, n, Z, n, ONE, ZERO)));
+    TRY(gemm64(c, gemm_args(n, k, n, OP_N, Hs, n, OP_N, Y, n, Z, n, ONE, ZERO)));
     CU(rayleigh_quotients(c->stream, n, k, Y, n, Z, n, lam));
     CU(cudaMemcpyAsync(h_lam, lam, sizeof(double) * k, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
@@ -635,7 +649,7 @@ chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, 
   CU(gather_columns(c->stream, n, nev, perm, Y, n, Y2, n));
   CU(cudaMemcpyAsync(evals, h_lam2, sizeof(double) * nev, cudaMemcpyHostToDevice, c->stream));
   // a11: X = L^{-H} Y
-  TRY(gemm(c, gemm_args(n, nev, n, OP_C, Linv, n, OP_N, Y2, n, (cplx*)Xout, n, ONE, ZERO, TRI_A_UPPER)));
+  TRY(gemm64(c, gemm_args(n, nev, n, OP_C, Linv, n, OP_N, Y2, n, (cplx*)Xout, n, ONE, ZERO, TRI_A_UPPER)));
   tm.mark(6);
   // sequence state: the whole block sorted by Ritz value
   std::vector<int> all(k);
@@ -701,9 +715,9 @@ chfsi_status solve_common(chfsi_ctx* c, const cplx* H, const cplx* S, const cplx
       // S changes inside a sequence: carry the block over as X = L_old^{-H} Y, Y_new = L_new^H X
       cplx* T;
       TRY(buf(c, "tmp_nk", (size_t)n * k, &T));
-      TRY(gemm(c, gemm_args(n, k, n, OP_C, Linv, n, OP_N, Y, n, T, n, ONE, ZERO, TRI_A_UPPER)));
+      TRY(gemm64(c, gemm_args(n, k, n, OP_C, Linv, n, OP_N, Y, n, T, n, ONE, ZERO, TRI_A_UPPER)));
       TRY(factor_S(c, n, S, L, Linv));
-      TRY(gemm(c, gemm_args(n, k, n, OP_C, L, n, OP_N, T, n, Y, n, ONE, ZERO, TRI_A_UPPER)));
+      TRY(gemm64(c, gemm_args(n, k, n, OP_C, L, n, OP_N, T, n, Y, n, ONE, ZERO, TRI_A_UPPER)));
     } else {
       TRY(factor_S(c, n, S, L, Linv));
     }
@@ -713,7 +727,7 @@ chfsi_status solve_common(chfsi_ctx* c, const cplx* H, const cplx* S, const cplx
   if (!seeded) {
     if (X0) {
       // Y0 = L^H X0
-      TRY(gemm(c, gemm_args(n, k, n, OP_C, L, n, OP_N, X0, n, Y, n, ONE, ZERO, TRI_A_UPPER)));
+      TRY(gemm64(c, gemm_args(n, k, n, OP_C, L, n, OP_N, X0, n, Y, n, ONE, ZERO, TRI_A_UPPER)));
     } else {
       CU(splitmix_block(c->stream, n, k, c->prm.seed, 2, Y, n));
     }
@@ -834,6 +848,7 @@ void chfsi_destroy(chfsi_ctx* c) {
   else cudaDeviceSynchronize();
   c->arena.release();
   if (c->tc) tc_filter_free(c->tc);
+  if (c->oz) ozaki_free(c->oz);
   if (c->d_err) cudaFree(c->d_err);
   if (c->h_d) cudaFreeHost(c->h_d);
   if (c->h_i) cudaFreeHost(c->h_i);
@@ -866,6 +881,29 @@ chfsi_status chfsi_next_in_sequence(chfsi_ctx* c, const void* H_next, const void
 }
 
 // ---- stage entry points ----------------------------------------------------------------
+chfsi_status chfsi_gemm(chfsi_ctx* c, char opA, char opB, int M, int N, int K, const double* alpha, const void* A,
+                        int lda, const void* B, int ldb, const double* beta, void* C, int ldc, int precision) {
+  if (!c || !valid_ptrs({alpha, A, B, beta, C}) || M < 0 || N < 0 || K < 0) return CHFSI_ERR_ARG;
+  if ((opA != 'N' && opA != 'C') || (opB != 'N' && opB != 'C')) return CHFSI_ERR_ARG;
+  if (precision != CHFSI_PREC_FP64 && precision != CHFSI_PREC_MIXED) return CHFSI_ERR_ARG;
+  const int oa = opA == 'N' ? OP_N : OP_C, ob = opB == 'N' ? OP_N : OP_C;
+  if (lda < std::max(1, oa == OP_N ? M : K) || ldb < std::max(1, ob == OP_N ? K : N) || ldc < std::max(1, M))
+    return CHFSI_ERR_ARG;
+  TRY(setup_device(c));
+  GemmArgs g = gemm_args(M, N, K, oa, (const cplx*)A, lda, ob, (const cplx*)B, ldb, (cplx*)C, ldc,
+                         cmk(alpha[0], alpha[1]), cmk(beta[0], beta[1]));
+  CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  if (precision == CHFSI_PREC_MIXED) {
+    if (!c->oz) c->oz = ozaki_new();
+    CU(ozaki_gemm(c->oz, g, c->stream, c->d_err));
+  } else {
+    TRY(gemm(c, g));
+  }
+  int e = 0;
+  TRY(read_err(c, &e));
+  return map_dev_err(e);
+}
+
 chfsi_status chfsi_cholesky(chfsi_ctx* c, int n, const void* S, void* L) {
   if (!c || !valid_ptrs({S, L}) || n < 1) return CHFSI_ERR_ARG;
   TRY(setup_device(c));
@@ -986,7 +1024,7 @@ chfsi_status chfsi_back_transform(chfsi_ctx* c, int n, int k, const void* L, con
   TRY(buf(c, "Linv_stage", (size_t)n * n, &Linv));
   CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   CU(trtri_lower(c->stream, n, (const cplx*)L, n, Linv, n, c->d_err));
-  TRY(gemm(c, gemm_args(n, k, n, OP_C, Linv, n, OP_N, (const cplx*)Y, n, (cplx*)X, n, ONE, ZERO, TRI_A_UPPER)));
+  TRY(gemm64(c, gemm_args(n, k, n, OP_C, Linv, n, OP_N, (const cplx*)Y, n, (cplx*)X, n, ONE, ZERO, TRI_A_UPPER)));
   int e = 0;
   TRY(read_err(c, &e));
   return map_dev_err(e);

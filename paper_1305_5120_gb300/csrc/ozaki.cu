@@ -1,0 +1,542 @@
+// FP64-accurate complex GEMM on the BF16 tensor cores.
+//
+// GB300 executes FP64 at ~1/1700 of its dense BF16 rate, so the FP64 products around the
+// filter (reduction to standard form, Rayleigh-Ritz, QR, back-transform) run as an
+// error-free digit expansion on tcgen05 (after Ozaki, Ogita, Oishi & Rump, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix multiplication
+// and its applications", Numer. Algorithms 2012):
+//
+//  * the complex product is a real GEMM through [Re A | Im A] (K interleaved) times
+//    [[Re B, Im B], [-Im B, Re B]] (columns interleaved);
+//  * every row of the real A (every column pair of the real B) is scaled by a power of two
+//    sigma >= its largest magnitude and expanded into S = 13 signed digits of beta = 5 bits,
+//    x = sigma 2^-(beta-1) sum_s 2^-(s beta) d_s,  |d_s| <= 16 (exact in BF16);
+//  * digit products d_s e_t are integers <= 256; all products of one significance level
+//    L = s + t (L <= S - 1) accumulate in their own TMEM accumulator.  With at most 13
+//    products per level and K <= 4992 real terms per pass, every partial sum is an integer
+//    below 2^24, so the FP32 accumulation is exact even though the tensor core truncates;
+//  * the epilogue combines the 13 levels in FP64 and applies the scales: each entry carries
+//    65 bits relative to its row (column) scale before the final FP64 rounding -- the
+//    expansion's error is relative to the largest entry of the row, not to the entry, and
+//    Hermitian matrices with a wide spectrum (large diagonal, small off-diagonal) need the
+//    extra digits to stay at FP64 accuracy.  Longer K runs in passes (split-K) whose FP64
+//    partial results a fixed-order reduction sums.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "ozaki.cuh"
+
+void count_launch(unsigned long long n);
+
+namespace {
+
+constexpr int SLICES = 13;       // digits per operand (65 bits relative to the row/column scale)
+constexpr int DIGIT_BITS = 5;    // |digit| <= 2^(DIGIT_BITS-1) = 16
+constexpr int LEVELS = SLICES;   // kept levels L = s + t = 0 .. SLICES-1
+constexpr int KPASS = 4992;      // real K per pass: 13 * 4992 * 256 < 2^24
+constexpr int BM = 128, BN = 32, BK = 16;   // BK bf16 = 32-byte rows (32B swizzle), one MMA K step
+constexpr int STAGES = 3;
+constexpr int A_TILE = BM * BK * 2;           // 4 KB
+constexpr int B_TILE = BN * BK * 2;           // 1 KB
+constexpr int STAGE_BYTES = SLICES * (A_TILE + B_TILE);
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int TMEM_COLS = 512;                // LEVELS * BN = 352 used
+constexpr int NTHREADS = 192;
+constexpr long WAIT_LIMIT = 1L << 24;
+static_assert(LEVELS * BN <= TMEM_COLS, "TMEM");
+static_assert(STAGE_BYTES % 1024 == 0, "stage alignment");
+static_assert(SMEM_BYTES <= 232448, "shared memory");
+static_assert((long)LEVELS * KPASS * 256 < (1L << 24), "exact accumulation");
+
+struct OzArgs {
+  int M, N2;              // rows, real columns (2N)
+  int mtiles;             // M_pad / BM
+  long npad;              // real columns padded (rows of each B slice)
+  int kblocks;            // K blocks (BK real each) in total
+  int per;                // K blocks per split (<= KPASS / BK keeps each split exact)
+  int tri;                // GemmTri flags in complex units
+  const int* rowexp;      // per row of A: exponent e (sigma = 2^e)
+  const int* colexp;      // per complex column of B
+  // output: splits > 1 -> partial[z] (M x N complex, FP64); else C = alpha v + beta C
+  cplx* C; long ldc;
+  cplx alpha, beta;
+  cplx* partial;          // [splits][M*N]
+  int splits;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+  for (long i = 0; i < WAIT_LIMIT; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 255) == 255 && *(volatile int*)err != DEV_OK) return false;
+  }
+  atomicExch(err, DEV_ERR_TIMEOUT);
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          dst),
+      "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+// K-major operand, 32-byte swizzle: 8-row atoms of 256 B
+__device__ __forceinline__ uint64_t umma_desc32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(256 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)6 << 61;    // SWIZZLE_32B
+  return d;
+}
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzArgs g) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* base_ptr = smem_raw + (base - raw);
+  const uint32_t bars = base + STAGES * STAGE_BYTES;
+  uint32_t* tmem_slot = (uint32_t*)(base_ptr + STAGES * STAGE_BYTES + 8 * (2 * STAGES + 1));
+  auto full = [&](int s) { return bars + 8u * s; };
+  auto empty = [&](int s) { return bars + 8u * (STAGES + s); };
+  const uint32_t accum = bars + 8u * (2 * STAGES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM;
+  const int n0 = blockIdx.y * BN;        // real column offset
+  const int z = blockIdx.z;
+
+  // K-block range: this split, pruned by the triangular structure of the tile (complex units
+  // -> real K = 2 * complex K)
+  int kb0 = z * g.per, kb1 = min(g.kblocks, kb0 + g.per);
+  {
+    int kc_begin = 0, kc_end = 1 << 30;
+    const int cm0 = m0, cm1 = m0 + BM, cn0 = n0 / 2, cn1 = (n0 + BN) / 2;
+    if (g.tri & TRI_A_LOWER) kc_end = min(kc_end, cm1);
+    if (g.tri & TRI_B_UPPER) kc_end = min(kc_end, cn1);
+    if (g.tri & TRI_A_UPPER) kc_begin = max(kc_begin, cm0);
+    if (g.tri & TRI_B_LOWER) kc_begin = max(kc_begin, cn0);
+    kb0 = max(kb0, (2 * kc_begin) / BK);
+    if (kc_end < (1 << 30)) kb1 = min(kb1, (2 * kc_end + BK - 1) / BK);
+  }
+  const int nkb = max(0, kb1 - kb0);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(accum, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *(volatile uint32_t*)tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int i = 0; i < nkb; ++i) {
+        const int s = i % STAGES;
+        const uint32_t ph = (i / STAGES) & 1;
+        if (!mbar_wait(empty(s), ph ^ 1, g.err)) break;
+        mbar_expect_tx(full(s), STAGE_BYTES);
+        const uint32_t st = base + s * STAGE_BYTES;
+        const int kx = (kb0 + i) * BK;
+        for (int q = 0; q < SLICES; ++q) tma_load_2d(st + q * A_TILE, &tmA, full(s), kx, q * g.mtiles * BM + m0);
+        for (int q = 0; q < SLICES; ++q)
+          tma_load_2d(st + SLICES * A_TILE + q * B_TILE, &tmB, full(s), kx, (int)(q * g.npad) + n0);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      for (int i = 0; i < nkb; ++i) {
+        const int s = i % STAGES;
+        const uint32_t ph = (i / STAGES) & 1;
+        if (!mbar_wait(full(s), ph, g.err)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st = base + s * STAGE_BYTES;
+        for (int sa = 0; sa < SLICES; ++sa) {
+          const uint64_t da = umma_desc32(st + sa * A_TILE);
+          for (int tb = 0; tb + sa < LEVELS; ++tb) {
+            const uint64_t db = umma_desc32(st + SLICES * A_TILE + tb * B_TILE);
+            const uint32_t acc = (i | sa) != 0;   // first write of level sa + tb: i == 0, sa == 0
+            umma_bf16(tmem + (uint32_t)((sa + tb) * BN), da, db, acc);
+          }
+        }
+        umma_commit(empty(s));
+      }
+      umma_commit(accum);
+    }
+  } else {
+    const int q = warp & 3;
+    const int row = m0 + q * 32 + lane;
+    bool ok = true;
+    if (nkb > 0) ok = mbar_wait(accum, 0, g.err);
+    ok = __all_sync(0xffffffffu, ok && *(volatile int*)g.err == DEV_OK);
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      double v[BN];
+#pragma unroll
+      for (int c = 0; c < BN; ++c) v[c] = 0.0;
+      if (nkb > 0) {
+        // sum_L 2^(-L beta) acc_L, smallest level first
+        for (int L = LEVELS - 1; L >= 0; --L) {
+          float a[BN];
+#pragma unroll
+          for (int c = 0; c < BN; c += 16) tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + L * BN + c, a + c);
+          const double w = ldexp(1.0, -L * DIGIT_BITS);
+#pragma unroll
+          for (int c = 0; c < BN; ++c) v[c] = fma((double)a[c], w, v[c]);
+        }
+      }
+      if (row < g.M) {
+        const int er = g.rowexp[row];
+#pragma unroll
+        for (int jj = 0; jj < BN / 2; ++jj) {
+          const int j = n0 / 2 + jj;
+          if (2 * j >= g.N2) continue;
+          const int sc = er + g.colexp[j] - 2 * (DIGIT_BITS - 1);
+          const cplx p = cmk(ldexp(v[2 * jj], sc), ldexp(v[2 * jj + 1], sc));
+          const long N = g.N2 / 2;
+          if (g.splits > 1) {
+            g.partial[(long)z * g.M * N + row + (long)j * g.M] = p;
+          } else {
+            cplx o = cmul(g.alpha, p);
+            if (g.beta.x != 0.0 || g.beta.y != 0.0) o = cadd(o, cmul(g.beta, g.C[row + (long)j * g.ldc]));
+            g.C[row + (long)j * g.ldc] = o;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (*(volatile int*)g.err != DEV_OK) __nanosleep(200000);
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+}
+
+// op(X)[r, c] of an R x Cn complex matrix stored column-major
+__device__ __forceinline__ cplx op_at(const cplx* X, long ld, int op, long r, long c) {
+  if (op == OP_N) return X[r + c * ld];
+  const cplx v = X[c + r * ld];
+  return cmk(v.x, -v.y);
+}
+
+__device__ __forceinline__ int exp_of(double x) {   // smallest e with |x| < 2^e (x != 0)
+  int e;
+  frexp(x, &e);
+  return e;
+}
+
+// Row exponents of op(A) (M x K): max over the row of exp_of(|Re|), exp_of(|Im|).
+// One thread per row, K-loop; reads coalesce across threads for op N (column-major).
+// For op C the rows are contiguous: one warp per row instead.
+__global__ void rowexp_kernel(int M, int K, const cplx* A, long lda, int op, int* out) {
+  if (op == OP_N) {
+    const long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (r >= M) return;
+    int e = -100000;
+    for (long c = 0; c < K; ++c) {
+      const cplx v = A[r + c * lda];
+      if (v.x != 0.0) e = max(e, exp_of(v.x));
+      if (v.y != 0.0) e = max(e, exp_of(v.y));
+    }
+    out[r] = e == -100000 ? 0 : e;
+  } else {
+    const long r = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= M) return;
+    int e = -100000;
+    for (long c = lane; c < K; c += 32) {
+      const cplx v = A[c + r * lda];
+      if (v.x != 0.0) e = max(e, exp_of(v.x));
+      if (v.y != 0.0) e = max(e, exp_of(v.y));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if (lane == 0) out[r] = e == -100000 ? 0 : e;
+  }
+}
+
+// digits of x / 2^e: d_0 = rint(u 2^(b-1)), then d_s = rint(r_{s-1} 2^b), r_s = r_{s-1} 2^b - d_s
+__device__ __forceinline__ void digits(double x, int e, __nv_bfloat16* d) {
+  double u = ldexp(x, DIGIT_BITS - 1 - e);
+#pragma unroll
+  for (int s = 0; s < SLICES; ++s) {
+    const double di = rint(u);
+    d[s] = __double2bfloat16(di);    // |di| <= 16: exact
+    u = (u - di) * (double)(1 << DIGIT_BITS);
+  }
+}
+
+// A digits: slice s, row r, columns 2c (Re) and 2c+1 (Im) of the real embedding; the tile is
+// staged through shared memory so that both the read (op-dependent) and the write coalesce.
+__global__ void slice_a_kernel(int M, int K, const cplx* A, long lda, int op, const int* rowexp, long mpad, long kpad,
+                               __nv_bfloat16* out) {
+  __shared__ cplx t[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  for (int i = ty; i < 32; i += 8) {
+    // element (r0 + a, c0 + b); read along the contiguous dimension
+    int a, b;
+    if (op == OP_N) { a = tx; b = i; } else { a = i; b = tx; }
+    const long r = r0 + a, c = c0 + b;
+    t[a][b] = (r < M && c < K) ? op_at(A, lda, op, r, c) : cmk(0.0, 0.0);
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const long r = r0 + i, c = c0 + tx;
+    if (r >= mpad || 2 * c >= kpad) continue;
+    const cplx v = t[i][tx];
+    const int e = r < M ? rowexp[r] : 0;
+    __nv_bfloat16 dr[SLICES], di[SLICES];
+    digits(v.x, e, dr);
+    digits(v.y, e, di);
+#pragma unroll
+    for (int s = 0; s < SLICES; ++s) {
+      __nv_bfloat162 p;
+      p.x = dr[s];
+      p.y = di[s];
+      *(__nv_bfloat162*)(out + (s * mpad + r) * kpad + 2 * c) = p;
+    }
+  }
+}
+
+// B digits: op(B) is K x N; real B^T rows 2j = (Re b, -Im b), 2j+1 = (Im b, Re b) over k.
+__global__ void slice_b_kernel(int K, int N, const cplx* B, long ldb, int op, const int* colexp, long npad, long kpad,
+                               __nv_bfloat16* out) {
+  __shared__ cplx t[32][33];
+  const int j0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int i = ty; i < 32; i += 8) {
+    int a, b;   // a: k offset, b: j offset
+    if (op == OP_N) { a = tx; b = i; } else { a = i; b = tx; }
+    const long kk = k0 + a, j = j0 + b;
+    t[b][a] = (kk < K && j < N) ? op_at(B, ldb, op, kk, j) : cmk(0.0, 0.0);
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const long j = j0 + i, kk = k0 + tx;
+    if (2 * j >= npad || 2 * kk >= kpad) continue;
+    const cplx v = t[i][tx];
+    const int e = j < N ? colexp[j] : 0;
+    __nv_bfloat16 dr[SLICES], di[SLICES];
+    digits(v.x, e, dr);
+    digits(v.y, e, di);
+#pragma unroll
+    for (int s = 0; s < SLICES; ++s) {
+      __nv_bfloat16* rowRe = out + (s * npad + 2 * j) * kpad;
+      __nv_bfloat162 p0, p1;
+      p0.x = dr[s]; p0.y = __hneg(di[s]);
+      p1.x = di[s]; p1.y = dr[s];
+      *(__nv_bfloat162*)(rowRe + 2 * kk) = p0;
+      *(__nv_bfloat162*)(rowRe + kpad + 2 * kk) = p1;
+    }
+  }
+}
+
+__global__ void oz_reduce_kernel(int M, int N, int splits, const cplx* partial, cplx* C, long ldc, cplx alpha,
+                                 cplx beta) {
+  const long total = (long)M * N;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    const long r = e % M, c = e / M;
+    cplx v = cmk(0.0, 0.0);
+    for (int z = 0; z < splits; ++z) v = cadd(v, partial[(long)z * total + e]);
+    cplx o = cmul(alpha, v);
+    if (beta.x != 0.0 || beta.y != 0.0) o = cadd(o, cmul(beta, C[r + c * ldc]));
+    C[r + c * ldc] = o;
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+bool make_map(CUtensorMap* m, void* ptr, long rows, long cols, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+long round_up(long x, long m) { return (x + m - 1) / m * m; }
+}  // namespace
+
+struct OzakiGemm {
+  __nv_bfloat16* A = nullptr;
+  __nv_bfloat16* B = nullptr;
+  size_t a_bytes = 0, b_bytes = 0;
+  int* exps = nullptr;
+  size_t exps_n = 0;
+  cplx* partial = nullptr;
+  size_t partial_bytes = 0;
+  bool attr = false;
+};
+
+OzakiGemm* ozaki_new() { return new OzakiGemm(); }
+void ozaki_free(OzakiGemm* o) {
+  if (!o) return;
+  cudaFree(o->A);
+  cudaFree(o->B);
+  cudaFree(o->exps);
+  cudaFree(o->partial);
+  delete o;
+}
+
+static cudaError_t grow(void** p, size_t* have, size_t need) {
+  if (*have >= need) return cudaSuccess;
+  cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  cudaError_t e = cudaMalloc(p, need);
+  if (e == cudaSuccess) *have = need;
+  return e;
+}
+
+cudaError_t ozaki_gemm(OzakiGemm* o, const GemmArgs& g, cudaStream_t s, int* err) {
+  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  if (g.K <= 0) {
+    // empty product: C = beta C through the DFMA path's epilogue
+    return zgemm_launch(g, s);
+  }
+  const long M = g.M, N = g.N, K = g.K;
+  const long mpad = round_up(M, BM), kpad = round_up(2 * K, BK), npad = round_up(2 * N, BN);
+  cudaError_t e;
+  if ((e = grow((void**)&o->A, &o->a_bytes, sizeof(__nv_bfloat16) * SLICES * mpad * kpad)) != cudaSuccess) return e;
+  if ((e = grow((void**)&o->B, &o->b_bytes, sizeof(__nv_bfloat16) * SLICES * npad * kpad)) != cudaSuccess) return e;
+  size_t have = o->exps_n * sizeof(int);
+  if ((e = grow((void**)&o->exps, &have, sizeof(int) * (M + N))) != cudaSuccess) return e;
+  o->exps_n = have / sizeof(int);
+  if (!o->attr) {
+    if ((e = cudaFuncSetAttribute(ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)) != cudaSuccess)
+      return e;
+    o->attr = true;
+  }
+  int* rowexp = o->exps;
+  int* colexp = o->exps + M;
+  // exponents: rows of op(A); columns of op(B) = rows of op'(B) with the opposite op
+  if (g.opA == OP_N) rowexp_kernel<<<(unsigned)((M + 127) / 128), 128, 0, s>>>((int)M, (int)K, g.A, g.lda, OP_N, rowexp);
+  else rowexp_kernel<<<(unsigned)((M * 32 + 255) / 256), 256, 0, s>>>((int)M, (int)K, g.A, g.lda, OP_C, rowexp);
+  count_launch(1);
+  // column j of op(B): for op N it is column j of B (contiguous) -> the "op C" branch with conj
+  // (magnitudes only matter); for op C it is row j of B -> the "op N" branch
+  if (g.opB == OP_N)
+    rowexp_kernel<<<(unsigned)((N * 32 + 255) / 256), 256, 0, s>>>((int)N, (int)K, g.B, g.ldb, OP_C, colexp);
+  else rowexp_kernel<<<(unsigned)((N + 127) / 128), 128, 0, s>>>((int)N, (int)K, g.B, g.ldb, OP_N, colexp);
+  count_launch(1);
+  {
+    dim3 ga((unsigned)((kpad / 2 + 31) / 32), (unsigned)(mpad / 32));
+    slice_a_kernel<<<ga, 256, 0, s>>>((int)M, (int)K, g.A, g.lda, g.opA, rowexp, mpad, kpad, o->A);
+    count_launch(1);
+    dim3 gb((unsigned)((kpad / 2 + 31) / 32), (unsigned)((npad / 2 + 31) / 32));
+    slice_b_kernel<<<gb, 256, 0, s>>>((int)K, (int)N, g.B, g.ldb, g.opB, colexp, npad, kpad, o->B);
+    count_launch(1);
+  }
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, o->A, SLICES * mpad, kpad, BM)) return cudaErrorInvalidValue;
+  if (!make_map(&tb, o->B, SLICES * npad, kpad, BN)) return cudaErrorInvalidValue;
+  const int kblocks = (int)(kpad / BK);
+  const int passes = (int)((kpad + KPASS - 1) / KPASS);
+  const long tiles = (mpad / BM) * (npad / BN);
+  int splits = passes;
+  // more K splits when the tile grid is small (each split stays within one exact pass)
+  while (tiles * splits < 2 * 152 && splits < 16 * passes && (long)kblocks / (splits + 1) >= 8) ++splits;
+  const int per = (kblocks + splits - 1) / splits;   // <= KPASS / BK since splits >= passes
+  OzArgs a{};
+  a.M = (int)M;
+  a.N2 = (int)(2 * N);
+  a.mtiles = (int)(mpad / BM);
+  a.npad = npad;
+  a.kblocks = kblocks;
+  a.per = per;
+  a.tri = g.tri;
+  a.rowexp = rowexp;
+  a.colexp = colexp;
+  a.C = g.C;
+  a.ldc = g.ldc;
+  a.alpha = g.alpha;
+  a.beta = g.beta;
+  a.splits = splits;
+  a.err = err;
+  if (splits > 1) {
+    if ((e = grow((void**)&o->partial, &o->partial_bytes, sizeof(cplx) * splits * M * N)) != cudaSuccess) return e;
+    a.partial = o->partial;
+  }
+  dim3 grid((unsigned)(mpad / BM), (unsigned)(npad / BN), (unsigned)splits);
+  ozaki_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(ta, tb, a);
+  count_launch(1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (splits > 1) {
+    const long total = M * N;
+    oz_reduce_kernel<<<(unsigned)std::min<long>((total + 255) / 256, 4096), 256, 0, s>>>(
+        (int)M, (int)N, splits, o->partial, g.C, g.ldc, g.alpha, g.beta);
+    count_launch(1);
+  }
+  return cudaGetLastError();
+}

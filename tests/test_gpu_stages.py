@@ -15,10 +15,12 @@ pytestmark = pytest.mark.gpu
 SIZES = [(200, 24), (333, 37), (512, 48)]
 
 
-@pytest.fixture(scope="module")
-def ctx():
+@pytest.fixture(scope="module", params=[lib.CHFSI_PREC_FP64, lib.CHFSI_PREC_MIXED], ids=["fp64", "mixed"])
+def ctx(request):
+    """Both precisions: in mixed mode the FP64 products of every stage run as the exact
+    BF16-digit expansion on the tensor cores; the parity bounds are the same."""
     torch_cuda()
-    c = lib.Context(device=0)
+    c = lib.Context(device=0, precision=request.param)
     yield c
     c.close()
 
