@@ -394,14 +394,21 @@ chfsi_status cholqr_pass(chfsi_ctx* c, int n, int k, cplx* Y, bool shifted, bool
     CU(cudaGetLastError());
   }
   CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
-  CU(chol_lower(c->stream, k, G, k, c->d_err));
+  const bool small = k <= CHOL_INV_KMAX;
+  if (small) {
+    char* w;
+    TRY(buf(c, "qr_cholinv", chol_inv_work_bytes(k), &w));
+    CU(chol_inv_small(c->stream, k, G, Ri, w, c->d_err));
+  } else {
+    CU(chol_lower(c->stream, k, G, k, c->d_err));
+  }
   int e = 0;
   TRY(read_err(c, &e));
   if (e != DEV_OK) {
     *ok = false;
     return CHFSI_OK;
   }
-  CU(trtri_lower(c->stream, k, G, k, Ri, k, c->d_err));
+  if (!small) CU(trtri_lower(c->stream, k, G, k, Ri, k, c->d_err));
   // Y <- Y R^{-1}, R = Lg^H  =>  R^{-1} = (Lg^{-1})^H (upper triangular)
   TRY(gemm64(c, gemm_args(n, k, k, OP_N, Y, n, OP_C, Ri, k, T, n, ONE, ZERO, TRI_B_UPPER)));
   CU(copy_block(c->stream, n, k, T, n, Y, n));

@@ -223,7 +223,11 @@ cudaError_t chol_lower(cudaStream_t s, int n, cplx* A, long lda, int* err) {
     }
     potrf_diag_kernel<<<1, 256, 0, s>>>(A, lda, j0, jb, err); count_launch();
     const int rows = n - j0 - jb;
-    if (rows > 0) potrf_panel_kernel<<<(rows + 127) / 128, 128, 0, s>>>(A, lda, n, j0, jb, err); count_launch();
+    // 32 rows per CTA: the per-row solves are FP64-latency bound, so spread them over SMs
+    if (rows > 0) {
+      potrf_panel_kernel<<<(rows + 31) / 32, 32, 0, s>>>(A, lda, n, j0, jb, err);
+      count_launch();
+    }
   }
   zero_upper_kernel<<<grid_for((long)n * n), 256, 0, s>>>(n, A, lda); count_launch();
   return cudaGetLastError();
@@ -248,7 +252,7 @@ cudaError_t trtri_lower(cudaStream_t s, int n, const cplx* L, long ldl, cplx* X,
       if (e != cudaSuccess) return e;
     }
     const int cols = i0 + jb;
-    trtri_rows_kernel<<<(cols + 127) / 128, 128, 0, s>>>(L, ldl, X, ldx, i0, jb, err); count_launch();
+    trtri_rows_kernel<<<(cols + 31) / 32, 32, 0, s>>>(L, ldl, X, ldx, i0, jb, err); count_launch();
   }
   return cudaGetLastError();
 }
@@ -296,4 +300,188 @@ cudaError_t copy_block(cudaStream_t s, int n, int k, const cplx* src, long lds, 
   if (n <= 0 || k <= 0) return cudaSuccess;
   copy_block_kernel<<<grid_for((long)n * k), 256, 0, s>>>(n, k, src, lds, dst, ldd); count_launch();
   return cudaGetLastError();
+}
+
+// ---- small Cholesky + inverse in one cooperative launch ----------------------------------
+// The k x k Gram matrices of CholQR (k = nev + nex) are too small for a launch-per-block
+// factorisation to keep more than a few SMs busy on the slow FP64 pipe.  Here every grid
+// barrier separates the three phases of a block step -- the 32 x 32 diagonal factor and its
+// inverse (one CTA), the panel L21 = A21 L11^{-H} (one warp per row), the trailing update of
+// the lower triangle (all threads) -- and then the block rows of X = L^{-1}.
+namespace {
+struct CholInvArgs {
+  int k;
+  cplx* A;
+  cplx* X;
+  cplx* Dinv;        // nb blocks of NB x NB: inverses of the diagonal blocks
+  GridBarrier bar;
+  int* err;
+  int* fail;
+};
+
+__global__ void __launch_bounds__(256) chol_inv_kernel(CholInvArgs g) {
+  __shared__ cplx T[NB][NB + 1];
+  __shared__ cplx Ti[NB][NB + 1];
+  __shared__ int bad;
+  const int k = g.k, nb = (k + NB - 1) / NB;
+  const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const long nth = (long)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const long wid = tid >> 5, nwarps = nth >> 5;
+  for (int jb = 0; jb < nb; ++jb) {
+    const int j0 = jb * NB, w = min(NB, k - j0);
+    if (blockIdx.x == 0) {
+      for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        const int r = e % w, c = e / w;
+        T[r][c] = g.A[(j0 + r) + (long)(j0 + c) * k];
+        Ti[r][c] = cmk(r == c ? 1.0 : 0.0, 0.0);
+      }
+      if (threadIdx.x == 0) bad = 0;
+      __syncthreads();
+      for (int c = 0; c < w; ++c) {
+        if (threadIdx.x == 0) {
+          const double p = T[c][c].x;
+          if (!(p > 0.0) || !isfinite(p)) bad = 1;
+          else T[c][c] = cmk(sqrt(p), 0.0);
+        }
+        __syncthreads();
+        if (bad) break;
+        const double inv = 1.0 / T[c][c].x;
+        for (int r = c + 1 + threadIdx.x; r < w; r += blockDim.x) T[r][c] = cscale(T[r][c], inv);
+        __syncthreads();
+        const int m = w - c - 1;
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+          const int r = c + 1 + e % m, q = c + 1 + e / m;
+          if (r >= q) T[r][q] = csub(T[r][q], cmulc(T[r][c], T[q][c]));
+        }
+        __syncthreads();
+      }
+      if (!bad) {
+        // Ti = T^{-1}: column c by forward substitution (one thread per column)
+        if (threadIdx.x < w) {
+          const int c = threadIdx.x;
+          for (int r = 0; r < w; ++r) {
+            cplx s = cmk(r == c ? 1.0 : 0.0, 0.0);
+            for (int q = c; q < r; ++q) s = csub(s, cmul(T[r][q], Ti[q][c]));
+            Ti[r][c] = (r < c) ? cmk(0.0, 0.0) : cscale(s, 1.0 / T[r][r].x);
+          }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+          const int r = e % w, c = e / w;
+          g.A[(j0 + r) + (long)(j0 + c) * k] = (r >= c) ? T[r][c] : cmk(0.0, 0.0);
+          g.X[(j0 + r) + (long)(j0 + c) * k] = Ti[r][c];
+          g.Dinv[(long)jb * NB * NB + r + c * NB] = Ti[r][c];
+        }
+      } else if (threadIdx.x == 0) {
+        *g.fail = 1;
+        atomicExch(g.err, DEV_ERR_NOT_HPD);
+      }
+    }
+    if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
+    if (*(volatile int*)g.fail) return;
+    // panel: rows below, L[r, j0+c] = sum_q A[r, j0+q] conj(Ti[c][q])  (one warp per row)
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+      const int r = e % w, c = e / w;
+      Ti[r][c] = g.Dinv[(long)jb * NB * NB + r + c * NB];
+    }
+    __syncthreads();
+    for (long row = j0 + w + wid; row < k; row += nwarps) {
+      const cplx a = lane < w ? g.A[row + (long)(j0 + lane) * k] : cmk(0.0, 0.0);
+      cplx x = cmk(0.0, 0.0);
+      for (int q = 0; q < w; ++q) {
+        cplx aq;
+        aq.x = __shfl_sync(0xffffffffu, a.x, q);
+        aq.y = __shfl_sync(0xffffffffu, a.y, q);
+        if (lane < w && q <= lane) x = cadd(x, cmulc(aq, Ti[lane][q]));
+      }
+      if (lane < w) g.A[row + (long)(j0 + lane) * k] = x;
+    }
+    if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
+    // trailing update of the lower triangle
+    const int t0 = j0 + w, m = k - t0;
+    for (long e = tid; e < (long)m * m; e += nth) {
+      const int r = t0 + (int)(e % m), c = t0 + (int)(e / m);
+      if (r < c) continue;
+      cplx s = g.A[r + (long)c * k];
+      for (int q = 0; q < w; ++q) s = csub(s, cmulc(g.A[r + (long)(j0 + q) * k], g.A[c + (long)(j0 + q) * k]));
+      g.A[r + (long)c * k] = s;
+    }
+    if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
+  }
+  // strictly upper triangle of L
+  for (long e = tid; e < (long)k * k; e += nth) {
+    const long r = e % k, c = e / k;
+    if (r < c) g.A[e] = cmk(0.0, 0.0);
+  }
+  // block rows of X = L^{-1}: X(i,0:i0) = -Ti (L(i,0:i0) X(0:i0,0:i0))
+  for (int ib = 1; ib < nb; ++ib) {
+    const int i0 = ib * NB, w = min(NB, k - i0);
+    for (long e = tid; e < (long)w * i0; e += nth) {
+      const int r = (int)(e % w), c = (int)(e / w);
+      cplx s = cmk(0.0, 0.0);
+      for (int q = c; q < i0; ++q) s = cadd(s, cmul(g.A[(i0 + r) + (long)q * k], g.X[q + (long)c * k]));
+      g.X[(i0 + r) + (long)c * k] = s;
+    }
+    if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+      const int r = e % w, c = e / w;
+      Ti[r][c] = g.Dinv[(long)ib * NB * NB + r + c * NB];
+    }
+    __syncthreads();
+    for (long c = tid; c < i0; c += nth) {
+      cplx t[NB];
+#pragma unroll
+      for (int q = 0; q < NB; ++q) t[q] = q < w ? g.X[(i0 + q) + c * k] : cmk(0.0, 0.0);
+#pragma unroll
+      for (int r = 0; r < NB; ++r) {
+        if (r >= w) break;
+        cplx s = cmk(0.0, 0.0);
+        for (int q = 0; q <= r; ++q) s = cadd(s, cmul(Ti[r][q], t[q]));
+        g.X[(i0 + r) + c * k] = cmk(-s.x, -s.y);
+      }
+    }
+    if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
+  }
+}
+
+int chol_inv_blocks() {
+  static int cap = 0;
+  if (cap == 0) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, chol_inv_kernel, 256, 0);
+    cap = sms * (occ < 1 ? 1 : 1);
+  }
+  return cap;
+}
+}  // namespace
+
+size_t chol_inv_work_bytes(int k) {
+  const int nb = (k + NB - 1) / NB;
+  return sizeof(cplx) * (size_t)nb * NB * NB + 64;
+}
+
+cudaError_t chol_inv_small(cudaStream_t s, int k, cplx* A, cplx* X, void* work, int* err) {
+  if (k <= 0) return cudaSuccess;
+  if (k > CHOL_INV_KMAX) return cudaErrorInvalidValue;
+  const int nb = (k + NB - 1) / NB;
+  CholInvArgs g{};
+  g.k = k;
+  g.A = A;
+  g.X = X;
+  g.Dinv = (cplx*)work;
+  unsigned* tail = (unsigned*)((char*)work + sizeof(cplx) * (size_t)nb * NB * NB);
+  g.bar.count = tail;
+  g.bar.gen = tail + 1;
+  g.fail = (int*)(tail + 2);
+  g.err = err;
+  cudaError_t e = cudaMemsetAsync(tail, 0, 16, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(X, 0, sizeof(cplx) * (size_t)k * k, s);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&g};
+  e = cudaLaunchCooperativeKernel((const void*)chol_inv_kernel, dim3(chol_inv_blocks()), dim3(256), args, 0, s);
+  count_launch();
+  return e;
 }

@@ -8,6 +8,7 @@
 // converges in one or two sweeps.
 #include <math.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "jacobi.cuh"
@@ -128,6 +129,124 @@ __global__ void __launch_bounds__(256) jacobi_kernel(JacobiArgs g) {
   }
 }
 
+// One barrier per round (k <= 2 * JF_MAXPAIRS): A is double-buffered, and every CTA derives
+// all rotations of the round from the current buffer's diagonal blocks into shared memory
+// (identical in every CTA), so the rotation table needs no grid-wide publication.  All CTAs
+// also count the round's rotations identically, which gives a consistent convergence test
+// without atomics.  Each round reads A_cur and writes every 2 x 2 block of A_next.
+constexpr int JF_MAXPAIRS = 256;
+struct RotS {
+  cplx upp, upq, uqp, uqq;
+  int p, q, on, pad;
+};
+struct JacobiFastArgs {
+  int k, kk;
+  cplx* A[2];
+  cplx* V;
+  double* fro;
+  GridBarrier bar;
+  int* err;
+  int* sweeps;
+  int* final_buf;
+  int max_sweeps;
+};
+
+__device__ __forceinline__ RotS make_rot(const cplx* A, int k, int p, int q, double thresh) {
+  RotS R;
+  if (p > q) { int t = p; p = q; q = t; }
+  R.p = p; R.q = q; R.on = 0; R.pad = 0;
+  R.upp = cmk(1, 0); R.uqq = cmk(1, 0); R.upq = cmk(0, 0); R.uqp = cmk(0, 0);
+  if (q < k) {
+    const cplx apq = A[p + (long)q * k];
+    const double ar = sqrt(cabs2(apq));
+    if (ar > thresh) {
+      const double app = A[p + (long)p * k].x, aqq = A[q + (long)q * k].x;
+      const cplx ph = cmk(apq.x / ar, apq.y / ar);
+      const double tau = (aqq - app) / (2.0 * ar);
+      const double t = (tau < 0.0 ? -1.0 : 1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+      const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+      R.upp = cmk(c, 0.0);
+      R.uqp = cmk(-sn * ph.x, sn * ph.y);
+      R.upq = cmk(sn, 0.0);
+      R.uqq = cmk(c * ph.x, -c * ph.y);
+      R.on = 1;
+    }
+  }
+  return R;
+}
+
+__global__ void __launch_bounds__(256) jacobi_fast_kernel(JacobiFastArgs g) {
+  __shared__ RotS rot[JF_MAXPAIRS];
+  __shared__ int s_on;
+  const int k = g.k, kk = g.kk, np = kk / 2;
+  const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const long nth = (long)gridDim.x * blockDim.x;
+  const double thresh = 2.220446049250313e-16 * (*g.fro);
+  for (long e = tid; e < (long)k * k; e += nth) g.V[e] = cmk((e % k) == (e / k) ? 1.0 : 0.0, 0.0);
+  int cur = 0, sweep = 0;
+  bool converged = false;
+  for (; sweep < g.max_sweeps && !converged; ++sweep) {
+    int on_sweep = 0;
+    for (int r = 0; r < kk - 1; ++r) {
+      const cplx* Ac = g.A[cur];
+      cplx* An = g.A[cur ^ 1];
+      if (threadIdx.x == 0) s_on = 0;
+      __syncthreads();
+      for (int j = threadIdx.x; j < np; j += blockDim.x) {
+        const RotS R = make_rot(Ac, k, rr_slot(j, r, kk), rr_slot(kk - 1 - j, r, kk), thresh);
+        rot[j] = R;
+        if (R.on) atomicAdd(&s_on, 1);
+      }
+      __syncthreads();
+      on_sweep += s_on;
+      const long nblk = (long)np * np;
+      for (long e = tid; e < nblk + (long)k * np; e += nth) {
+        if (e < nblk) {
+          const RotS P = rot[e % np], R = rot[e / np];
+          const bool pq_ok = P.q < k, rs_ok = R.q < k;
+          cplx b00 = Ac[P.p + (long)R.p * k];
+          cplx b01 = rs_ok ? Ac[P.p + (long)R.q * k] : cmk(0, 0);
+          cplx b10 = pq_ok ? Ac[P.q + (long)R.p * k] : cmk(0, 0);
+          cplx b11 = (pq_ok && rs_ok) ? Ac[P.q + (long)R.q * k] : cmk(0, 0);
+          if (P.on || R.on) {
+            const cplx t00 = cadd(cmul(b00, R.upp), cmul(b01, R.uqp));
+            const cplx t01 = cadd(cmul(b00, R.upq), cmul(b01, R.uqq));
+            const cplx t10 = cadd(cmul(b10, R.upp), cmul(b11, R.uqp));
+            const cplx t11 = cadd(cmul(b10, R.upq), cmul(b11, R.uqq));
+            b00 = cadd(cmul(cconj(P.upp), t00), cmul(cconj(P.uqp), t10));
+            b01 = cadd(cmul(cconj(P.upp), t01), cmul(cconj(P.uqp), t11));
+            b10 = cadd(cmul(cconj(P.upq), t00), cmul(cconj(P.uqq), t10));
+            b11 = cadd(cmul(cconj(P.upq), t01), cmul(cconj(P.uqq), t11));
+            if (e % np == e / np && P.on) {
+              b00.y = 0.0; b11.y = 0.0; b01 = cmk(0, 0); b10 = cmk(0, 0);
+            }
+          }
+          An[P.p + (long)R.p * k] = b00;
+          if (rs_ok) An[P.p + (long)R.q * k] = b01;
+          if (pq_ok) An[P.q + (long)R.p * k] = b10;
+          if (pq_ok && rs_ok) An[P.q + (long)R.q * k] = b11;
+        } else {
+          const long f = e - nblk;
+          const int i = (int)(f % k);
+          const RotS R = rot[f / k];
+          if (!R.on) continue;
+          const cplx x = g.V[i + (long)R.p * k], y = g.V[i + (long)R.q * k];
+          g.V[i + (long)R.p * k] = cadd(cmul(x, R.upp), cmul(y, R.uqp));
+          g.V[i + (long)R.q * k] = cadd(cmul(x, R.upq), cmul(y, R.uqq));
+        }
+      }
+      if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
+      cur ^= 1;
+    }
+    converged = on_sweep == 0;
+  }
+  if (tid == 0) {
+    *g.sweeps = sweep;
+    *g.final_buf = cur;
+    if (!converged) atomicExch(g.err, DEV_ERR_NO_CONV);
+  }
+}
+
 // rank sort of the diagonal; W = V permuted, lam ascending (ties by index)
 __global__ void jacobi_sort_kernel(int k, const cplx* A, const cplx* V, double* lam, cplx* W) {
   for (int i = blockIdx.x; i < k; i += gridDim.x) {
@@ -138,6 +257,28 @@ __global__ void jacobi_sort_kernel(int k, const cplx* A, const cplx* V, double* 
     int cnt = 0;
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
       double lj = A[j + (long)j * k].x;
+      if (lj < li || (lj == li && j < i)) ++cnt;
+    }
+    atomicAdd(&rank_sh, cnt);
+    __syncthreads();
+    const int rk = rank_sh;
+    if (threadIdx.x == 0) lam[rk] = li;
+    for (int r = threadIdx.x; r < k; r += blockDim.x) W[r + (long)rk * k] = V[r + (long)i * k];
+    __syncthreads();
+  }
+}
+
+__global__ void jacobi_sort_pick_kernel(int k, const cplx* A0, const cplx* A1, const int* final_buf, const cplx* V,
+                                        double* lam, cplx* W) {
+  const cplx* A = (*final_buf) ? A1 : A0;
+  for (int i = blockIdx.x; i < k; i += gridDim.x) {
+    const double li = A[i + (long)i * k].x;
+    __shared__ int rank_sh;
+    if (threadIdx.x == 0) rank_sh = 0;
+    __syncthreads();
+    int cnt = 0;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+      const double lj = A[j + (long)j * k].x;
       if (lj < li || (lj == li && j < i)) ++cnt;
     }
     atomicAdd(&rank_sh, cnt);
@@ -165,12 +306,59 @@ int coop_blocks(int needed) {
 size_t jacobi_work_bytes(int k) {
   const int kk = k + (k & 1);
   const int max_sweeps = 64;
-  return sizeof(cplx) * (size_t)k * k + sizeof(Rot) * (size_t)(kk / 2) + sizeof(int) * max_sweeps +
+  return 2 * sizeof(cplx) * (size_t)k * k + sizeof(Rot) * (size_t)(kk / 2) + sizeof(int) * max_sweeps +
          sizeof(double) * 2 + sizeof(unsigned) * 4 + 256;
+}
+
+int fast_coop_blocks() {
+  static int cap = 0;
+  if (cap == 0) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_fast_kernel, 256, 0);
+    cap = std::min(64, sms * std::max(occ, 1));
+  }
+  return cap;
 }
 
 cudaError_t jacobi_eig(cudaStream_t s, int k, cplx* G, double* lam, cplx* W, void* work, int* err, int* sweeps) {
   if (k <= 0) return cudaSuccess;
+  if (k <= 2 * JF_MAXPAIRS) {
+    // one barrier per round; the second A buffer follows V in the workspace
+    const int kk = k + (k & 1);
+    const int max_sweeps = 64;
+    char* w = (char*)work;
+    JacobiFastArgs g{};
+    g.k = k;
+    g.kk = kk;
+    g.A[0] = G;
+    g.V = (cplx*)w;                 w += sizeof(cplx) * (size_t)k * k;
+    g.A[1] = (cplx*)w;              w += sizeof(cplx) * (size_t)k * k;
+    w += sizeof(Rot) * (size_t)(kk / 2);
+    char* zero_begin = w;
+    w += sizeof(int) * max_sweeps;
+    g.fro = (double*)w;             w += sizeof(double) * 2;
+    unsigned* bar = (unsigned*)w;   w += sizeof(unsigned) * 4;
+    g.final_buf = (int*)(bar + 2);
+    g.bar.count = bar;
+    g.bar.gen = bar + 1;
+    g.err = err;
+    g.sweeps = sweeps;
+    g.max_sweeps = max_sweeps;
+    cudaError_t e = cudaMemsetAsync(zero_begin, 0, (size_t)(w - zero_begin), s);
+    if (e != cudaSuccess) return e;
+    fro_kernel<<<1, 1024, 0, s>>>(k, G, g.fro);
+    count_launch();
+    void* args[] = {&g};
+    e = cudaLaunchCooperativeKernel((const void*)jacobi_fast_kernel, dim3(fast_coop_blocks()), dim3(256), args, 0, s);
+    count_launch();
+    if (e != cudaSuccess) return e;
+    jacobi_sort_pick_kernel<<<k < 1024 ? k : 1024, 128, 0, s>>>(k, g.A[0], g.A[1], g.final_buf, (const cplx*)g.V, lam,
+                                                                W);
+    count_launch();
+    return cudaGetLastError();
+  }
   const int kk = k + (k & 1);
   const int max_sweeps = 64;
   char* w = (char*)work;

@@ -239,12 +239,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
       if (row < g.M) {
-        const int er = g.rowexp[row];
+        const int er = g.rowexp[row] > -100000 ? g.rowexp[row] : 0;
 #pragma unroll
         for (int jj = 0; jj < BN / 2; ++jj) {
           const int j = n0 / 2 + jj;
           if (2 * j >= g.N2) continue;
-          const int sc = er + g.colexp[j] - 2 * (DIGIT_BITS - 1);
+          const int ec = g.colexp[j] > -100000 ? g.colexp[j] : 0;
+          const int sc = er + ec - 2 * (DIGIT_BITS - 1);
           const cplx p = cmk(ldexp(v[2 * jj], sc), ldexp(v[2 * jj + 1], sc));
           const long N = g.N2 / 2;
           if (g.splits > 1) {
@@ -280,45 +281,61 @@ __device__ __forceinline__ int exp_of(double x) {   // smallest e with |x| < 2^e
   return e;
 }
 
-// Row exponents of op(A) (M x K): max over the row of exp_of(|Re|), exp_of(|Im|).
-// One thread per row, K-loop; reads coalesce across threads for op N (column-major).
-// For op C the rows are contiguous: one warp per row instead.
-__global__ void rowexp_kernel(int M, int K, const cplx* A, long lda, int op, int* out) {
-  if (op == OP_N) {
-    const long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (r >= M) return;
-    int e = -100000;
-    for (long c = 0; c < K; ++c) {
-      const cplx v = A[r + c * lda];
+// Exponent of the largest magnitude in every row of op(X) (rows = true) or column of op(X)
+// (rows = false), op(X) being R x C: 32 x 32 tiles read along the contiguous dimension,
+// reduced with shared and global atomicMax (order-independent).  out[] starts at a large
+// negative sentinel (all-zero rows keep it).
+__global__ void exp_tile_kernel(int R, int C, const cplx* X, long ld, int op, bool rows, int* out) {
+  __shared__ int m[32];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  if (threadIdx.x < 32) m[threadIdx.x] = -100000;
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    int a, b;   // element (r0 + a, c0 + b) of op(X)
+    if (op == OP_N) { a = tx; b = i; } else { a = i; b = tx; }
+    const long r = r0 + a, c = c0 + b;
+    if (r < R && c < C) {
+      const cplx v = op_at(X, ld, op, r, c);
+      int e = -100000;
       if (v.x != 0.0) e = max(e, exp_of(v.x));
       if (v.y != 0.0) e = max(e, exp_of(v.y));
+      if (e > -100000) atomicMax(&m[rows ? a : b], e);
     }
-    out[r] = e == -100000 ? 0 : e;
-  } else {
-    const long r = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (r >= M) return;
-    int e = -100000;
-    for (long c = lane; c < K; c += 32) {
-      const cplx v = A[c + r * lda];
-      if (v.x != 0.0) e = max(e, exp_of(v.x));
-      if (v.y != 0.0) e = max(e, exp_of(v.y));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
-    if (lane == 0) out[r] = e == -100000 ? 0 : e;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const long idx = (rows ? r0 : c0) + threadIdx.x;
+    if (m[threadIdx.x] > -100000 && idx < (rows ? R : C)) atomicMax(out + idx, m[threadIdx.x]);
   }
 }
 
-// digits of x / 2^e: d_0 = rint(u 2^(b-1)), then d_s = rint(r_{s-1} 2^b), r_s = r_{s-1} 2^b - d_s
+// Balanced base-32 digits of x / 2^e (|x| < 2^e):  x = 2^e 2^-4 sum_s 2^(-5 s) d_s, |d_s| <= 16.
+// Integer arithmetic on the FP64 bit pattern: G = round(|x| 2^(64-e)) < 2^64, then digits from
+// the least significant up (r = G mod 32 taken in [-15, 16], G = (G - r) / 32); the sign of x
+// is applied to every digit.
 __device__ __forceinline__ void digits(double x, int e, __nv_bfloat16* d) {
-  double u = ldexp(x, DIGIT_BITS - 1 - e);
-#pragma unroll
-  for (int s = 0; s < SLICES; ++s) {
-    const double di = rint(u);
-    d[s] = __double2bfloat16(di);    // |di| <= 16: exact
-    u = (u - di) * (double)(1 << DIGIT_BITS);
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int bexp = (int)((bits >> 52) & 0x7FF);
+  unsigned long long G = 0;
+  if (bexp != 0) {   // zero and subnormals (far below any row scale here) give zero digits
+    const unsigned long long man = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = (bexp - 1023) - e + 12;   // x = man 2^(bexp-1075); G = man 2^(sh)
+    if (sh >= 0) G = man << sh;
+    else if (sh > -64) G = (man >> -sh) + ((man >> (-sh - 1)) & 1ull);
   }
+  const bool neg = (bits >> 63) != 0;
+  int dig[SLICES];
+#pragma unroll
+  for (int s = SLICES - 1; s > 0; --s) {
+    int r = (int)(G & 31ull);
+    if (r > 16) r -= 32;
+    dig[s] = r;
+    G = (G - (long long)r) >> 5;
+  }
+  dig[0] = (int)G;
+#pragma unroll
+  for (int s = 0; s < SLICES; ++s) d[s] = __int2bfloat16_rn(neg ? -dig[s] : dig[s]);
 }
 
 // A digits: slice s, row r, columns 2c (Re) and 2c+1 (Im) of the real embedding; the tile is
@@ -340,7 +357,7 @@ __global__ void slice_a_kernel(int M, int K, const cplx* A, long lda, int op, co
     const long r = r0 + i, c = c0 + tx;
     if (r >= mpad || 2 * c >= kpad) continue;
     const cplx v = t[i][tx];
-    const int e = r < M ? rowexp[r] : 0;
+    const int e = (r < M && rowexp[r] > -100000) ? rowexp[r] : 0;
     __nv_bfloat16 dr[SLICES], di[SLICES];
     digits(v.x, e, dr);
     digits(v.y, e, di);
@@ -371,7 +388,7 @@ __global__ void slice_b_kernel(int K, int N, const cplx* B, long ldb, int op, co
     const long j = j0 + i, kk = k0 + tx;
     if (2 * j >= npad || 2 * kk >= kpad) continue;
     const cplx v = t[i][tx];
-    const int e = j < N ? colexp[j] : 0;
+    const int e = (j < N && colexp[j] > -100000) ? colexp[j] : 0;
     __nv_bfloat16 dr[SLICES], di[SLICES];
     digits(v.x, e, dr);
     digits(v.y, e, di);
@@ -480,16 +497,16 @@ cudaError_t ozaki_gemm(OzakiGemm* o, const GemmArgs& g, cudaStream_t s, int* err
   }
   int* rowexp = o->exps;
   int* colexp = o->exps + M;
-  // exponents: rows of op(A); columns of op(B) = rows of op'(B) with the opposite op
-  if (g.opA == OP_N) rowexp_kernel<<<(unsigned)((M + 127) / 128), 128, 0, s>>>((int)M, (int)K, g.A, g.lda, OP_N, rowexp);
-  else rowexp_kernel<<<(unsigned)((M * 32 + 255) / 256), 256, 0, s>>>((int)M, (int)K, g.A, g.lda, OP_C, rowexp);
-  count_launch(1);
-  // column j of op(B): for op N it is column j of B (contiguous) -> the "op C" branch with conj
-  // (magnitudes only matter); for op C it is row j of B -> the "op N" branch
-  if (g.opB == OP_N)
-    rowexp_kernel<<<(unsigned)((N * 32 + 255) / 256), 256, 0, s>>>((int)N, (int)K, g.B, g.ldb, OP_C, colexp);
-  else rowexp_kernel<<<(unsigned)((N + 127) / 128), 128, 0, s>>>((int)N, (int)K, g.B, g.ldb, OP_N, colexp);
-  count_launch(1);
+  // exponents: rows of op(A), columns of op(B) (sentinel 0x80808080 = very negative)
+  if ((e = cudaMemsetAsync(o->exps, 0x80, sizeof(int) * (M + N), s)) != cudaSuccess) return e;
+  {
+    dim3 gA((unsigned)((K + 31) / 32), (unsigned)((M + 31) / 32));
+    exp_tile_kernel<<<gA, 256, 0, s>>>((int)M, (int)K, g.A, g.lda, g.opA, true, rowexp);
+    count_launch(1);
+    dim3 gB((unsigned)((N + 31) / 32), (unsigned)((K + 31) / 32));
+    exp_tile_kernel<<<gB, 256, 0, s>>>((int)K, (int)N, g.B, g.ldb, g.opB, false, colexp);
+    count_launch(1);
+  }
   {
     dim3 ga((unsigned)((kpad / 2 + 31) / 32), (unsigned)(mpad / 32));
     slice_a_kernel<<<ga, 256, 0, s>>>((int)M, (int)K, g.A, g.lda, g.opA, rowexp, mpad, kpad, o->A);

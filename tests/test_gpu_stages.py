@@ -114,7 +114,7 @@ def test_filter_per_vector_degree(ctx):
     assert rel_err(lib.to_numpy(Y), ref) < 1e-11
 
 
-@pytest.mark.parametrize("n,k,nl", [(200, 24, 0), (333, 37, 11), (512, 48, 32)])
+@pytest.mark.parametrize("n,k,nl", [(200, 24, 0), (333, 37, 11), (512, 48, 32), (1000, 240, 16), (1200, 513, 0)])
 def test_orthonormalize(ctx, n, k, nl):
     rng = synth.rng_for(5, n)
     Yl = O2.orthonormalize(None, synth.complex_gaussian(rng, (n, nl))) if nl else None
