@@ -76,6 +76,10 @@ typedef struct {
                               2 filter, 3 QR, 4 Rayleigh-Ritz, 5 residual+locking,
                               6 back-transform, 7 whole call */
   double ms_filter_lowp;   /* part of ms_stage[2] spent in tensor-core (low-precision) filter passes */
+  double ms_gemm_tc;       /* device time of the FP64-accurate tensor-core GEMMs (all stages) */
+  double gemm_tc_flop;     /* their algorithmic work: 8 M N K_eff real flops per complex product */
+  double ms_eig;           /* device time of the reduced eigensolver (Rayleigh-Ritz) */
+  int eig_sweeps;          /* Jacobi sweeps summed over the call */
 } chfsi_info;
 
 /* Fills *p with the defaults listed above. */

@@ -40,13 +40,15 @@ class Info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("locked", ctypes.c_int), ("filter_col_steps", ctypes.c_longlong),
                 ("filter_col_steps_lowp", ctypes.c_longlong), ("max_resid", ctypes.c_double),
                 ("kappa_L", ctypes.c_double), ("bounds", ctypes.c_double * 3), ("ms_stage", ctypes.c_double * 8),
-                ("ms_filter_lowp", ctypes.c_double)]
+                ("ms_filter_lowp", ctypes.c_double), ("ms_gemm_tc", ctypes.c_double),
+                ("gemm_tc_flop", ctypes.c_double), ("ms_eig", ctypes.c_double), ("eig_sweeps", ctypes.c_int)]
 
     def as_dict(self):
         return {"iterations": self.iterations, "locked": self.locked, "filter_col_steps": self.filter_col_steps,
                 "filter_col_steps_lowp": self.filter_col_steps_lowp, "max_resid": self.max_resid,
                 "kappa_L": self.kappa_L, "bounds": list(self.bounds), "ms_stage": list(self.ms_stage),
-                "ms_filter_lowp": self.ms_filter_lowp}
+                "ms_filter_lowp": self.ms_filter_lowp, "ms_gemm_tc": self.ms_gemm_tc,
+                "gemm_tc_flop": self.gemm_tc_flop, "ms_eig": self.ms_eig, "eig_sweeps": self.eig_sweeps}
 
 
 _lib = None

@@ -92,6 +92,19 @@ struct chfsi_ctx {
   double tol = 1e-10, kappa_L = 1.0;
   std::vector<double> block_lam;   // ascending Ritz values of the stored block
   cudaEvent_t ev[16] = {};
+  // per-kernel-family device time: event pairs recorded around each launch, resolved at
+  // the next synchronisation point
+  struct Span {
+    cudaEvent_t a, b;
+    int kind;   // 0 tensor-core GEMM, 1 reduced eigensolver
+    double flop;
+  };
+  std::vector<Span> spans;
+  std::vector<cudaEvent_t> ev_pool;
+  double acc_ms[2] = {0, 0}, acc_flop = 0;
+  int acc_sweeps = 0;
+  int* sweeps_host = nullptr;     // pinned ring of sweep counts copied after each eigensolve
+  int n_sweeps_pending = 0;
 };
 
 namespace {
@@ -127,10 +140,15 @@ chfsi_status ensure_host(chfsi_ctx* c, int k) {
   return CHFSI_OK;
 }
 
+void spans_flush(chfsi_ctx* c);
+
 chfsi_status read_err(chfsi_ctx* c, int* dev_err) {
   int h = 0;
   CU(cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
+  spans_flush(c);
+  for (int q = 0; q < c->n_sweeps_pending && q < 64; ++q) c->acc_sweeps += c->sweeps_host[q];
+  c->n_sweeps_pending = 0;
   *dev_err = h;
   return CHFSI_OK;
 }
@@ -173,13 +191,52 @@ GemmArgs gemm_args(int M, int N, int K, int opA, const cplx* A, long lda, int op
 }
 const cplx ONE = {1.0, 0.0}, ZERO = {0.0, 0.0}, MONE = {-1.0, 0.0};
 
+cudaEvent_t pool_event(chfsi_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+void span_begin(chfsi_ctx* c, int kind, double flop) {
+  chfsi_ctx::Span sp{pool_event(c), pool_event(c), kind, flop};
+  cudaEventRecord(sp.a, c->stream);
+  c->spans.push_back(sp);
+}
+void span_end(chfsi_ctx* c) { cudaEventRecord(c->spans.back().b, c->stream); }
+// call after a stream synchronisation: adds the finished spans to the accumulators
+void spans_flush(chfsi_ctx* c) {
+  for (auto& sp : c->spans) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, sp.a, sp.b) == cudaSuccess) c->acc_ms[sp.kind] += ms;
+    if (sp.kind == 0) c->acc_flop += sp.flop;
+    c->ev_pool.push_back(sp.a);
+    c->ev_pool.push_back(sp.b);
+  }
+  c->spans.clear();
+}
+
+double gemm_flop(const GemmArgs& g) {
+  // algorithmic complex work with the triangular pruning counted as half
+  double f = 8.0 * g.M * g.N * (double)g.K;
+  int tri = 0;
+  if (g.tri & (TRI_A_LOWER | TRI_A_UPPER)) ++tri;
+  if (g.tri & (TRI_B_LOWER | TRI_B_UPPER)) ++tri;
+  return tri ? 0.5 * f : f;
+}
+
 // FP64-accurate product: in mixed-precision mode the large ones run as the error-free digit
 // expansion on the tensor cores (ozaki.cu); otherwise, and for small shapes, on the DFMA pipe.
 chfsi_status gemm64(chfsi_ctx* c, const GemmArgs& g) {
   if (c->prm.precision == CHFSI_PREC_MIXED && g.epi == EPI_GEMM && g.N > 1 && g.M > 1 &&
       (double)g.M * g.N * g.K >= 4.0e6) {
     if (!c->oz) c->oz = ozaki_new();
+    span_begin(c, 0, gemm_flop(g));
     CU(ozaki_gemm(c->oz, g, c->stream, c->d_err));
+    span_end(c);
     return CHFSI_OK;
   }
   return gemm(c, g);
@@ -189,8 +246,17 @@ chfsi_status gemm64(chfsi_ctx* c, const GemmArgs& g) {
 chfsi_status factor_S(chfsi_ctx* c, int n, const cplx* S, cplx* L, cplx* Linv) {
   CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   CU(cudaMemcpyAsync(L, S, sizeof(cplx) * (size_t)n * n, cudaMemcpyDeviceToDevice, c->stream));
-  CU(chol_lower(c->stream, n, L, n, c->d_err));
-  if (Linv) CU(trtri_lower(c->stream, n, L, n, Linv, n, c->d_err));
+  if (n <= CHOL_INV_KMAX) {
+    // one cooperative launch for L and L^{-1} over all SMs
+    cplx* X = Linv;
+    if (!X) TRY(buf(c, "chol_inv_X", (size_t)n * n, &X));
+    char* w;
+    TRY(buf(c, "chol_inv_work", chol_inv_work_bytes(n), &w));
+    CU(chol_inv_small(c->stream, n, L, X, w, c->d_err));
+  } else {
+    CU(chol_lower(c->stream, n, L, n, c->d_err));
+    if (Linv) CU(trtri_lower(c->stream, n, L, n, Linv, n, c->d_err));
+  }
   int e = 0;
   TRY(read_err(c, &e));
   return map_dev_err(e);
@@ -444,7 +510,12 @@ chfsi_status reduced_eig(chfsi_ctx* c, int k, cplx* G, double* lam, cplx* W) {
   char* work;
   TRY(buf(c, "jac_work", jacobi_work_bytes(k), &work));
   CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  span_begin(c, 1, 0.0);
   CU(jacobi_eig(c->stream, k, G, lam, W, work, c->d_err, c->d_sweeps));
+  span_end(c);
+  if (c->n_sweeps_pending < 64)
+    CU(cudaMemcpyAsync(&c->sweeps_host[c->n_sweeps_pending++], c->d_sweeps, sizeof(int), cudaMemcpyDeviceToHost,
+                       c->stream));
   return CHFSI_OK;
 }
 
@@ -582,6 +653,9 @@ chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, 
     tm.mark(5);
     CU(cudaStreamSynchronize(c->stream));
     tm.flush();
+    spans_flush(c);
+    for (int q = 0; q < c->n_sweeps_pending && q < 64; ++q) c->acc_sweeps += c->sweeps_host[q];
+    c->n_sweeps_pending = 0;
     if (h_err != DEV_OK) return map_dev_err(h_err);
     for (int i = 0; i < ka; ++i)
       if (!isfinite(h_res[i]) || !isfinite(h_lam[i])) return CHFSI_ERR_NUMERIC;
@@ -715,6 +789,9 @@ chfsi_status solve_common(chfsi_ctx* c, const cplx* H, const cplx* S, const cplx
   TRY(buf(c, "lz_beta", 256, &be));
   TRY(buf(c, "lz_bounds", 16, &bd));
   if (info) memset(info, 0, sizeof(*info));
+  c->acc_ms[0] = c->acc_ms[1] = 0.0;
+  c->acc_flop = 0.0;
+  c->acc_sweeps = 0;
   cudaEvent_t r0 = c->ev[12], r1 = c->ev[13];
   CU(cudaEventRecord(r0, c->stream));
   if (S) {
@@ -765,12 +842,19 @@ chfsi_status solve_common(chfsi_ctx* c, const cplx* H, const cplx* S, const cplx
   chfsi_status st = iterate(c, Hs, Y, a, b, a0, evals, (cplx*)X, Linv, info, seeded);
   CU(cudaEventRecord(t1, c->stream));
   CU(cudaEventSynchronize(t1));
+  spans_flush(c);
+  for (int q = 0; q < c->n_sweeps_pending && q < 64; ++q) c->acc_sweeps += c->sweeps_host[q];
+  c->n_sweeps_pending = 0;
   if (info) {
     float tot = 0.f;
     cudaEventElapsedTime(&tot, t0, t1);
     info->ms_stage[0] += ms_reduce;
     info->ms_stage[1] += ms_lanczos;
     info->ms_stage[7] = tot;
+    info->ms_gemm_tc = c->acc_ms[0];
+    info->gemm_tc_flop = c->acc_flop;
+    info->ms_eig = c->acc_ms[1];
+    info->eig_sweeps = c->acc_sweeps;
   }
   if (st == CHFSI_OK || st == CHFSI_ERR_NO_CONV) c->have_seq = true;
   return st;
@@ -840,6 +924,7 @@ chfsi_status chfsi_create(chfsi_ctx** out, int device, void* cuda_stream, const 
     s = cu(cudaMemset(c->d_err, 0, 2 * sizeof(int)), "err");
   }
   for (int i = 0; i < 16 && s == CHFSI_OK; ++i) s = cu(cudaEventCreate(&c->ev[i]), "event");
+  if (s == CHFSI_OK) s = cu(cudaMallocHost((void**)&c->sweeps_host, 64 * sizeof(int)), "pinned");
   if (s != CHFSI_OK) {
     chfsi_destroy(c);
     return s;
@@ -861,6 +946,12 @@ void chfsi_destroy(chfsi_ctx* c) {
   if (c->h_i) cudaFreeHost(c->h_i);
   for (int i = 0; i < 16; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  for (auto& sp : c->spans) {
+    cudaEventDestroy(sp.a);
+    cudaEventDestroy(sp.b);
+  }
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  if (c->sweeps_host) cudaFreeHost(c->sweeps_host);
   delete c;
 }
 

@@ -193,8 +193,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // MMA issuer: six slice products per 16-wide K step into one accumulator
-      const int prod_a[6] = {0, 0, 1, 0, 1, 2};
-      const int prod_b[6] = {0, 1, 0, 2, 1, 0};
+      constexpr int prod_a[6] = {0, 0, 1, 0, 1, 2};
+      constexpr int prod_b[6] = {0, 1, 0, 2, 1, 0};
       bool ok = true;
       for (int kb = 0; kb < g.kblocks && ok; ++kb) {
         const int s = kb % STAGES;
@@ -205,16 +205,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t st = base + s * STAGE_BYTES;
+        // base descriptors once per stage; products and K steps are start-address offsets
+        const uint64_t da0 = umma_desc(st), db0 = umma_desc(st + NSLICE * A_TILE);
+        const uint32_t later = kb != 0;
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk) {
 #pragma unroll
           for (int p = 0; p < 6; ++p) {
-            const uint64_t da = umma_desc(st + prod_a[p] * A_TILE + kk * 32);
-            const uint64_t db = umma_desc(st + NSLICE * A_TILE + prod_b[p] * B_TILE + kk * 32);
+            const uint64_t da = da0 + (uint64_t)((prod_a[p] * A_TILE + kk * 32) >> 4);
+            const uint64_t db = db0 + (uint64_t)((prod_b[p] * B_TILE + kk * 32) >> 4);
             // the leading product s = t = 0 and the five corrections accumulate apart: the
             // accumulator's per-instruction truncation then acts on each at its own scale
-            if (p == 0) umma_bf16(tmem, da, db, (kb | kk) != 0);
-            else umma_bf16(tmem + BN, da, db, (kb | kk | (p - 1)) != 0);
+            if (p == 0) umma_bf16(tmem, da, db, (kk != 0) ? 1u : later);
+            else umma_bf16(tmem + BN, da, db, (kk != 0 || p > 1) ? 1u : later);
           }
         }
         umma_commit(empty(s));   // frees the stage once these MMAs have read it

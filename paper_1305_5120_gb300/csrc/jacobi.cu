@@ -151,6 +151,11 @@ struct JacobiFastArgs {
   int max_sweeps;
 };
 
+// Rotation of pair (p, q) from the current 2 x 2 diagonal block.  Only the tangent t is taken
+// in FP32 (an FP64 division/square-root chain costs microseconds on this FP64 pipe): the
+// rotation built from it in FP64 (c = 1/sqrt(1 + t^2), s = t c, unit phase) is unitary to
+// FP64 rounding, so the matrix stays exactly similar; it leaves |a_pq| reduced by ~1e-7
+// instead of zero, which later sweeps remove.
 __device__ __forceinline__ RotS make_rot(const cplx* A, int k, int p, int q, double thresh) {
   RotS R;
   if (p > q) { int t = p; p = q; q = t; }
@@ -158,13 +163,15 @@ __device__ __forceinline__ RotS make_rot(const cplx* A, int k, int p, int q, dou
   R.upp = cmk(1, 0); R.uqq = cmk(1, 0); R.upq = cmk(0, 0); R.uqp = cmk(0, 0);
   if (q < k) {
     const cplx apq = A[p + (long)q * k];
-    const double ar = sqrt(cabs2(apq));
-    if (ar > thresh) {
+    const double ar2 = cabs2(apq);
+    if (ar2 > thresh * thresh) {
+      const double inv_r = rsqrt(ar2);
       const double app = A[p + (long)p * k].x, aqq = A[q + (long)q * k].x;
-      const cplx ph = cmk(apq.x / ar, apq.y / ar);
-      const double tau = (aqq - app) / (2.0 * ar);
-      const double t = (tau < 0.0 ? -1.0 : 1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-      const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+      const cplx ph = cmk(apq.x * inv_r, apq.y * inv_r);
+      const float tau = (float)((aqq - app) * 0.5 * inv_r);
+      const float tf = (tau < 0.f ? -1.f : 1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+      const double t = (double)tf;
+      const double c = rsqrt(1.0 + t * t), sn = t * c;
       R.upp = cmk(c, 0.0);
       R.uqp = cmk(-sn * ph.x, sn * ph.y);
       R.upq = cmk(sn, 0.0);
@@ -217,8 +224,10 @@ __global__ void __launch_bounds__(256) jacobi_fast_kernel(JacobiFastArgs g) {
             b01 = cadd(cmul(cconj(P.upp), t01), cmul(cconj(P.uqp), t11));
             b10 = cadd(cmul(cconj(P.upq), t00), cmul(cconj(P.uqq), t10));
             b11 = cadd(cmul(cconj(P.upq), t01), cmul(cconj(P.uqq), t11));
-            if (e % np == e / np && P.on) {
-              b00.y = 0.0; b11.y = 0.0; b01 = cmk(0, 0); b10 = cmk(0, 0);
+            if (e % np == e / np) {   // diagonal block: keep the diagonal real
+              b00.y = 0.0;
+              b11.y = 0.0;
+              b10 = cconj(b01);
             }
           }
           An[P.p + (long)R.p * k] = b00;

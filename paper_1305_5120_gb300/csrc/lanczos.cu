@@ -64,32 +64,49 @@ __global__ void lanczos_step_kernel(int n, int j, cplx* v, cplx* vp, cplx* w, do
   }
 }
 
-// number of eigenvalues of tridiag(beta, alpha, beta) below x (Sturm sequence / LDL^T pivots)
+// Number of eigenvalues of tridiag(beta, alpha, beta) below x: sign changes of the Sturm
+// sequence p_0 = 1, p_i = (alpha_i - x) p_{i-1} - beta_{i-1}^2 p_{i-2} (no division: FP64
+// division is a long latency chain here); rescaled by 2^-256 when it grows past 2^256.
 __device__ int sturm_count(int m, const double* al, const double* be, double x) {
   int cnt = 0;
-  double q = 1.0;
+  double pm2 = 0.0, pm1 = 1.0;
   for (int i = 0; i < m; ++i) {
-    double b2 = (i > 0) ? be[i - 1] * be[i - 1] : 0.0;
-    q = al[i] - x - ((i > 0) ? b2 / q : 0.0);
-    if (q == 0.0) q = -1e-300;
-    if (q < 0.0) ++cnt;
+    const double b2 = (i > 0) ? be[i - 1] * be[i - 1] : 0.0;
+    double p = (al[i] - x) * pm1 - b2 * pm2;
+    if (p == 0.0) p = -1e-300 * (pm1 < 0.0 ? -1.0 : 1.0);   // a zero takes the sign opposite to p_{i-1}
+    if ((p < 0.0) != (pm1 < 0.0)) ++cnt;
+    pm2 = pm1;
+    pm1 = p;
+    if (fabs(pm1) > 0x1.0p256) {
+      pm1 *= 0x1.0p-256;
+      pm2 *= 0x1.0p-256;
+    }
   }
   return cnt;
 }
 
-// index-th smallest eigenvalue (0-based) by bisection on the Gershgorin interval
-__device__ double tridiag_eig_bisect(int m, const double* al, const double* be, int index) {
+// index-th smallest eigenvalue (0-based) by warp multisection: each step the 32 lanes count
+// at 32 interior points of [lo, hi] and the bracket shrinks 33-fold (the whole warp calls it)
+__device__ double tridiag_eig_multisect(int m, const double* al, const double* be, int index) {
+  const int lane = threadIdx.x & 31;
   double lo = al[0], hi = al[0];
   for (int i = 0; i < m; ++i) {
-    double r = ((i > 0) ? fabs(be[i - 1]) : 0.0) + ((i + 1 < m) ? fabs(be[i]) : 0.0);
+    const double r = ((i > 0) ? fabs(be[i - 1]) : 0.0) + ((i + 1 < m) ? fabs(be[i]) : 0.0);
     lo = fmin(lo, al[i] - r);
     hi = fmax(hi, al[i] + r);
   }
-  for (int it = 0; it < 200; ++it) {
-    double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (sturm_count(m, al, be, mid) <= index) lo = mid;
-    else hi = mid;
+  lo -= 1e-300;
+  for (int it = 0; it < 14; ++it) {
+    const double h = (hi - lo) / 33.0;
+    const double x = lo + h * (lane + 1);
+    const bool below = sturm_count(m, al, be, x) <= index;   // eigenvalue index is >= x
+    const unsigned bal = __ballot_sync(0xffffffffu, below);
+    const int j = __popc(bal);                              // points at or below the eigenvalue
+    const double nlo = (j == 0) ? lo : lo + h * j;
+    const double nhi = (j == 32) ? hi : lo + h * (j + 1);
+    if (!(nhi - nlo < hi - lo)) break;
+    lo = nlo;
+    hi = nhi;
   }
   return 0.5 * (lo + hi);
 }
@@ -110,14 +127,19 @@ __global__ void lanczos_bounds_kernel(int steps, int n, int k, const double* alp
   j += 1;
   if (j > m - 1) j = m - 1;
   if (j < 1) j = 1;
-  if (threadIdx.x == 0) {
-    double mu_max = tridiag_eig_bisect(m, al, be, m - 1);
-    out[0] = mu_max + fabs(be[m - 1]);
-    out[3] = mu_max;
-  } else if (threadIdx.x == 1) {
-    out[1] = tridiag_eig_bisect(m, al, be, j - 1);
-  } else if (threadIdx.x == 2) {
-    out[2] = tridiag_eig_bisect(m, al, be, 0);
+  const int w = threadIdx.x >> 5;   // three warps: mu_max, mu_j, mu_min
+  if (w == 0) {
+    const double mu_max = tridiag_eig_multisect(m, al, be, m - 1);
+    if ((threadIdx.x & 31) == 0) {
+      out[0] = mu_max + fabs(be[m - 1]);
+      out[3] = mu_max;
+    }
+  } else if (w == 1) {
+    const double v = tridiag_eig_multisect(m, al, be, j - 1);
+    if ((threadIdx.x & 31) == 0) out[1] = v;
+  } else if (w == 2) {
+    const double v = tridiag_eig_multisect(m, al, be, 0);
+    if ((threadIdx.x & 31) == 0) out[2] = v;
   }
 }
 
@@ -160,7 +182,7 @@ cudaError_t lanczos_step(cudaStream_t s, int n, int j, cplx* v, cplx* v_prev, cp
 cudaError_t lanczos_bounds(cudaStream_t s, int steps, int n, int k, const double* alpha, const double* beta,
                            double* out) {
   if (steps < 2 || steps > 256) return cudaErrorInvalidValue;
-  lanczos_bounds_kernel<<<1, 32, 0, s>>>(steps, n, k, alpha, beta, out); count_launch();
+  lanczos_bounds_kernel<<<1, 96, 0, s>>>(steps, n, k, alpha, beta, out); count_launch();
   return cudaGetLastError();
 }
 

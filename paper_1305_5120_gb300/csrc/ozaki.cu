@@ -203,12 +203,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!mbar_wait(full(s), ph, g.err)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t st = base + s * STAGE_BYTES;
+        // descriptors differ only in the start-address field (address >> 4), so each product's
+        // descriptor is the stage's base descriptor plus a compile-time offset; the fully
+        // unrolled 91-product sequence then costs a few integer adds per MMA
+        const uint64_t da0 = umma_desc32(st), db0 = umma_desc32(st + SLICES * A_TILE);
+        const uint32_t first = i != 0;
+#pragma unroll
         for (int sa = 0; sa < SLICES; ++sa) {
-          const uint64_t da = umma_desc32(st + sa * A_TILE);
-          for (int tb = 0; tb + sa < LEVELS; ++tb) {
-            const uint64_t db = umma_desc32(st + SLICES * A_TILE + tb * B_TILE);
-            const uint32_t acc = (i | sa) != 0;   // first write of level sa + tb: i == 0, sa == 0
-            umma_bf16(tmem + (uint32_t)((sa + tb) * BN), da, db, acc);
+#pragma unroll
+          for (int tb = 0; tb < LEVELS; ++tb) {
+            if (tb + sa < LEVELS)
+              umma_bf16(tmem + (uint32_t)((sa + tb) * BN), da0 + (uint64_t)((sa * A_TILE) >> 4),
+                        db0 + (uint64_t)((tb * B_TILE) >> 4), sa == 0 ? first : 1u);
           }
         }
         umma_commit(empty(s));
