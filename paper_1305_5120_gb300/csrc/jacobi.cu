@@ -136,7 +136,8 @@ __global__ void __launch_bounds__(256) jacobi_kernel(JacobiArgs g) {
 // without atomics.  Each round reads A_cur and writes every 2 x 2 block of A_next.
 constexpr int JF_MAXPAIRS = 256;
 struct RotS {
-  cplx upp, upq, uqp, uqq;
+  cplx upp, upq, uqp, uqq;   // the 2 x 2 unitary (upp = c, upq = s real; uqp = -s conj(ph), uqq = c conj(ph))
+  cplx phc;                  // conj(ph)
   int p, q, on, pad;
 };
 struct JacobiFastArgs {
@@ -160,7 +161,7 @@ __device__ __forceinline__ RotS make_rot(const cplx* A, int k, int p, int q, dou
   RotS R;
   if (p > q) { int t = p; p = q; q = t; }
   R.p = p; R.q = q; R.on = 0; R.pad = 0;
-  R.upp = cmk(1, 0); R.uqq = cmk(1, 0); R.upq = cmk(0, 0); R.uqp = cmk(0, 0);
+  R.upp = cmk(1, 0); R.uqq = cmk(1, 0); R.upq = cmk(0, 0); R.uqp = cmk(0, 0); R.phc = cmk(1, 0);
   if (q < k) {
     const cplx apq = A[p + (long)q * k];
     const double ar2 = cabs2(apq);
@@ -176,6 +177,7 @@ __device__ __forceinline__ RotS make_rot(const cplx* A, int k, int p, int q, dou
       R.uqp = cmk(-sn * ph.x, sn * ph.y);
       R.upq = cmk(sn, 0.0);
       R.uqq = cmk(c * ph.x, -c * ph.y);
+      R.phc = cmk(ph.x, -ph.y);
       R.on = 1;
     }
   }
@@ -216,14 +218,31 @@ __global__ void __launch_bounds__(256) jacobi_fast_kernel(JacobiFastArgs g) {
           cplx b10 = pq_ok ? Ac[P.q + (long)R.p * k] : cmk(0, 0);
           cplx b11 = (pq_ok && rs_ok) ? Ac[P.q + (long)R.q * k] : cmk(0, 0);
           if (P.on || R.on) {
-            const cplx t00 = cadd(cmul(b00, R.upp), cmul(b01, R.uqp));
-            const cplx t01 = cadd(cmul(b00, R.upq), cmul(b01, R.uqq));
-            const cplx t10 = cadd(cmul(b10, R.upp), cmul(b11, R.uqp));
-            const cplx t11 = cadd(cmul(b10, R.upq), cmul(b11, R.uqq));
-            b00 = cadd(cmul(cconj(P.upp), t00), cmul(cconj(P.uqp), t10));
-            b01 = cadd(cmul(cconj(P.upp), t01), cmul(cconj(P.uqp), t11));
-            b10 = cadd(cmul(cconj(P.upq), t00), cmul(cconj(P.uqq), t10));
-            b11 = cadd(cmul(cconj(P.upq), t01), cmul(cconj(P.uqq), t11));
+            // U = [[c, s], [-s conj(ph), c conj(ph)]] with real c, s: B U costs one complex
+            // product per row (w = b_q1 conj(ph)) plus real scalings, and likewise U^H (B U)
+            const double cR = R.upp.x, sR = R.upq.x, cP = P.upp.x, sP = P.upq.x;
+            const cplx phR = R.phc;
+            cplx t00, t01, t10, t11;
+            if (R.on) {
+              const cplx w0 = cmul(b01, phR), w1 = cmul(b11, phR);   // b_x1 conj(ph_R)
+              t00 = cmk(cR * b00.x - sR * w0.x, cR * b00.y - sR * w0.y);
+              t01 = cmk(sR * b00.x + cR * w0.x, sR * b00.y + cR * w0.y);
+              t10 = cmk(cR * b10.x - sR * w1.x, cR * b10.y - sR * w1.y);
+              t11 = cmk(sR * b10.x + cR * w1.x, sR * b10.y + cR * w1.y);
+            } else {
+              t00 = b00; t01 = b01; t10 = b10; t11 = b11;
+            }
+            if (P.on) {
+              // U_P^H T: rows p, q -> (c t_p - s ph t_q, s t_p + c ph t_q), ph = conj of the stored phase
+              const cplx phP = cconj(P.phc);
+              const cplx v0 = cmul(phP, t10), v1 = cmul(phP, t11);
+              b00 = cmk(cP * t00.x - sP * v0.x, cP * t00.y - sP * v0.y);
+              b01 = cmk(cP * t01.x - sP * v1.x, cP * t01.y - sP * v1.y);
+              b10 = cmk(sP * t00.x + cP * v0.x, sP * t00.y + cP * v0.y);
+              b11 = cmk(sP * t01.x + cP * v1.x, sP * t01.y + cP * v1.y);
+            } else {
+              b00 = t00; b01 = t01; b10 = t10; b11 = t11;
+            }
             if (e % np == e / np) {   // diagonal block: keep the diagonal real
               b00.y = 0.0;
               b11.y = 0.0;
@@ -240,8 +259,10 @@ __global__ void __launch_bounds__(256) jacobi_fast_kernel(JacobiFastArgs g) {
           const RotS R = rot[f / k];
           if (!R.on) continue;
           const cplx x = g.V[i + (long)R.p * k], y = g.V[i + (long)R.q * k];
-          g.V[i + (long)R.p * k] = cadd(cmul(x, R.upp), cmul(y, R.uqp));
-          g.V[i + (long)R.q * k] = cadd(cmul(x, R.upq), cmul(y, R.uqq));
+          const cplx w = cmul(y, R.phc);
+          const double c = R.upp.x, sn = R.upq.x;
+          g.V[i + (long)R.p * k] = cmk(c * x.x - sn * w.x, c * x.y - sn * w.y);
+          g.V[i + (long)R.q * k] = cmk(sn * x.x + c * w.x, sn * x.y + c * w.y);
         }
       }
       if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
@@ -326,7 +347,7 @@ int fast_coop_blocks() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_fast_kernel, 256, 0);
-    cap = std::min(64, sms * std::max(occ, 1));
+    cap = sms * std::min(std::max(occ, 1), 1);
   }
   return cap;
 }

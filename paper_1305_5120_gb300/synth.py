@@ -140,3 +140,37 @@ class Workload:
 SINGLE_N512 = Workload("single n=512 nev=32 nex=16 m=20", 512, 32, 16, 32, 50.0, 1, 20)
 SEQ_N2000 = Workload("sequence n=2000 x20 nev=200 nex=40 m=20", 2000, 200, 40, 200, 80.0, 20, 20)
 SEQ_N13000 = Workload("sequence n=13000 x8 nev=1300 nex=260 m=10..25", 13000, 1300, 260, 1300, 80.0, 8, 20)
+
+
+# Large problems: the same recipe generated on a CUDA device with torch (numpy's QR of an
+# n = 13000 complex matrix takes minutes on host cores).  Inputs only: the factorisations
+# here build the test matrices and are not part of the solver.
+def _torch_haar(n, gen, device):
+    import torch
+    z = (torch.randn(n, n, generator=gen, device=device, dtype=torch.float64)
+         + 1j * torch.randn(n, n, generator=gen, device=device, dtype=torch.float64)) * (0.5 ** 0.5)
+    q, r = torch.linalg.qr(z)
+    d = torch.diagonal(r)
+    return q * (d / d.abs())[None, :]
+
+
+def prescribed_pencil_device(n: int, n_low: int, high: float, seed: int, device="cuda", cond: float = 10.0):
+    """(H, S, lam) as column-major-ready torch tensors on `device` (mathematical
+    orientation, complex128); lam ascending, the exact eigenvalues of the pencil."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed) * 1000003 + 17)
+    v = _torch_haar(n, gen, device)
+    g = torch.from_numpy(semicircle(rng_for(seed, 1), n)).to(device)
+    g[0], g[1] = -1.0, 1.0
+    t = (cond - 1.0) / (cond + 1.0)
+    s = 1.0 + t * g
+    S = (v * s[None, :]) @ v.conj().T
+    S = 0.5 * (S + S.conj().T)
+    M = v * torch.sqrt(s)[None, :]
+    lam = torch.from_numpy(prescribed_spectrum(n, n_low, high, seed)).to(device)
+    q = _torch_haar(n, gen, device)
+    mq = M @ q
+    H = (mq * lam[None, :]) @ mq.conj().T
+    H = 0.5 * (H + H.conj().T)
+    return H, S, lam
