@@ -144,7 +144,8 @@ chfsi_status chfsi_reduce(chfsi_ctx *c, int n, const void *H, const void *L, voi
 
 /* a3. `steps`-step Lanczos on Hermitian Hs from v0 (n vector, normalised internally; NULL =
  * SplitMix64 stream 0 of params.seed).  alpha[steps], beta[steps]: recurrence coefficients
- * (device).  bounds[4] (device): b_sup = max Ritz value + |beta_last| (Algorithm 1 line 1),
+ * (device).  bounds[4] (device): b_sup = max Ritz value + |beta_last| |z_last| (the residual
+ * norm of the top Ritz pair, z its eigenvector of T) + 1e-3 of the Ritz spread (Algorithm 1 line 1),
  * a = first-solve lower end of the damped interval, a0 = smallest Ritz value, max Ritz value.
  * k = block size used for a. */
 chfsi_status chfsi_lanczos(chfsi_ctx *c, int n, const void *Hs, int steps, int k, const void *v0,

@@ -86,13 +86,15 @@ def lanczos(H: np.ndarray, v0: np.ndarray, steps: int):
 
 
 def lanczos_bounds(alpha, beta, n: int, k: int):
-    """(b_sup, a, a0) from a Lanczos run (Zhou & Li 2011 upper bound; first-solve a, a0).
+    """(b_sup, a, a0) from a Lanczos run (first-solve a, a0; upper bound after Zhou & Li 2011).
 
-    b_sup = max Ritz value + |beta_last|; a0 = min Ritz value; a = the j-th smallest Ritz
-    value with j = max(1, ceil(k_L * k / n)) + 1 (1-based), at most k_L - 1."""
-    mu = direct.tridiagonal_eig(np.asarray(alpha), np.asarray(beta[:-1]), vectors=False)
+    b_sup = mu_max + |beta_last| |z_last|: the top Ritz value plus the residual norm of its
+    Ritz pair (z = the eigenvector of T for mu_max), plus a margin of 1e-3 of the Ritz
+    spread; a0 = min Ritz value; a = the j-th smallest Ritz value with
+    j = max(1, ceil(k_L * k / n)) + 1 (1-based), at most k_L - 1."""
+    mu, Z = direct.tridiagonal_eig(np.asarray(alpha), np.asarray(beta[:-1]), vectors=True)
     kl = mu.size
-    b_sup = mu[-1] + abs(beta[-1])
+    b_sup = mu[-1] + abs(beta[-1]) * abs(Z[-1, -1]) + 1e-3 * (mu[-1] - mu[0])
     j = min(max(1, math.ceil(kl * k / n)) + 1, kl - 1)
     return b_sup, mu[max(j - 1, 0)], mu[0]
 

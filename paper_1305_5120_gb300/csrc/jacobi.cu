@@ -152,11 +152,10 @@ struct JacobiFastArgs {
   int max_sweeps;
 };
 
-// Rotation of pair (p, q) from the current 2 x 2 diagonal block.  Only the tangent t is taken
-// in FP32 (an FP64 division/square-root chain costs microseconds on this FP64 pipe): the
-// rotation built from it in FP64 (c = 1/sqrt(1 + t^2), s = t c, unit phase) is unitary to
-// FP64 rounding, so the matrix stays exactly similar; it leaves |a_pq| reduced by ~1e-7
-// instead of zero, which later sweeps remove.
+// Rotation of pair (p, q) from the current 2 x 2 diagonal block.  The tangent t starts in
+// FP32 (an FP64 division/square-root chain costs microseconds on this FP64 pipe) and one FP64
+// Newton step makes it FP64-accurate; the rotation built from it (c = 1/sqrt(1 + t^2),
+// s = t c, unit phase via rsqrt) is unitary to FP64 rounding.
 __device__ __forceinline__ RotS make_rot(const cplx* A, int k, int p, int q, double thresh) {
   RotS R;
   if (p > q) { int t = p; p = q; q = t; }
@@ -169,9 +168,14 @@ __device__ __forceinline__ RotS make_rot(const cplx* A, int k, int p, int q, dou
       const double inv_r = rsqrt(ar2);
       const double app = A[p + (long)p * k].x, aqq = A[q + (long)q * k].x;
       const cplx ph = cmk(apq.x * inv_r, apq.y * inv_r);
-      const float tau = (float)((aqq - app) * 0.5 * inv_r);
+      const double taud = (aqq - app) * 0.5 * inv_r;
+      const float tau = (float)taud;
       const float tf = (tau < 0.f ? -1.f : 1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-      const double t = (double)tf;
+      // one Newton step on t^2 + 2 tau t - 1 = 0 in FP64 (the step's own reciprocal needs only
+      // FP32 accuracy): the tangent becomes FP64-accurate and sweeps converge quadratically
+      double t = (double)tf;
+      const double f = fma(t, t + 2.0 * taud, -1.0);
+      t -= f * (double)(0.5f / (float)(t + taud));
       const double c = rsqrt(1.0 + t * t), sn = t * c;
       R.upp = cmk(c, 0.0);
       R.uqp = cmk(-sn * ph.x, sn * ph.y);

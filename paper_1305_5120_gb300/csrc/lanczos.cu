@@ -131,7 +131,24 @@ __global__ void lanczos_bounds_kernel(int steps, int n, int k, const double* alp
   if (w == 0) {
     const double mu_max = tridiag_eig_multisect(m, al, be, m - 1);
     if ((threadIdx.x & 31) == 0) {
-      out[0] = mu_max + fabs(be[m - 1]);
+      // eigenvector z of T for mu_max by the three-term recurrence
+      //   beta_i z_{i+1} = (mu - alpha_i) z_i - beta_{i-1} z_{i-1},  z_0 = 1,
+      // rescaled when it grows; the bound is mu_max + |beta_last| |z_last| / ||z|| (the
+      // residual norm of the top Ritz pair) plus 1e-3 of the Ritz spread
+      double zm1 = 0.0, z = 1.0, ss = 1.0;
+      for (int i = 0; i + 1 < m; ++i) {
+        double zn = ((mu_max - al[i]) * z - (i > 0 ? be[i - 1] * zm1 : 0.0)) / be[i];
+        zm1 = z;
+        z = zn;
+        ss += z * z;
+        if (ss > 1e200) {
+          zm1 *= 1e-100;
+          z *= 1e-100;
+          ss *= 1e-200;
+        }
+      }
+      const double zlast = fabs(z) / sqrt(ss);
+      out[0] = mu_max + fabs(be[m - 1]) * zlast;
       out[3] = mu_max;
     }
   } else if (w == 1) {
@@ -141,6 +158,9 @@ __global__ void lanczos_bounds_kernel(int steps, int n, int k, const double* alp
     const double v = tridiag_eig_multisect(m, al, be, 0);
     if ((threadIdx.x & 31) == 0) out[2] = v;
   }
+  __syncthreads();
+  __threadfence_block();
+  if (threadIdx.x == 0) out[0] += 1e-3 * (out[3] - out[2]);
 }
 
 __global__ void vector_degrees_kernel(int k, const double* lam, const double* res, double a, double b, double tol,
