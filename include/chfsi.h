@@ -116,6 +116,11 @@ chfsi_status chfsi_solve(chfsi_ctx *c, const void *H, const void *S, int n, int 
 chfsi_status chfsi_next_in_sequence(chfsi_ctx *c, const void *H_next, const void *S_next,
                                     double *evals, void *X, chfsi_info *info);
 
+/* Upper estimate of the device memory (bytes) a context allocates to solve problems of size
+ * (n, nev, nex) in the given precision; callers that admit work by memory budget (the
+ * serving loop) use it.  Inputs and outputs owned by the caller are not included. */
+size_t chfsi_workspace_bytes(int n, int nev, int nex, int precision);
+
 void chfsi_destroy(chfsi_ctx *c);
 const char *chfsi_status_string(chfsi_status s);
 
@@ -146,7 +151,8 @@ chfsi_status chfsi_reduce(chfsi_ctx *c, int n, const void *H, const void *L, voi
  * SplitMix64 stream 0 of params.seed).  alpha[steps], beta[steps]: recurrence coefficients
  * (device).  bounds[4] (device): b_sup = max Ritz value + |beta_last| |z_last| (the residual
  * norm of the top Ritz pair, z its eigenvector of T) + 1e-3 of the Ritz spread (Algorithm 1 line 1),
- * a = first-solve lower end of the damped interval, a0 = smallest Ritz value, max Ritz value.
+ * a = first-solve lower end of the damped interval (the Lanczos density-of-states estimate of
+ * lambda_{k+1}), a0 = smallest Ritz value, max Ritz value.
  * k = block size used for a. */
 chfsi_status chfsi_lanczos(chfsi_ctx *c, int n, const void *Hs, int steps, int k, const void *v0,
                            double *alpha, double *beta, double *bounds);
@@ -194,7 +200,9 @@ chfsi_status chfsi_reduced_eig(chfsi_ctx *c, int k, const void *G, double *lam, 
  * up that array's device address (a one-time set-up with the device current); make that
  * first call before any stream capture.  Every call on a device shares the array and
  * re-initialises it, so calls whose work overlaps on the GPU (other streams, other host
- * threads) race and must be serialised by the caller.  Nothing is allocated or freed. */
+ * threads) race and must be serialised by the caller; the same holds against solves of
+ * other contexts running at that time, since both use grid-wide barriers.  Nothing is
+ * allocated or freed. */
 #define CHFSI_NOALLOC_KMAX 256
 chfsi_status chfsi_reduced_eig_noalloc(void *cuda_stream, int k, const void *G, double *lam, void *W);
 

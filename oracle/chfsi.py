@@ -16,9 +16,11 @@ Readings of the paper used here (each is also listed in the design notes):
   b = max Ritz value + |beta_{k_L}|.
 * The block holds nev + nex vectors; the lower end a of the damped interval is the largest
   Ritz value of the block, a0 (the normalisation point) the smallest.
-* Res(y, lam) is the relative residual ||H y - lam y|| / ||H y||; a pair locks when it is
-  below tol / kappa_L, where kappa_L >= cond_2(L) makes the generalized relative residual
-  ||A x - lam B x|| / ||A x|| <= tol (kappa_L = 1 for a standard problem).
+* Res(y, lam) is the relative residual ||H y - lam y|| / max(||H y||, 1e-4 ||H||) (||H||
+  estimated by max(|a0|, |b|)); a pair locks when it is below tol / kappa_L, where
+  kappa_L >= cond_2(L) makes the generalized relative residual ||A x - lam B x|| / ||A x||
+  <= tol (kappa_L = 1 for a standard problem) for every eigenvalue with |lam| >= 1e-4 ||H||;
+  nearer to zero the test is absolute, since a relative 1e-10 is below FP64's reach there.
 * Locking follows the loop "for i = converged to nev": every active Ritz pair whose global
   index is below nev and whose residual passes is locked, contiguous or not.
 """
@@ -90,13 +92,20 @@ def lanczos_bounds(alpha, beta, n: int, k: int):
 
     b_sup = mu_max + |beta_last| |z_last|: the top Ritz value plus the residual norm of its
     Ritz pair (z = the eigenvector of T for mu_max), plus a margin of 1e-3 of the Ritz
-    spread; a0 = min Ritz value; a = the j-th smallest Ritz value with
-    j = max(1, ceil(k_L * k / n)) + 1 (1-based), at most k_L - 1."""
+    spread; a0 = min Ritz value.  a estimates lambda_{k+1} from the Lanczos density of
+    states: the Ritz values with the squared first components of their eigenvectors of T
+    (the Gauss quadrature of the start vector's spectral measure, which for a random start
+    approximates the eigenvalue distribution) give a cumulative distribution, and a is the
+    first Ritz value (from the second on) whose cumulative weight reaches k / n, at most the
+    second largest."""
     mu, Z = direct.tridiagonal_eig(np.asarray(alpha), np.asarray(beta[:-1]), vectors=True)
     kl = mu.size
     b_sup = mu[-1] + abs(beta[-1]) * abs(Z[-1, -1]) + 1e-3 * (mu[-1] - mu[0])
-    j = min(max(1, math.ceil(kl * k / n)) + 1, kl - 1)
-    return b_sup, mu[max(j - 1, 0)], mu[0]
+    cdf = np.cumsum(Z[0, :] ** 2)
+    j = 1
+    while j < kl - 2 and cdf[j] < k / n:
+        j += 1
+    return b_sup, mu[j], mu[0]
 
 
 # --- Algorithm 1, line "Filtering the vectors" (Chebyshev filter, Eq. (3term)) -------------
@@ -231,6 +240,7 @@ def chfsi(H: np.ndarray, nev: int, nex: int, Y0: np.ndarray, tol: float, degree:
     else:
         a0, a = prev_bounds
         a0 = min(a0, a0_l)
+    a0_init = a0
     tol_lock = tol / kappa_L
 
     Y_locked = np.zeros((n, 0), dtype=np.complex128)
@@ -254,7 +264,10 @@ def chfsi(H: np.ndarray, nev: int, nex: int, Y0: np.ndarray, tol: float, degree:
         Q = orthonormalize(Y_locked if Y_locked.shape[1] else None, Y)
         # Lines 5-7: Rayleigh-Ritz
         lam, Y, Z = rayleigh_ritz(H, Q)
-        res = residual_norms(Z, Y, lam) / np.maximum(np.linalg.norm(Z, axis=0), np.finfo(float).tiny)
+        # relative to max(||H y||, 1e-4 ||H||): absolute for eigenvalues near 0, where a relative
+        # residual of tol would lie below FP64's reach
+        floor = 1e-4 * max(abs(a0_init), abs(b_sup))
+        res = residual_norms(Z, Y, lam) / np.maximum(np.linalg.norm(Z, axis=0), floor)
         # Lines 8-12: deflation and locking, i = converged .. nev
         nl = Y_locked.shape[1]
         lock = np.zeros(Y.shape[1], dtype=bool)

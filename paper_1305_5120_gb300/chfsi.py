@@ -64,6 +64,7 @@ _SIGS = {
     "chfsi_destroy": [_P],
     "chfsi_status_string": [_I],
     "chfsi_kernel_launches": [],
+    "chfsi_workspace_bytes": [_I, _I, _I, _I],
     "chfsi_gemm": [_P, ctypes.c_char, ctypes.c_char, _I, _I, _I, ctypes.POINTER(_D), _P, _I, _P, _I,
                    ctypes.POINTER(_D), _P, _I, _I],
     "chfsi_cholesky": [_P, _I, _P, _P],
@@ -84,6 +85,10 @@ _SIGS = {
 
 def kernel_launches() -> int:
     return int(load().chfsi_kernel_launches())
+
+
+def workspace_bytes(n, nev, nex, precision=CHFSI_PREC_MIXED) -> int:
+    return int(load().chfsi_workspace_bytes(n, nev, nex, precision))
 
 
 def exported_names():
@@ -107,7 +112,8 @@ def load(build_if_missing: bool = True):
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = {"chfsi_status_string": ctypes.c_char_p, "chfsi_destroy": None,
-                     "chfsi_kernel_launches": ctypes.c_ulonglong}.get(name, _I)
+                     "chfsi_kernel_launches": ctypes.c_ulonglong,
+                     "chfsi_workspace_bytes": ctypes.c_size_t}.get(name, _I)
     _lib = lib
     return lib
 

@@ -116,3 +116,10 @@ chfsi_status chfsi_cuda_error(cudaError_t e, const char* what);
 
 // Number of kernels this library has launched (process-wide); chfsi_kernel_launches() reads it.
 void count_launch(unsigned long long n = 1);
+
+// Cooperative launch serialised against every other cooperative launch of this library on
+// the device (an event chain across streams): kernels whose blocks wait on one another at a
+// grid barrier must never share the device with another such kernel, or each could hold
+// SMs the other's unscheduled blocks need.
+cudaError_t coop_launch(const void* fn, dim3 grid, dim3 block, void** args, cudaStream_t s);
+cudaError_t coop_launch_smem(const void* fn, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t s);

@@ -141,7 +141,7 @@ __global__ void gather_values_kernel(int cnt, const int* perm, const double* src
 }
 
 __global__ void residual_kernel(int n, const cplx* Z, long ldz, const cplx* Y, long ldy, const double* lam,
-                                double* res, double* resabs) {
+                                double* res, double* resabs, double floor) {
   __shared__ double sh[32];
   const int j = blockIdx.x;
   const double l = lam[j];
@@ -157,7 +157,7 @@ __global__ void residual_kernel(int n, const cplx* Z, long ldz, const cplx* Y, l
   if (threadIdx.x == 0) {
     double a = sqrt(num), b = sqrt(den);
     resabs[j] = a;
-    res[j] = a / fmax(b, 1e-300);
+    res[j] = a / fmax(fmax(b, floor), 1e-300);
   }
 }
 
@@ -277,9 +277,9 @@ cudaError_t gather_values(cudaStream_t s, int cnt, const int* perm, const double
 }
 
 cudaError_t residual_norms(cudaStream_t s, int n, int k, const cplx* Z, long ldz, const cplx* Y, long ldy,
-                           const double* lam, double* res, double* resabs) {
+                           const double* lam, double* res, double* resabs, double floor) {
   if (k <= 0) return cudaSuccess;
-  residual_kernel<<<k, 256, 0, s>>>(n, Z, ldz, Y, ldy, lam, res, resabs); count_launch();
+  residual_kernel<<<k, 256, 0, s>>>(n, Z, ldz, Y, ldy, lam, res, resabs, floor); count_launch();
   return cudaGetLastError();
 }
 
@@ -481,7 +481,7 @@ cudaError_t chol_inv_small(cudaStream_t s, int k, cplx* A, cplx* X, void* work, 
   if (e == cudaSuccess) e = cudaMemsetAsync(X, 0, sizeof(cplx) * (size_t)k * k, s);
   if (e != cudaSuccess) return e;
   void* args[] = {&g};
-  e = cudaLaunchCooperativeKernel((const void*)chol_inv_kernel, dim3(chol_inv_blocks()), dim3(256), args, 0, s);
+  e = coop_launch((const void*)chol_inv_kernel, dim3(chol_inv_blocks()), dim3(256), args, s);
   count_launch();
   return e;
 }

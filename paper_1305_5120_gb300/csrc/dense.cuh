@@ -14,9 +14,10 @@ cudaError_t hermitize(cudaStream_t s, int n, cplx* A, long lda);
 cudaError_t gather_columns(cudaStream_t s, int n, int cnt, const int* perm, const cplx* src, long lds,
                            cplx* dst, long ldd);
 cudaError_t gather_values(cudaStream_t s, int cnt, const int* perm, const double* src, double* dst);
-// Column-wise relative residuals res[j] = ||Z_j - lam_j Y_j|| / ||Z_j||, and abs[j] the numerator.
+// Column-wise relative residuals res[j] = ||Z_j - lam_j Y_j|| / max(||Z_j||, floor), and abs[j]
+// the numerator.
 cudaError_t residual_norms(cudaStream_t s, int n, int k, const cplx* Z, long ldz, const cplx* Y, long ldy,
-                           const double* lam, double* res, double* resabs);
+                           const double* lam, double* res, double* resabs, double floor = 0.0);
 // lam[j] = Re(Y_j^H Z_j) (Rayleigh quotients when Z = H Y and ||Y_j|| = 1).
 cudaError_t rayleigh_quotients(cudaStream_t s, int n, int k, const cplx* Y, long ldy, const cplx* Z, long ldz,
                                double* lam);

@@ -129,12 +129,12 @@ __global__ void __launch_bounds__(256) jacobi_kernel(JacobiArgs g) {
   }
 }
 
-// One barrier per round (k <= 2 * JF_MAXPAIRS): A is double-buffered, and every CTA derives
+// One barrier per round (k <= 2 * JF_MAXPAIRS = 2048): A is double-buffered, and every CTA derives
 // all rotations of the round from the current buffer's diagonal blocks into shared memory
 // (identical in every CTA), so the rotation table needs no grid-wide publication.  All CTAs
 // also count the round's rotations identically, which gives a consistent convergence test
 // without atomics.  Each round reads A_cur and writes every 2 x 2 block of A_next.
-constexpr int JF_MAXPAIRS = 256;
+constexpr int JF_MAXPAIRS = 1024;
 struct RotS {
   cplx upp, upq, uqp, uqq;   // the 2 x 2 unitary (upp = c, upq = s real; uqp = -s conj(ph), uqq = c conj(ph))
   cplx phc;                  // conj(ph)
@@ -189,7 +189,7 @@ __device__ __forceinline__ RotS make_rot(const cplx* A, int k, int p, int q, dou
 }
 
 __global__ void __launch_bounds__(256) jacobi_fast_kernel(JacobiFastArgs g) {
-  __shared__ RotS rot[JF_MAXPAIRS];
+  extern __shared__ RotS rot[];   // kk / 2 rotations of the round
   __shared__ int s_on;
   const int k = g.k, kk = g.kk, np = kk / 2;
   const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -350,7 +350,9 @@ int fast_coop_blocks() {
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_fast_kernel, 256, 0);
+    cudaFuncSetAttribute(jacobi_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(RotS) * JF_MAXPAIRS));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_fast_kernel, 256, sizeof(RotS) * JF_MAXPAIRS);
     cap = sms * std::min(std::max(occ, 1), 1);
   }
   return cap;
@@ -385,7 +387,8 @@ cudaError_t jacobi_eig(cudaStream_t s, int k, cplx* G, double* lam, cplx* W, voi
     fro_kernel<<<1, 1024, 0, s>>>(k, G, g.fro);
     count_launch();
     void* args[] = {&g};
-    e = cudaLaunchCooperativeKernel((const void*)jacobi_fast_kernel, dim3(fast_coop_blocks()), dim3(256), args, 0, s);
+    e = coop_launch_smem((const void*)jacobi_fast_kernel, dim3(fast_coop_blocks()), dim3(256), args,
+                         sizeof(RotS) * (size_t)(kk / 2), s);
     count_launch();
     if (e != cudaSuccess) return e;
     jacobi_sort_pick_kernel<<<k < 1024 ? k : 1024, 128, 0, s>>>(k, g.A[0], g.A[1], g.final_buf, (const cplx*)g.V, lam,
@@ -419,7 +422,7 @@ cudaError_t jacobi_eig(cudaStream_t s, int k, cplx* G, double* lam, cplx* W, voi
   const long work_items = (long)(kk / 2) * (kk / 2) + (long)k * (kk / 2);
   int blocks = coop_blocks((int)((work_items + 255) / 256));
   void* args[] = {&g};
-  e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(blocks), dim3(256), args, 0, s);
+  e = coop_launch((const void*)jacobi_kernel, dim3(blocks), dim3(256), args, s);
   count_launch();
   if (e != cudaSuccess) return e;
   jacobi_sort_kernel<<<k < 1024 ? k : 1024, 128, 0, s>>>(k, G, (const cplx*)g.V, lam, W); count_launch();

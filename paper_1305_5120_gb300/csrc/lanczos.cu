@@ -113,54 +113,71 @@ __device__ double tridiag_eig_multisect(int m, const double* al, const double* b
 
 __global__ void lanczos_bounds_kernel(int steps, int n, int k, const double* alpha, const double* beta,
                                       double* out) {
-  __shared__ double al[256], be[256];
+  __shared__ double al[256], be[256], mu[256], th[256], w[256];
   const int m = steps;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     al[i] = alpha[i];
     be[i] = beta[i];
   }
   __syncthreads();
-  // j = max(1, ceil(m k / n)) + 1 (1-based), at most m - 1
-  long prod = (long)m * k;
-  int j = (int)((prod + n - 1) / n);
-  if (j < 1) j = 1;
-  j += 1;
-  if (j > m - 1) j = m - 1;
-  if (j < 1) j = 1;
-  const int w = threadIdx.x >> 5;   // three warps: mu_max, mu_j, mu_min
-  if (w == 0) {
-    const double mu_max = tridiag_eig_multisect(m, al, be, m - 1);
-    if ((threadIdx.x & 31) == 0) {
-      // eigenvector z of T for mu_max by the three-term recurrence
-      //   beta_i z_{i+1} = (mu - alpha_i) z_i - beta_{i-1} z_{i-1},  z_0 = 1,
-      // rescaled when it grows; the bound is mu_max + |beta_last| |z_last| / ||z|| (the
-      // residual norm of the top Ritz pair) plus 1e-3 of the Ritz spread
-      double zm1 = 0.0, z = 1.0, ss = 1.0;
-      for (int i = 0; i + 1 < m; ++i) {
-        double zn = ((mu_max - al[i]) * z - (i > 0 ? be[i - 1] * zm1 : 0.0)) / be[i];
-        zm1 = z;
-        z = zn;
-        ss += z * z;
-        if (ss > 1e200) {
-          zm1 *= 1e-100;
-          z *= 1e-100;
-          ss *= 1e-200;
-        }
-      }
-      const double zlast = fabs(z) / sqrt(ss);
-      out[0] = mu_max + fabs(be[m - 1]) * zlast;
-      out[3] = mu_max;
+  // all Ritz values (eigenvalues of T) and the eigenvalues of its trailing block T(2:m, 2:m),
+  // one warp per eigenvalue
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
+  for (int idx = warp; idx < 2 * m - 1; idx += nw) {
+    if (idx < m) {
+      const double v = tridiag_eig_multisect(m, al, be, idx);
+      if (lane == 0) mu[idx] = v;
+    } else {
+      const double v = tridiag_eig_multisect(m - 1, al + 1, be + 1, idx - m);
+      if (lane == 0) th[idx - m] = v;
     }
-  } else if (w == 1) {
-    const double v = tridiag_eig_multisect(m, al, be, j - 1);
-    if ((threadIdx.x & 31) == 0) out[1] = v;
-  } else if (w == 2) {
-    const double v = tridiag_eig_multisect(m, al, be, 0);
-    if ((threadIdx.x & 31) == 0) out[2] = v;
   }
   __syncthreads();
-  __threadfence_block();
-  if (threadIdx.x == 0) out[0] += 1e-3 * (out[3] - out[2]);
+  // Gauss weights w_i = z_1(mu_i)^2 = prod_j (mu_i - theta_j) / prod_{j != i} (mu_i - mu_j)
+  // (the squared first component of the i-th eigenvector of T, from the interlacing
+  // eigenvalues of the trailing block; positive by interlacing)
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    double lg = 0.0;
+    for (int j = 0; j < m - 1; ++j) lg += log(fabs(mu[i] - th[j]) + 1e-300);
+    for (int j = 0; j < m; ++j)
+      if (j != i) lg -= log(fabs(mu[i] - mu[j]) + 1e-300);
+    w[i] = exp(lg);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double mu_max = mu[m - 1], mu_min = mu[0];
+    // eigenvector z of T for mu_max by the three-term recurrence
+    //   beta_i z_{i+1} = (mu - alpha_i) z_i - beta_{i-1} z_{i-1},  z_0 = 1 (rescaled when it
+    // grows); the bound is mu_max + |beta_last| |z_last| / ||z|| (the residual norm of the
+    // top Ritz pair) plus 1e-3 of the Ritz spread
+    double zm1 = 0.0, z = 1.0, ss = 1.0;
+    for (int i = 0; i + 1 < m; ++i) {
+      const double zn = ((mu_max - al[i]) * z - (i > 0 ? be[i - 1] * zm1 : 0.0)) / be[i];
+      zm1 = z;
+      z = zn;
+      ss += z * z;
+      if (ss > 1e200) {
+        zm1 *= 1e-100;
+        z *= 1e-100;
+        ss *= 1e-200;
+      }
+    }
+    out[0] = mu_max + fabs(be[m - 1]) * fabs(z) / sqrt(ss) + 1e-3 * (mu_max - mu_min);
+    out[3] = mu_max;
+    out[2] = mu_min;
+    // first-solve a: the first Ritz value (from the second on) whose cumulative Gauss weight
+    // reaches k / n -- the Lanczos density-of-states estimate of lambda_{k+1}
+    double tot = 0.0;
+    for (int i = 0; i < m; ++i) tot += w[i];
+    const double target = (double)k / (double)n * tot;
+    double cdf = w[0] + w[1];
+    int j = 1;
+    while (j < m - 2 && cdf < target) {
+      ++j;
+      cdf += w[j];
+    }
+    out[1] = mu[j];
+  }
 }
 
 __global__ void vector_degrees_kernel(int k, const double* lam, const double* res, double a, double b, double tol,
@@ -202,7 +219,7 @@ cudaError_t lanczos_step(cudaStream_t s, int n, int j, cplx* v, cplx* v_prev, cp
 cudaError_t lanczos_bounds(cudaStream_t s, int steps, int n, int k, const double* alpha, const double* beta,
                            double* out) {
   if (steps < 2 || steps > 256) return cudaErrorInvalidValue;
-  lanczos_bounds_kernel<<<1, 96, 0, s>>>(steps, n, k, alpha, beta, out); count_launch();
+  lanczos_bounds_kernel<<<1, 1024, 0, s>>>(steps, n, k, alpha, beta, out); count_launch();
   return cudaGetLastError();
 }
 

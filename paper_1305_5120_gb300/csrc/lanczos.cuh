@@ -11,9 +11,10 @@ cudaError_t normalize_vec(cudaStream_t s, int n, cplx* v);
 // w -= alpha_j v + beta_{j-1} v_prev; beta_j = ||w||; v_prev <- v; v <- w / beta_j.
 cudaError_t lanczos_step(cudaStream_t s, int n, int j, cplx* v, cplx* v_prev, cplx* w, double* alpha,
                          double* beta);
-// From T = tridiag(beta, alpha, beta) of `steps` steps: out[0] = b_sup = mu_max + |beta_last|,
-// out[1] = a = mu_j (j = max(1, ceil(steps*k/n)) + 1, 1-based, at most steps-1), out[2] = a0 = mu_min,
-// out[3] = mu_max.  Eigenvalues of T by Sturm-count bisection.
+// From T = tridiag(beta, alpha, beta) of `steps` steps: out[0] = b_sup = mu_max + |beta_last| |z_last|
+// + 1e-3 (mu_max - mu_min); out[1] = a, the Lanczos density-of-states estimate of lambda_{k+1}
+// (first Ritz value from the second on whose cumulative Gauss weight reaches k / n);
+// out[2] = a0 = mu_min; out[3] = mu_max.  Eigenvalues of T by Sturm-count multisection.
 cudaError_t lanczos_bounds(cudaStream_t s, int steps, int n, int k, const double* alpha, const double* beta,
                            double* out);
 // m_i = clamp(ceil(ln(tol / r_i) / ln(rho_i)), m_min, m_max), rho_i = 1 / (|t_i| + sqrt(t_i^2 - 1)),
