@@ -314,14 +314,88 @@ struct CholInvArgs {
   cplx* A;
   cplx* X;
   cplx* Dinv;        // nb blocks of NB x NB: inverses of the diagonal blocks
+  cplx* Tmp;         // NB x k staging of one block row of X
   GridBarrier bar;
   int* err;
   int* fail;
 };
 
+// On this GPU a dependent FP64 FMA costs 64 cycles and an FP64 division or square root
+// 400-700, so every serial chain below is kept short: one rsqrt per pivot (no division),
+// computed redundantly by all threads; dot products split over eight accumulators.
+constexpr int ACC = 8;
+
+// The w x w (w <= 32) diagonal block at (j0, j0), by one CTA of 256 threads in shared memory:
+// L (lower) into A, L^{-1} into X's diagonal block and into Dinv.
+__device__ void diag_factor_cta(cplx* A, cplx* X, cplx* Dinv, int k, int j0, int w, int* fail, int* err,
+                                cplx (*T)[NB + 1], cplx (*Ti)[NB + 1], double* invd, int* bad) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < w * w; e += blockDim.x) {
+    const int r = e % w, c = e / w;
+    T[r][c] = A[(j0 + r) + (long)(j0 + c) * k];
+  }
+  if (tid == 0) *bad = 0;
+  __syncthreads();
+  for (int c = 0; c < w; ++c) {
+    const double p = T[c][c].x;   // every thread reads the pivot and takes its rsqrt
+    const bool ok = p > 0.0 && isfinite(p);
+    const double inv = ok ? rsqrt(p) : 1.0;
+    __syncthreads();
+    if (!ok) {
+      if (tid == 0) *bad = 1;
+      break;
+    }
+    if (tid == 0) {
+      T[c][c] = cmk(p * inv, 0.0);
+      invd[c] = inv;
+    }
+    for (int r = c + 1 + tid; r < w; r += blockDim.x) T[r][c] = cscale(T[r][c], inv);
+    __syncthreads();
+    const int m = w - c - 1;
+    for (int e = tid; e < m * m; e += blockDim.x) {
+      const int r = c + 1 + e % m, q = c + 1 + e / m;
+      if (r >= q) T[r][q] = csub(T[r][q], cmulc(T[r][c], T[q][c]));
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (*bad) {
+    if (tid == 0) {
+      *fail = 1;
+      atomicExch(err, DEV_ERR_NOT_HPD);
+    }
+    return;
+  }
+  // Ti = T^{-1} row by row: Ti[r][c] = (delta_rc - sum_{c<=q<r} T[r][q] Ti[q][c]) invd[r];
+  // 8 threads per column split the sum (shuffle reduction), 32 columns per pass
+  const int c = tid >> 3, part = tid & 7;
+  for (int r = 0; r < w; ++r) {
+    cplx sacc = cmk(0.0, 0.0);
+    if (c < w)
+      for (int q = c + part; q < r; q += 8) sacc = cadd(sacc, cmul(T[r][q], Ti[q][c]));
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+      sacc.x += __shfl_xor_sync(0xffffffffu, sacc.x, o);
+      sacc.y += __shfl_xor_sync(0xffffffffu, sacc.y, o);
+    }
+    if (part == 0 && c < w) {
+      const double d = (r == c) ? 1.0 : 0.0;
+      Ti[r][c] = (r < c) ? cmk(0.0, 0.0) : cmk((d - sacc.x) * invd[r], -sacc.y * invd[r]);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < w * w; e += blockDim.x) {
+    const int r = e % w, cc = e / w;
+    A[(j0 + r) + (long)(j0 + cc) * k] = (r >= cc) ? T[r][cc] : cmk(0.0, 0.0);
+    X[(j0 + r) + (long)(j0 + cc) * k] = Ti[r][cc];
+    Dinv[r + cc * NB] = Ti[r][cc];
+  }
+}
+
 __global__ void __launch_bounds__(256) chol_inv_kernel(CholInvArgs g) {
   __shared__ cplx T[NB][NB + 1];
   __shared__ cplx Ti[NB][NB + 1];
+  __shared__ double invd[NB];
   __shared__ int bad;
   const int k = g.k, nb = (k + NB - 1) / NB;
   const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -330,57 +404,12 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(CholInvArgs g) {
   const long wid = tid >> 5, nwarps = nth >> 5;
   for (int jb = 0; jb < nb; ++jb) {
     const int j0 = jb * NB, w = min(NB, k - j0);
-    if (blockIdx.x == 0) {
-      for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-        const int r = e % w, c = e / w;
-        T[r][c] = g.A[(j0 + r) + (long)(j0 + c) * k];
-        Ti[r][c] = cmk(r == c ? 1.0 : 0.0, 0.0);
-      }
-      if (threadIdx.x == 0) bad = 0;
-      __syncthreads();
-      for (int c = 0; c < w; ++c) {
-        if (threadIdx.x == 0) {
-          const double p = T[c][c].x;
-          if (!(p > 0.0) || !isfinite(p)) bad = 1;
-          else T[c][c] = cmk(sqrt(p), 0.0);
-        }
-        __syncthreads();
-        if (bad) break;
-        const double inv = 1.0 / T[c][c].x;
-        for (int r = c + 1 + threadIdx.x; r < w; r += blockDim.x) T[r][c] = cscale(T[r][c], inv);
-        __syncthreads();
-        const int m = w - c - 1;
-        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-          const int r = c + 1 + e % m, q = c + 1 + e / m;
-          if (r >= q) T[r][q] = csub(T[r][q], cmulc(T[r][c], T[q][c]));
-        }
-        __syncthreads();
-      }
-      if (!bad) {
-        // Ti = T^{-1}: column c by forward substitution (one thread per column)
-        if (threadIdx.x < w) {
-          const int c = threadIdx.x;
-          for (int r = 0; r < w; ++r) {
-            cplx s = cmk(r == c ? 1.0 : 0.0, 0.0);
-            for (int q = c; q < r; ++q) s = csub(s, cmul(T[r][q], Ti[q][c]));
-            Ti[r][c] = (r < c) ? cmk(0.0, 0.0) : cscale(s, 1.0 / T[r][r].x);
-          }
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-          const int r = e % w, c = e / w;
-          g.A[(j0 + r) + (long)(j0 + c) * k] = (r >= c) ? T[r][c] : cmk(0.0, 0.0);
-          g.X[(j0 + r) + (long)(j0 + c) * k] = Ti[r][c];
-          g.Dinv[(long)jb * NB * NB + r + c * NB] = Ti[r][c];
-        }
-      } else if (threadIdx.x == 0) {
-        *g.fail = 1;
-        atomicExch(g.err, DEV_ERR_NOT_HPD);
-      }
-    }
+    if (blockIdx.x == 0)
+      diag_factor_cta(g.A, g.X, g.Dinv + (long)jb * NB * NB, k, j0, w, g.fail, g.err, T, Ti, invd, &bad);
     if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
     if (*(volatile int*)g.fail) return;
-    // panel: rows below, L[r, j0+c] = sum_q A[r, j0+q] conj(Ti[c][q])  (one warp per row)
+    // panel: rows below, L[r, j0+c] = sum_q A[r, j0+q] conj(Ti[c][q])  (one warp per row,
+    // lane c; eight interleaved accumulators)
     for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
       const int r = e % w, c = e / w;
       Ti[r][c] = g.Dinv[(long)jb * NB * NB + r + c * NB];
@@ -388,14 +417,19 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(CholInvArgs g) {
     __syncthreads();
     for (long row = j0 + w + wid; row < k; row += nwarps) {
       const cplx a = lane < w ? g.A[row + (long)(j0 + lane) * k] : cmk(0.0, 0.0);
-      cplx x = cmk(0.0, 0.0);
-      for (int q = 0; q < w; ++q) {
+      cplx acc[ACC];
+#pragma unroll
+      for (int t = 0; t < ACC; ++t) acc[t] = cmk(0.0, 0.0);
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
         cplx aq;
         aq.x = __shfl_sync(0xffffffffu, a.x, q);
         aq.y = __shfl_sync(0xffffffffu, a.y, q);
-        if (lane < w && q <= lane) x = cadd(x, cmulc(aq, Ti[lane][q]));
+        if (lane < w && q <= lane) acc[q % ACC] = cadd(acc[q % ACC], cmulc(aq, Ti[lane][q]));
       }
-      if (lane < w) g.A[row + (long)(j0 + lane) * k] = x;
+#pragma unroll
+      for (int t = 1; t < ACC; ++t) acc[0] = cadd(acc[0], acc[t]);
+      if (lane < w) g.A[row + (long)(j0 + lane) * k] = acc[0];
     }
     if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
     // trailing update of the lower triangle
@@ -403,9 +437,15 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(CholInvArgs g) {
     for (long e = tid; e < (long)m * m; e += nth) {
       const int r = t0 + (int)(e % m), c = t0 + (int)(e / m);
       if (r < c) continue;
-      cplx s = g.A[r + (long)c * k];
-      for (int q = 0; q < w; ++q) s = csub(s, cmulc(g.A[r + (long)(j0 + q) * k], g.A[c + (long)(j0 + q) * k]));
-      g.A[r + (long)c * k] = s;
+      cplx acc[ACC];
+#pragma unroll
+      for (int t = 0; t < ACC; ++t) acc[t] = cmk(0.0, 0.0);
+#pragma unroll
+      for (int q = 0; q < NB; ++q)
+        if (q < w) acc[q % ACC] = cadd(acc[q % ACC], cmulc(g.A[r + (long)(j0 + q) * k], g.A[c + (long)(j0 + q) * k]));
+#pragma unroll
+      for (int t = 1; t < ACC; ++t) acc[0] = cadd(acc[0], acc[t]);
+      g.A[r + (long)c * k] = csub(g.A[r + (long)c * k], acc[0]);
     }
     if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
   }
@@ -419,9 +459,19 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(CholInvArgs g) {
     const int i0 = ib * NB, w = min(NB, k - i0);
     for (long e = tid; e < (long)w * i0; e += nth) {
       const int r = (int)(e % w), c = (int)(e / w);
-      cplx s = cmk(0.0, 0.0);
-      for (int q = c; q < i0; ++q) s = cadd(s, cmul(g.A[(i0 + r) + (long)q * k], g.X[q + (long)c * k]));
-      g.X[(i0 + r) + (long)c * k] = s;
+      cplx acc[ACC];
+#pragma unroll
+      for (int t = 0; t < ACC; ++t) acc[t] = cmk(0.0, 0.0);
+      int q = c;
+      for (; q + ACC <= i0; q += ACC) {
+#pragma unroll
+        for (int t = 0; t < ACC; ++t)
+          acc[t] = cadd(acc[t], cmul(g.A[(i0 + r) + (long)(q + t) * k], g.X[(q + t) + (long)c * k]));
+      }
+      for (; q < i0; ++q) acc[0] = cadd(acc[0], cmul(g.A[(i0 + r) + (long)q * k], g.X[q + (long)c * k]));
+#pragma unroll
+      for (int t = 1; t < ACC; ++t) acc[0] = cadd(acc[0], acc[t]);
+      g.X[(i0 + r) + (long)c * k] = acc[0];
     }
     if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
     for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
@@ -429,17 +479,26 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(CholInvArgs g) {
       Ti[r][c] = g.Dinv[(long)ib * NB * NB + r + c * NB];
     }
     __syncthreads();
-    for (long c = tid; c < i0; c += nth) {
-      cplx t[NB];
+    // X(i0 + r, c) = -sum_{q<=r} Ti[r][q] T(q, c): one thread per (r, c), eight accumulators
+    for (long e = tid; e < (long)w * i0; e += nth) {
+      const int r = (int)(e % w);
+      const long c = e / w;
+      cplx acc[ACC];
 #pragma unroll
-      for (int q = 0; q < NB; ++q) t[q] = q < w ? g.X[(i0 + q) + c * k] : cmk(0.0, 0.0);
+      for (int t = 0; t < ACC; ++t) acc[t] = cmk(0.0, 0.0);
 #pragma unroll
-      for (int r = 0; r < NB; ++r) {
-        if (r >= w) break;
-        cplx s = cmk(0.0, 0.0);
-        for (int q = 0; q <= r; ++q) s = cadd(s, cmul(Ti[r][q], t[q]));
-        g.X[(i0 + r) + c * k] = cmk(-s.x, -s.y);
-      }
+      for (int q = 0; q < NB; ++q)
+        if (q <= r) acc[q % ACC] = cadd(acc[q % ACC], cmul(Ti[r][q], g.X[(i0 + q) + c * k]));
+#pragma unroll
+      for (int t = 1; t < ACC; ++t) acc[0] = cadd(acc[0], acc[t]);
+      g.Tmp[(long)r + c * NB] = acc[0];
+    }
+    if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
+    for (long e = tid; e < (long)w * i0; e += nth) {
+      const int r = (int)(e % w);
+      const long c = e / w;
+      const cplx v = g.Tmp[(long)r + c * NB];
+      g.X[(i0 + r) + c * k] = cmk(-v.x, -v.y);
     }
     if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
   }
@@ -460,7 +519,7 @@ int chol_inv_blocks() {
 
 size_t chol_inv_work_bytes(int k) {
   const int nb = (k + NB - 1) / NB;
-  return sizeof(cplx) * (size_t)nb * NB * NB + 64;
+  return sizeof(cplx) * ((size_t)nb * NB * NB + (size_t)NB * k) + 64;
 }
 
 cudaError_t chol_inv_small(cudaStream_t s, int k, cplx* A, cplx* X, void* work, int* err) {
@@ -472,7 +531,8 @@ cudaError_t chol_inv_small(cudaStream_t s, int k, cplx* A, cplx* X, void* work, 
   g.A = A;
   g.X = X;
   g.Dinv = (cplx*)work;
-  unsigned* tail = (unsigned*)((char*)work + sizeof(cplx) * (size_t)nb * NB * NB);
+  g.Tmp = g.Dinv + (size_t)nb * NB * NB;
+  unsigned* tail = (unsigned*)(g.Tmp + (size_t)NB * k);
   g.bar.count = tail;
   g.bar.gen = tail + 1;
   g.fail = (int*)(tail + 2);
