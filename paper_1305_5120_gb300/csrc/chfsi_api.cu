@@ -508,7 +508,73 @@ chfsi_status cholqr_pass(chfsi_ctx* c, int n, int k, cplx* Y, bool shifted, bool
   return CHFSI_OK;
 }
 
-chfsi_status orthonormalize(chfsi_ctx* c, int n, int nl, const cplx* Yl, int k, cplx* Y) {
+// E = G - I in place; *fro2 = ||E||_F^2 (one CTA, fixed-order reduction)
+__global__ void sub_identity_kernel(int k, cplx* G, double* fro2) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (long e = threadIdx.x; e < (long)k * k; e += blockDim.x) {
+    cplx v = G[e];
+    if (e % k == e / k) v.x -= 1.0;
+    G[e] = v;
+    s += cabs2(v);
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) *fro2 = s;
+}
+// P = a E + b I
+__global__ void axpi_kernel(int k, const cplx* E, double a, double b, cplx* P) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)k * k; e += (long)gridDim.x * blockDim.x) {
+    cplx v = cscale(E[e], a);
+    if (e % k == e / k) v.x += b;
+    P[e] = v;
+  }
+}
+
+// Second orthonormalisation pass for an almost orthonormal block: with G = Y^H Y = I + E and
+// ||E||_F <= 1e-3, X = (I + E)^{-1/2} = I - E/2 + 3E^2/8 - 5E^3/16 + 35E^4/128 + O(E^5)
+// (Horner: three k x k products, no serial FP64 chain) gives Y X with (Y X)^H (Y X) = I +
+// O(||E||^5), the same span and the basis closest to Y.  *ok = false when E is too large.
+chfsi_status lowdin_pass(chfsi_ctx* c, int n, int k, cplx* Y, bool* ok) {
+  cplx *E, *P, *Q, *T;
+  double* fro2;
+  TRY(buf(c, "qr_G", (size_t)k * k, &E));
+  TRY(buf(c, "qr_P", (size_t)k * k, &P));
+  TRY(buf(c, "qr_Q", (size_t)k * k, &Q));
+  TRY(buf(c, "qr_T", (size_t)n * k, &T));
+  TRY(buf(c, "qr_fro2", 2, &fro2));
+  TRY(gemm64(c, gemm_args(k, k, n, OP_C, Y, n, OP_N, Y, n, E, k, ONE, ZERO)));
+  CU(hermitize(c->stream, k, E, k));
+  sub_identity_kernel<<<1, 1024, 0, c->stream>>>(k, E, fro2);
+  count_launch();
+  double h = 0.0;
+  CU(cudaMemcpyAsync(&h, fro2, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (!(sqrt(h) <= 1e-3)) {
+    *ok = false;
+    return CHFSI_OK;
+  }
+  const unsigned gb = (unsigned)std::min<long>(((long)k * k + 255) / 256, 1024);
+  const double cf[5] = {1.0, -0.5, 0.375, -0.3125, 0.2734375};   // binomial series of (1+x)^(-1/2)
+  axpi_kernel<<<gb, 256, 0, c->stream>>>(k, E, cf[4], cf[3], P);   // P = c4 E + c3 I
+  count_launch();
+  for (int j = 2; j >= 0; --j) {
+    // Q = E P + c_j I
+    axpi_kernel<<<gb, 256, 0, c->stream>>>(k, E, 0.0, cf[j], Q);
+    count_launch();
+    TRY(gemm64(c, gemm_args(k, k, k, OP_N, E, k, OP_N, P, k, Q, k, ONE, ONE)));
+    cplx* t = P;
+    P = Q;
+    Q = t;
+  }
+  // Y <- Y X
+  TRY(gemm64(c, gemm_args(n, k, k, OP_N, Y, n, OP_N, P, k, T, n, ONE, ZERO)));
+  CU(copy_block(c->stream, n, k, T, n, Y, n));
+  *ok = true;
+  return CHFSI_OK;
+}
+
+chfsi_status orthonormalize(chfsi_ctx* c, int n, int nl, const cplx* Yl, int k, cplx* Y,
+                            bool exact_qr = true) {
   if (k <= 0) return CHFSI_OK;
   if (nl > 0) {
     cplx* Cm;
@@ -525,6 +591,11 @@ chfsi_status orthonormalize(chfsi_ctx* c, int n, int nl, const cplx* Yl, int k, 
     if (!ok) return CHFSI_ERR_NUMERIC;
     TRY(cholqr_pass(c, n, k, Y, false, &ok));
     if (!ok) return CHFSI_ERR_NUMERIC;
+  }
+  if (!exact_qr) {
+    // inside the solve only the span and orthonormality matter (Rayleigh-Ritz follows)
+    TRY(lowdin_pass(c, n, k, Y, &ok));
+    if (ok) return CHFSI_OK;
   }
   TRY(cholqr_pass(c, n, k, Y, false, &ok));
   if (!ok) return CHFSI_ERR_NUMERIC;
@@ -663,7 +734,7 @@ chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, 
     if (prec == CHFSI_PREC_MIXED) colsteps_lowp += cs;
     tm.mark(prec == CHFSI_PREC_MIXED ? 8 : 2);
     // line 4: QR against the locked vectors
-    TRY(orthonormalize(c, n, nl, Y, ka, Ya));
+    TRY(orthonormalize(c, n, nl, Y, ka, Ya, false));
     tm.mark(3);
     // lines 5-7: Rayleigh-Ritz
     TRY(rayleigh_ritz(c, n, ka, Hs, Ya, lama, Za));
