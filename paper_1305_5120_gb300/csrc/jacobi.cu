@@ -211,7 +211,11 @@ __global__ void __launch_bounds__(256) jacobi_fast_kernel(JacobiFastArgs g) {
         if (R.on) atomicAdd(&s_on, 1);
       }
       __syncthreads();
-      on_sweep += s_on;
+      const int on_round = s_on;
+      on_sweep += on_round;
+      // no pair rotates this round: nothing changes, so every CTA (all computed the same
+      // rotations from the same data) skips the copy, the buffer swap and the grid barrier
+      if (on_round == 0) continue;
       const long nblk = (long)np * np;
       for (long e = tid; e < nblk + (long)k * np; e += nth) {
         if (e < nblk) {
