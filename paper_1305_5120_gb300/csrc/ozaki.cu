@@ -9,14 +9,16 @@
 //  * the complex product is a real GEMM through [Re A | Im A] (K interleaved) times
 //    [[Re B, Im B], [-Im B, Re B]] (columns interleaved);
 //  * every row of the real A (every column pair of the real B) is scaled by a power of two
-//    sigma >= its largest magnitude and expanded into S = 13 signed digits of beta = 5 bits,
-//    x = sigma 2^-(beta-1) sum_s 2^-(s beta) d_s,  |d_s| <= 16 (exact in BF16);
-//  * digit products d_s e_t are integers <= 256; all products of one significance level
-//    L = s + t (L <= S - 1) accumulate in their own TMEM accumulator.  With at most 13
-//    products per level and K <= 4992 real terms per pass, every partial sum is an integer
-//    below 2^24, so the FP32 accumulation is exact even though the tensor core truncates;
-//  * the epilogue combines the 13 levels in FP64 and applies the scales: each entry carries
-//    65 bits relative to its row (column) scale before the final FP64 rounding -- the
+//    sigma >= its largest magnitude and expanded into S = 12 signed digits, a top digit of
+//    7 bits and eleven of 5 bits: x = sigma 2^-6 sum_s 2^(-5 s) d_s, |d_0| <= 64,
+//    |d_s| <= 16 (exact in BF16);
+//  * digit products are integers; all products of one significance level L = s + t
+//    (L <= S - 1, 78 products) accumulate in their own TMEM accumulator.  With K <= 3584
+//    real terms per pass every partial sum is an integer below 2^24 (level 0: 64 * 64 per
+//    term; level L: at most 2 * 64 * 16 + (L - 1) * 256), so the FP32 accumulation is exact
+//    even though the tensor core truncates;
+//  * the epilogue combines the 12 levels in FP64 and applies the scales: each entry carries
+//    61 bits relative to its row (column) scale before the final FP64 rounding -- the
 //    expansion's error is relative to the largest entry of the row, not to the entry, and
 //    Hermitian matrices with a wide spectrum (large diagonal, small off-diagonal) need the
 //    extra digits to stay at FP64 accuracy.  Longer K runs in passes (split-K) whose FP64
@@ -33,23 +35,33 @@ void count_launch(unsigned long long n);
 
 namespace {
 
-constexpr int SLICES = 13;       // digits per operand (65 bits relative to the row/column scale)
-constexpr int DIGIT_BITS = 5;    // |digit| <= 2^(DIGIT_BITS-1) = 16
+constexpr int SLICES = 12;       // digits per operand: a 7-bit top digit and 11 of 5 bits (61 bits)
+constexpr int DIGIT_BITS = 5;    // lower digits: |d| <= 16; top digit: |d| <= 64 (exact in BF16)
+constexpr int TOP_SHIFT = 61;    // |x| 2^(61 - e) < 2^61: the integer the digits expand
 constexpr int LEVELS = SLICES;   // kept levels L = s + t = 0 .. SLICES-1
-constexpr int KPASS = 4992;      // real K per pass: 13 * 4992 * 256 < 2^24
-constexpr int BM = 128, BN = 32, BK = 16;   // BK bf16 = 32-byte rows (32B swizzle), one MMA K step
+// real K per pass: level 0 sums 64 * 64 per term, level L >= 1 at most 2 * 64 * 16 + (L - 1) * 256
+// = 4608 at L = 11; 4608 * 3584 < 2^24
+constexpr int KPASS = 3584;
+constexpr int BM = 128, BN = 32, BK = 16;   // BK bf16 = 32-byte rows, one MMA K step
 constexpr int STAGES = 3;
 constexpr int A_TILE = BM * BK * 2;           // 4 KB
 constexpr int B_TILE = BN * BK * 2;           // 1 KB
 constexpr int STAGE_BYTES = SLICES * (A_TILE + B_TILE);
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr int TMEM_COLS = 512;                // LEVELS * BN = 352 used
+constexpr int NBARS = 2 * STAGES + 1 + 4;   // full, empty, accum, a_full[2], a_free[2]
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 512;
+static_assert(8 * NBARS + 4 <= 512, "barrier area");
+constexpr int TMEM_COLS = 512;
+constexpr int ACOL = LEVELS * BN;             // TMEM columns of the staged A digit slices
+constexpr int TSL = 8;                        // A slices 0..TSL-1 staged in TMEM (8 columns each),
+                                              // double-buffered; slices TSL.. stay in shared memory
+static_assert(ACOL + 2 * 8 * TSL <= TMEM_COLS, "TMEM: accumulators + two A buffers");
 constexpr int NTHREADS = 192;
 constexpr long WAIT_LIMIT = 1L << 24;
 static_assert(LEVELS * BN <= TMEM_COLS, "TMEM");
 static_assert(STAGE_BYTES % 1024 == 0, "stage alignment");
 static_assert(SMEM_BYTES <= 232448, "shared memory");
-static_assert((long)LEVELS * KPASS * 256 < (1L << 24), "exact accumulation");
+static_assert((2L * 64 * 16 + (LEVELS - 2) * 256L) * KPASS < (1L << 24), "exact accumulation");
+static_assert(64L * 64 * KPASS < (1L << 24), "exact accumulation (level 0)");
 
 struct OzArgs {
   int M, N2;              // rows, real columns (2N)
@@ -111,11 +123,31 @@ __device__ __forceinline__ uint64_t umma_desc32(uint32_t saddr) {
 }
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void umma_ss(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
       "l"(a), "l"(b), "r"(IDESC), "r"(accumulate));
+}
+// A operand from TMEM (128 lanes = rows, K packed two bf16 per 32-bit column), B from shared memory
+__device__ __forceinline__ void umma_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(IDESC), "r"(accumulate));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ uint4 lds128(uint32_t a) {
+  uint4 v;
+  asm volatile("ld.shared.v4.b32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, uint4 a, uint4 b) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(a.x),
+               "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
+               : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -139,10 +171,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* base_ptr = smem_raw + (base - raw);
   const uint32_t bars = base + STAGES * STAGE_BYTES;
-  uint32_t* tmem_slot = (uint32_t*)(base_ptr + STAGES * STAGE_BYTES + 8 * (2 * STAGES + 1));
+  uint32_t* tmem_slot = (uint32_t*)(base_ptr + STAGES * STAGE_BYTES + 8 * NBARS);
   auto full = [&](int s) { return bars + 8u * s; };
   auto empty = [&](int s) { return bars + 8u * (STAGES + s); };
   const uint32_t accum = bars + 8u * (2 * STAGES);
+  auto a_full = [&](int b) { return bars + 8u * (2 * STAGES + 1 + b); };
+  auto a_free = [&](int b) { return bars + 8u * (2 * STAGES + 3 + b); };
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * BM;
   const int n0 = blockIdx.y * BN;        // real column offset
@@ -166,9 +200,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full(s), 1);
-      mbar_init(empty(s), 1);
+      mbar_init(empty(s), 1 + 4);   // the MMA commit (B read) and the four A-staging warps
     }
     mbar_init(accum, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(a_full(b), 4);      // one arrival per staging warp
+      mbar_init(a_free(b), 1);      // MMA commit: the products that read TMEM buffer b completed
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -203,29 +241,76 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!mbar_wait(full(s), ph, g.err)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t st = base + s * STAGE_BYTES;
-        // descriptors differ only in the start-address field (address >> 4), so each product's
-        // descriptor is the stage's base descriptor plus a compile-time offset; the fully
-        // unrolled 91-product sequence then costs a few integer adds per MMA
+        // descriptors differ only in the start-address field (address >> 4): the stage's base
+        // descriptors plus compile-time offsets.  Products whose A slice is at least TSL read
+        // it from shared memory and go first; then, once the staging warps have filled TMEM
+        // buffer i & 1 with slices 0..TSL-1 of this block, the rest take A from TMEM.  In
+        // this order the first product of level L is the one with B slice 0.
         const uint64_t da0 = umma_desc32(st), db0 = umma_desc32(st + SLICES * A_TILE);
         const uint32_t first = i != 0;
+        const uint32_t abuf = tmem + (uint32_t)(ACOL + (i & 1) * 8 * TSL);
 #pragma unroll
-        for (int sa = 0; sa < SLICES; ++sa) {
+        for (int sa = SLICES - 1; sa >= TSL; --sa) {
 #pragma unroll
-          for (int tb = 0; tb < LEVELS; ++tb) {
+          for (int tb = 0; tb < LEVELS; ++tb)
             if (tb + sa < LEVELS)
-              umma_bf16(tmem + (uint32_t)((sa + tb) * BN), da0 + (uint64_t)((sa * A_TILE) >> 4),
-                        db0 + (uint64_t)((tb * B_TILE) >> 4), sa == 0 ? first : 1u);
-          }
+              umma_ss(tmem + (uint32_t)((sa + tb) * BN), da0 + (uint64_t)((sa * A_TILE) >> 4),
+                      db0 + (uint64_t)((tb * B_TILE) >> 4), tb == 0 ? first : 1u);
         }
+        if (!mbar_wait(a_full(i & 1), (i >> 1) & 1, g.err)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int sa = TSL - 1; sa >= 0; --sa) {
+#pragma unroll
+          for (int tb = 0; tb < LEVELS; ++tb)
+            if (tb + sa < LEVELS)
+              umma_ts(tmem + (uint32_t)((sa + tb) * BN), abuf + (uint32_t)(8 * sa),
+                      db0 + (uint64_t)((tb * B_TILE) >> 4), tb == 0 ? first : 1u);
+        }
+        umma_commit(a_free(i & 1));
         umma_commit(empty(s));
       }
       umma_commit(accum);
     }
   } else {
-    const int q = warp & 3;
+    const int q = warp & 3;                 // TMEM lanes 32 q .. 32 q + 31 belong to this warp
     const int row = m0 + q * 32 + lane;
+    const uint32_t lanes = (uint32_t)(q * 32) << 16;
     bool ok = true;
-    if (nkb > 0) ok = mbar_wait(accum, 0, g.err);
+    // main loop: stage A digit slices 0..TSL-1 of every K block into TMEM buffer i & 1 (row r
+    // -> lane r, 16 bf16 -> 8 columns), one K block ahead of the products.  Buffer b is
+    // rewritten once the products of block i - 2 that read it have completed (a_free).  The
+    // tiles carry the 32-byte swizzle of the shared-memory operands: logical 16-byte half c of
+    // row r sits at physical half c ^ ((r >> 2) & 1), so reading physical half sw first gives
+    // the low half and keeps the 8-thread shared-memory phases free of bank conflicts.
+    const int rr = q * 32 + lane;
+    const uint32_t sw = (uint32_t)((rr >> 2) & 1) * 16u;
+    for (int i = 0; i < nkb && ok; ++i) {
+      const int s = i % STAGES;
+      ok = __all_sync(0xffffffffu, mbar_wait(full(s), (i / STAGES) & 1, g.err));
+      if (!ok) break;
+      if (i >= 2) {
+        ok = __all_sync(0xffffffffu, mbar_wait(a_free(i & 1), ((i >> 1) - 1) & 1, g.err));
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      }
+      const uint32_t src = base + s * STAGE_BYTES + (uint32_t)rr * 32u;
+      const uint32_t dst = tmem + lanes + (uint32_t)(ACOL + (i & 1) * 8 * TSL);
+#pragma unroll
+      for (int sa = 0; sa < TSL; ++sa) {
+        const uint4 lo = lds128(src + sa * A_TILE + sw);
+        const uint4 hi = lds128(src + sa * A_TILE + (16u - sw));
+        tmem_st8(dst + (uint32_t)(8 * sa), lo, hi);
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(a_full(i & 1));
+        mbar_arrive(empty(s));
+      }
+    }
+    if (nkb > 0 && ok) ok = mbar_wait(accum, 0, g.err);
     ok = __all_sync(0xffffffffu, ok && *(volatile int*)g.err == DEV_OK);
     __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -251,7 +336,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int j = n0 / 2 + jj;
           if (2 * j >= g.N2) continue;
           const int ec = g.colexp[j] > -100000 ? g.colexp[j] : 0;
-          const int sc = er + ec - 2 * (DIGIT_BITS - 1);
+          const int sc = er + ec - 2 * (TOP_SHIFT - DIGIT_BITS * (SLICES - 1));
           const cplx p = cmk(ldexp(v[2 * jj], sc), ldexp(v[2 * jj + 1], sc));
           const long N = g.N2 / 2;
           if (g.splits > 1) {
@@ -316,9 +401,10 @@ __global__ void exp_tile_kernel(int R, int C, const cplx* X, long ld, int op, bo
   }
 }
 
-// Balanced base-32 digits of x / 2^e (|x| < 2^e):  x = 2^e 2^-4 sum_s 2^(-5 s) d_s, |d_s| <= 16.
-// Integer arithmetic on the FP64 bit pattern: G = round(|x| 2^(64-e)) < 2^64, then digits from
-// the least significant up (r = G mod 32 taken in [-15, 16], G = (G - r) / 32); the sign of x
+// Digits of x / 2^e (|x| < 2^e):  x = 2^e 2^-6 sum_s 2^(-5 s) d_s with |d_0| <= 64 and
+// |d_s| <= 16 (s >= 1).  Integer arithmetic on the FP64 bit pattern: G = round(|x| 2^(61-e))
+// < 2^61, then balanced base-32 digits from the least significant up (r = G mod 32 taken in
+// [-15, 16], G = (G - r) / 32); what remains after eleven is the top digit.  The sign of x
 // is applied to every digit.
 __device__ __forceinline__ void digits(double x, int e, __nv_bfloat16* d) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
@@ -326,7 +412,7 @@ __device__ __forceinline__ void digits(double x, int e, __nv_bfloat16* d) {
   unsigned long long G = 0;
   if (bexp != 0) {   // zero and subnormals (far below any row scale here) give zero digits
     const unsigned long long man = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = (bexp - 1023) - e + 12;   // x = man 2^(bexp-1075); G = man 2^(sh)
+    const int sh = (bexp - 1023) - e + (TOP_SHIFT - 52);   // x = man 2^(bexp-1075); G = man 2^sh
     if (sh >= 0) G = man << sh;
     else if (sh > -64) G = (man >> -sh) + ((man >> (-sh - 1)) & 1ull);
   }
@@ -437,7 +523,7 @@ EncodeTiledFn encode_fn() {
   }
   return fn;
 }
-bool make_map(CUtensorMap* m, void* ptr, long rows, long cols, int box_rows) {
+bool make_map(CUtensorMap* m, void* ptr, long rows, long cols, int box_rows, CUtensorMapSwizzle swz) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
@@ -445,7 +531,7 @@ bool make_map(CUtensorMap* m, void* ptr, long rows, long cols, int box_rows) {
   cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+            swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
          CUDA_SUCCESS;
 }
 long round_up(long x, long m) { return (x + m - 1) / m * m; }
@@ -522,8 +608,8 @@ cudaError_t ozaki_gemm(OzakiGemm* o, const GemmArgs& g, cudaStream_t s, int* err
     count_launch(1);
   }
   CUtensorMap ta, tb;
-  if (!make_map(&ta, o->A, SLICES * mpad, kpad, BM)) return cudaErrorInvalidValue;
-  if (!make_map(&tb, o->B, SLICES * npad, kpad, BN)) return cudaErrorInvalidValue;
+  if (!make_map(&ta, o->A, SLICES * mpad, kpad, BM, CU_TENSOR_MAP_SWIZZLE_32B)) return cudaErrorInvalidValue;
+  if (!make_map(&tb, o->B, SLICES * npad, kpad, BN, CU_TENSOR_MAP_SWIZZLE_32B)) return cudaErrorInvalidValue;
   const int kblocks = (int)(kpad / BK);
   const int passes = (int)((kpad + KPASS - 1) / KPASS);
   const long tiles = (mpad / BM) * (npad / BN);

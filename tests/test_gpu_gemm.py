@@ -2,8 +2,8 @@
 extended-precision host product.
 
 Bound: an FP64 GEMM satisfies |C - C_exact| <= K u sum_k |a_ik||b_kj| (u = 2^-53).  The
-tensor-core expansion keeps 65 bits of every entry relative to its row (column) scale and
-accumulates exactly, so it obeys the same form with K u replaced by ~ (2^-60 + u); both are
+tensor-core expansion keeps 61 bits of every entry relative to its row (column) scale and
+accumulates exactly, so it obeys the same form with K u replaced by ~ (2^-58 + u); both are
 tested against 2^-44 sum|a||b| (the K u bound with a margin of 2^9 for K <= 6000), and
 the typical (rms) error against 1e-15 of the rms of sum|a||b|."""
 import numpy as np
