@@ -47,14 +47,10 @@ constexpr int STAGES = 3;
 constexpr int A_TILE = BM * BK * 2;           // 4 KB
 constexpr int B_TILE = BN * BK * 2;           // 1 KB
 constexpr int STAGE_BYTES = SLICES * (A_TILE + B_TILE);
-constexpr int NBARS = 2 * STAGES + 1 + 4;   // full, empty, accum, a_full[2], a_free[2]
+constexpr int NBARS = 2 * STAGES + 1;       // full, empty, accum
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 512;
 static_assert(8 * NBARS + 4 <= 512, "barrier area");
-constexpr int TMEM_COLS = 512;
-constexpr int ACOL = LEVELS * BN;             // TMEM columns of the staged A digit slices
-constexpr int TSL = 8;                        // A slices 0..TSL-1 staged in TMEM (8 columns each),
-                                              // double-buffered; slices TSL.. stay in shared memory
-static_assert(ACOL + 2 * 8 * TSL <= TMEM_COLS, "TMEM: accumulators + two A buffers");
+constexpr int TMEM_COLS = 512;                // LEVELS * BN = 384 used
 constexpr int NTHREADS = 192;
 constexpr long WAIT_LIMIT = 1L << 24;
 static_assert(LEVELS * BN <= TMEM_COLS, "TMEM");
@@ -121,33 +117,16 @@ __device__ __forceinline__ uint64_t umma_desc32(uint32_t saddr) {
   d |= (uint64_t)6 << 61;    // SWIZZLE_32B
   return d;
 }
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
-__device__ __forceinline__ void umma_ss(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B (both K-major), M = BM, N = n
+__host__ __device__ constexpr uint32_t idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+__device__ __forceinline__ void umma_ss(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc_n,
+                                        uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate));
-}
-// A operand from TMEM (128 lanes = rows, K packed two bf16 per 32-bit column), B from shared memory
-__device__ __forceinline__ void umma_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "r"(tmem_a), "l"(b), "r"(IDESC), "r"(accumulate));
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ uint4 lds128(uint32_t a) {
-  uint4 v;
-  asm volatile("ld.shared.v4.b32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
-  return v;
-}
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, uint4 a, uint4 b) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(a.x),
-               "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
-               : "memory");
+      "l"(a), "l"(b), "r"(idesc_n), "r"(accumulate));
 }
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -175,8 +154,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   auto full = [&](int s) { return bars + 8u * s; };
   auto empty = [&](int s) { return bars + 8u * (STAGES + s); };
   const uint32_t accum = bars + 8u * (2 * STAGES);
-  auto a_full = [&](int b) { return bars + 8u * (2 * STAGES + 1 + b); };
-  auto a_free = [&](int b) { return bars + 8u * (2 * STAGES + 3 + b); };
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * BM;
   const int n0 = blockIdx.y * BN;        // real column offset
@@ -200,13 +177,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full(s), 1);
-      mbar_init(empty(s), 1 + 4);   // the MMA commit (B read) and the four A-staging warps
+      mbar_init(empty(s), 1);
     }
     mbar_init(accum, 1);
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(a_full(b), 4);      // one arrival per staging warp
-      mbar_init(a_free(b), 1);      // MMA commit: the products that read TMEM buffer b completed
-    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -241,33 +214,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!mbar_wait(full(s), ph, g.err)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t st = base + s * STAGE_BYTES;
-        // descriptors differ only in the start-address field (address >> 4): the stage's base
-        // descriptors plus compile-time offsets.  Products whose A slice is at least TSL read
-        // it from shared memory and go first; then, once the staging warps have filled TMEM
-        // buffer i & 1 with slices 0..TSL-1 of this block, the rest take A from TMEM.  In
-        // this order the first product of level L is the one with B slice 0.
+        // The B digit tiles of the stage lie one after another (slice t at rows 32 t of one
+        // K-major operand), and level L = s + t of the products with A slice s sits in TMEM
+        // columns 32 L.  So all products of A slice s are one wide MMA: B rows [0, 32 (S - s))
+        // into columns [32 s, 32 S), split at N = 256.  Sixteen instructions per K block; the
+        // first (s = 0) covers every level and starts the accumulation.
         const uint64_t da0 = umma_desc32(st), db0 = umma_desc32(st + SLICES * A_TILE);
         const uint32_t first = i != 0;
-        const uint32_t abuf = tmem + (uint32_t)(ACOL + (i & 1) * 8 * TSL);
 #pragma unroll
-        for (int sa = SLICES - 1; sa >= TSL; --sa) {
-#pragma unroll
-          for (int tb = 0; tb < LEVELS; ++tb)
-            if (tb + sa < LEVELS)
-              umma_ss(tmem + (uint32_t)((sa + tb) * BN), da0 + (uint64_t)((sa * A_TILE) >> 4),
-                      db0 + (uint64_t)((tb * B_TILE) >> 4), tb == 0 ? first : 1u);
+        for (int sa = 0; sa < SLICES; ++sa) {
+          constexpr int NMAX = 256;
+          const int ntot = BN * (LEVELS - sa);
+          const int n1 = ntot < NMAX ? ntot : NMAX;
+          const uint64_t da = da0 + (uint64_t)((sa * A_TILE) >> 4);
+          const uint32_t acc = sa == 0 ? first : 1u;
+          umma_ss(tmem + (uint32_t)(sa * BN), da, db0, idesc(n1), acc);
+          if (ntot > NMAX)
+            umma_ss(tmem + (uint32_t)(sa * BN + NMAX), da, db0 + (uint64_t)((NMAX * BK * 2) >> 4), idesc(ntot - NMAX),
+                    acc);
         }
-        if (!mbar_wait(a_full(i & 1), (i >> 1) & 1, g.err)) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-        for (int sa = TSL - 1; sa >= 0; --sa) {
-#pragma unroll
-          for (int tb = 0; tb < LEVELS; ++tb)
-            if (tb + sa < LEVELS)
-              umma_ts(tmem + (uint32_t)((sa + tb) * BN), abuf + (uint32_t)(8 * sa),
-                      db0 + (uint64_t)((tb * B_TILE) >> 4), tb == 0 ? first : 1u);
-        }
-        umma_commit(a_free(i & 1));
         umma_commit(empty(s));
       }
       umma_commit(accum);
@@ -275,42 +240,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else {
     const int q = warp & 3;                 // TMEM lanes 32 q .. 32 q + 31 belong to this warp
     const int row = m0 + q * 32 + lane;
-    const uint32_t lanes = (uint32_t)(q * 32) << 16;
     bool ok = true;
-    // main loop: stage A digit slices 0..TSL-1 of every K block into TMEM buffer i & 1 (row r
-    // -> lane r, 16 bf16 -> 8 columns), one K block ahead of the products.  Buffer b is
-    // rewritten once the products of block i - 2 that read it have completed (a_free).  The
-    // tiles carry the 32-byte swizzle of the shared-memory operands: logical 16-byte half c of
-    // row r sits at physical half c ^ ((r >> 2) & 1), so reading physical half sw first gives
-    // the low half and keeps the 8-thread shared-memory phases free of bank conflicts.
-    const int rr = q * 32 + lane;
-    const uint32_t sw = (uint32_t)((rr >> 2) & 1) * 16u;
-    for (int i = 0; i < nkb && ok; ++i) {
-      const int s = i % STAGES;
-      ok = __all_sync(0xffffffffu, mbar_wait(full(s), (i / STAGES) & 1, g.err));
-      if (!ok) break;
-      if (i >= 2) {
-        ok = __all_sync(0xffffffffu, mbar_wait(a_free(i & 1), ((i >> 1) - 1) & 1, g.err));
-        if (!ok) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      }
-      const uint32_t src = base + s * STAGE_BYTES + (uint32_t)rr * 32u;
-      const uint32_t dst = tmem + lanes + (uint32_t)(ACOL + (i & 1) * 8 * TSL);
-#pragma unroll
-      for (int sa = 0; sa < TSL; ++sa) {
-        const uint4 lo = lds128(src + sa * A_TILE + sw);
-        const uint4 hi = lds128(src + sa * A_TILE + (16u - sw));
-        tmem_st8(dst + (uint32_t)(8 * sa), lo, hi);
-      }
-      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(a_full(i & 1));
-        mbar_arrive(empty(s));
-      }
-    }
-    if (nkb > 0 && ok) ok = mbar_wait(accum, 0, g.err);
+    if (nkb > 0) ok = mbar_wait(accum, 0, g.err);
     ok = __all_sync(0xffffffffu, ok && *(volatile int*)g.err == DEV_OK);
     __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
