@@ -22,8 +22,15 @@
 //    expansion's error is relative to the largest entry of the row, not to the entry, and
 //    Hermitian matrices with a wide spectrum (large diagonal, small off-diagonal) need the
 //    extra digits to stay at FP64 accuracy.  Longer K runs in passes (split-K) whose FP64
-//    partial results a fixed-order reduction sums.
-#include <cuda.h>
+//    partial results a fixed-order reduction sums;
+//  * the slicing kernels write every 128 x 16 (A) and 32 x 16 (B) digit tile as the exact
+//    shared-memory image the MMA reads (K-major, 32-byte swizzle), ordered so that the twelve
+//    slices of one K block are adjacent: a pipeline stage is two contiguous bulk copies
+//    (48 KB + 12 KB) instead of 24 tensor-map copies of 32-byte rows, whose per-row requests
+//    had saturated the SM's request path to L2;
+//  * the products of A slice s with B slices 0 .. S-1-s land in the adjacent level columns
+//    [32 s, 32 S) of TMEM, so they are one wide MMA (N up to 256, split above): 16
+//    instructions per K block instead of 78.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -61,13 +68,14 @@ static_assert(64L * 64 * KPASS < (1L << 24), "exact accumulation (level 0)");
 
 struct OzArgs {
   int M, N2;              // rows, real columns (2N)
-  int mtiles;             // M_pad / BM
-  long npad;              // real columns padded (rows of each B slice)
   int kblocks;            // K blocks (BK real each) in total
   int per;                // K blocks per split (<= KPASS / BK keeps each split exact)
   int tri;                // GemmTri flags in complex units
   const int* rowexp;      // per row of A: exponent e (sigma = 2^e)
   const int* colexp;      // per complex column of B
+  // digit tiles: [row tile][K block][slice], each the shared-memory image of one operand tile
+  const __nv_bfloat16* A;
+  const __nv_bfloat16* B;
   // output: splits > 1 -> partial[z] (M x N complex, FP64); else C = alpha v + beta C
   cplx* C; long ldc;
   cplx alpha, beta;
@@ -100,12 +108,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* er
   atomicExch(err, DEV_ERR_TIMEOUT);
   return false;
 }
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-          dst),
-      "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
-      : "memory");
+// one contiguous global -> shared copy (16-byte aligned, size a multiple of 16) on the TMA engine
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
 }
 // K-major operand, 32-byte swizzle: 8-row atoms of 256 B
 __device__ __forceinline__ uint64_t umma_desc32(uint32_t saddr) {
@@ -143,8 +150,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 2^x as a double: the exponent field directly in the normal range, ldexp outside it
+__device__ __forceinline__ double pow2(int x) {
+  if (x >= -1022 && x <= 1023) return __longlong_as_double((long long)(x + 1023) << 52);
+  return ldexp(1.0, x);
+}
+
 __global__ void __launch_bounds__(NTHREADS, 1)
-    ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzArgs g) {
+    ozaki_kernel(OzArgs g) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -200,10 +213,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!mbar_wait(empty(s), ph ^ 1, g.err)) break;
         mbar_expect_tx(full(s), STAGE_BYTES);
         const uint32_t st = base + s * STAGE_BYTES;
-        const int kx = (kb0 + i) * BK;
-        for (int q = 0; q < SLICES; ++q) tma_load_2d(st + q * A_TILE, &tmA, full(s), kx, q * g.mtiles * BM + m0);
-        for (int q = 0; q < SLICES; ++q)
-          tma_load_2d(st + SLICES * A_TILE + q * B_TILE, &tmB, full(s), kx, (int)(q * g.npad) + n0);
+        // the stage's twelve A tiles and twelve B tiles are each one contiguous run
+        const long kb = kb0 + i;
+        bulk_load(st, g.A + ((long)blockIdx.x * g.kblocks + kb) * (SLICES * BM * BK), SLICES * A_TILE, full(s));
+        bulk_load(st + SLICES * A_TILE, g.B + ((long)blockIdx.y * g.kblocks + kb) * (SLICES * BN * BK),
+                  SLICES * B_TILE, full(s));
       }
     }
   } else if (warp == 1) {
@@ -246,36 +260,49 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
-      double v[BN];
+      // The level accumulators hold exact integers (|acc_L| < 2^24).  Their combination
+      // sum_L acc_L 2^(-5 L) is formed exactly in two 64-bit integers, levels 0..4 in units of
+      // 2^-20 and levels 5..11 in units of 2^-55 (|hi| < 2^45, |lo| < 2^55), and rounded to FP64
+      // once: two conversions and one FMA per entry instead of twelve FP64 FMAs.
+      constexpr int LSPLIT = 5;
+      const int er = (row < g.M && g.rowexp[row] > -100000) ? g.rowexp[row] : 0;
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16);
 #pragma unroll
-      for (int c = 0; c < BN; ++c) v[c] = 0.0;
-      if (nkb > 0) {
-        // sum_L 2^(-L beta) acc_L, smallest level first
-        for (int L = LEVELS - 1; L >= 0; --L) {
-          float a[BN];
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        long long hi[16], lo[16];
 #pragma unroll
-          for (int c = 0; c < BN; c += 16) tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + L * BN + c, a + c);
-          const double w = ldexp(1.0, -L * DIGIT_BITS);
+        for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0;
+        if (nkb > 0) {
 #pragma unroll
-          for (int c = 0; c < BN; ++c) v[c] = fma((double)a[c], w, v[c]);
+          for (int L = 0; L < LEVELS; ++L) {
+            float a[16];
+            tmem_ld16(taddr + (uint32_t)(L * BN + c0), a);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              const long long d = (long long)__float2int_rz(a[c]);
+              if (L < LSPLIT) hi[c] += d * (1LL << (DIGIT_BITS * (LSPLIT - 1 - L)));
+              else lo[c] += d * (1LL << (DIGIT_BITS * (LEVELS - 1 - L)));
+            }
+          }
         }
-      }
-      if (row < g.M) {
-        const int er = g.rowexp[row] > -100000 ? g.rowexp[row] : 0;
+        if (row < g.M) {
 #pragma unroll
-        for (int jj = 0; jj < BN / 2; ++jj) {
-          const int j = n0 / 2 + jj;
-          if (2 * j >= g.N2) continue;
-          const int ec = g.colexp[j] > -100000 ? g.colexp[j] : 0;
-          const int sc = er + ec - 2 * (TOP_SHIFT - DIGIT_BITS * (SLICES - 1));
-          const cplx p = cmk(ldexp(v[2 * jj], sc), ldexp(v[2 * jj + 1], sc));
-          const long N = g.N2 / 2;
-          if (g.splits > 1) {
-            g.partial[(long)z * g.M * N + row + (long)j * g.M] = p;
-          } else {
-            cplx o = cmul(g.alpha, p);
-            if (g.beta.x != 0.0 || g.beta.y != 0.0) o = cadd(o, cmul(g.beta, g.C[row + (long)j * g.ldc]));
-            g.C[row + (long)j * g.ldc] = o;
+          for (int jj = 0; jj < 8; ++jj) {
+            const int j = (n0 + c0) / 2 + jj;
+            if (2 * j >= g.N2) continue;
+            const int ec = g.colexp[j] > -100000 ? g.colexp[j] : 0;
+            const int sc = er + ec - 2 * (TOP_SHIFT - DIGIT_BITS * (SLICES - 1));
+            const double wh = pow2(sc - DIGIT_BITS * (LSPLIT - 1)), wl = pow2(sc - DIGIT_BITS * (LEVELS - 1));
+            const cplx p = cmk(fma((double)hi[2 * jj], wh, (double)lo[2 * jj] * wl),
+                               fma((double)hi[2 * jj + 1], wh, (double)lo[2 * jj + 1] * wl));
+            const long N = g.N2 / 2;
+            if (g.splits > 1) {
+              g.partial[(long)z * g.M * N + row + (long)j * g.M] = p;
+            } else {
+              cplx o = cmul(g.alpha, p);
+              if (g.beta.x != 0.0 || g.beta.y != 0.0) o = cadd(o, cmul(g.beta, g.C[row + (long)j * g.ldc]));
+              g.C[row + (long)j * g.ldc] = o;
+            }
           }
         }
       }
@@ -361,6 +388,18 @@ __device__ __forceinline__ void digits(double x, int e, __nv_bfloat16* d) {
   for (int s = 0; s < SLICES; ++s) d[s] = __int2bfloat16_rn(neg ? -dig[s] : dig[s]);
 }
 
+// Element offset of (row r, real k) of digit slice s in the tiled layout the GEMM copies from:
+// tiles of R rows x BK, ordered [row tile][K block][slice], each stored as the shared-memory
+// image of a K-major operand with the 32-byte swizzle (row rr at 32 rr bytes, 16-byte half c
+// at physical half c ^ ((rr >> 2) & 1)).
+template <int R>
+__device__ __forceinline__ long tiled_off(long r, long k, int s, long kblocks) {
+  const long rt = r / R, rr = r % R, kb = k / BK;
+  const int kc = (int)(k % BK);
+  const int c = kc >> 3, e = kc & 7;
+  return ((rt * kblocks + kb) * SLICES + s) * (long)(R * BK) + rr * BK + ((c ^ (int)((rr >> 2) & 1)) << 3) + e;
+}
+
 // A digits: slice s, row r, columns 2c (Re) and 2c+1 (Im) of the real embedding; the tile is
 // staged through shared memory so that both the read (op-dependent) and the write coalesce.
 __global__ void slice_a_kernel(int M, int K, const cplx* A, long lda, int op, const int* rowexp, long mpad, long kpad,
@@ -389,7 +428,7 @@ __global__ void slice_a_kernel(int M, int K, const cplx* A, long lda, int op, co
       __nv_bfloat162 p;
       p.x = dr[s];
       p.y = di[s];
-      *(__nv_bfloat162*)(out + (s * mpad + r) * kpad + 2 * c) = p;
+      *(__nv_bfloat162*)(out + tiled_off<BM>(r, 2 * c, s, kpad / BK)) = p;
     }
   }
 }
@@ -417,12 +456,11 @@ __global__ void slice_b_kernel(int K, int N, const cplx* B, long ldb, int op, co
     digits(v.y, e, di);
 #pragma unroll
     for (int s = 0; s < SLICES; ++s) {
-      __nv_bfloat16* rowRe = out + (s * npad + 2 * j) * kpad;
       __nv_bfloat162 p0, p1;
       p0.x = dr[s]; p0.y = __hneg(di[s]);
       p1.x = di[s]; p1.y = dr[s];
-      *(__nv_bfloat162*)(rowRe + 2 * kk) = p0;
-      *(__nv_bfloat162*)(rowRe + kpad + 2 * kk) = p1;
+      *(__nv_bfloat162*)(out + tiled_off<BN>(2 * j, 2 * kk, s, kpad / BK)) = p0;
+      *(__nv_bfloat162*)(out + tiled_off<BN>(2 * j + 1, 2 * kk, s, kpad / BK)) = p1;
     }
   }
 }
@@ -440,31 +478,6 @@ __global__ void oz_reduce_kernel(int M, int N, int splits, const cplx* partial, 
   }
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)p;
-  }
-  return fn;
-}
-bool make_map(CUtensorMap* m, void* ptr, long rows, long cols, int box_rows, CUtensorMapSwizzle swz) {
-  EncodeTiledFn fn = encode_fn();
-  if (!fn) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
-  cuuint32_t es[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
-         CUDA_SUCCESS;
-}
 long round_up(long x, long m) { return (x + m - 1) / m * m; }
 }  // namespace
 
@@ -477,6 +490,7 @@ struct OzakiGemm {
   cplx* partial = nullptr;
   size_t partial_bytes = 0;
   bool attr = false;
+  int sms = 0;
 };
 
 OzakiGemm* ozaki_new() { return new OzakiGemm(); }
@@ -538,26 +552,41 @@ cudaError_t ozaki_gemm(OzakiGemm* o, const GemmArgs& g, cudaStream_t s, int* err
     slice_b_kernel<<<gb, 256, 0, s>>>((int)K, (int)N, g.B, g.ldb, g.opB, colexp, npad, kpad, o->B);
     count_launch(1);
   }
-  CUtensorMap ta, tb;
-  if (!make_map(&ta, o->A, SLICES * mpad, kpad, BM, CU_TENSOR_MAP_SWIZZLE_32B)) return cudaErrorInvalidValue;
-  if (!make_map(&tb, o->B, SLICES * npad, kpad, BN, CU_TENSOR_MAP_SWIZZLE_32B)) return cudaErrorInvalidValue;
   const int kblocks = (int)(kpad / BK);
   const int passes = (int)((kpad + KPASS - 1) / KPASS);
   const long tiles = (mpad / BM) * (npad / BN);
+  if (o->sms == 0) {
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&o->sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  }
+  // K splits (each within one exact pass): one CTA per SM, so the launch takes
+  // ceil(tiles * splits / SMs) waves of (K blocks per split + ~8 blocks of pipeline fill and
+  // epilogue); take the cheapest split count, the smallest among equals
   int splits = passes;
-  // more K splits when the tile grid is small (each split stays within one exact pass)
-  while (tiles * splits < 2 * 152 && splits < 16 * passes && (long)kblocks / (splits + 1) >= 8) ++splits;
+  {
+    long best = -1;
+    for (int sp = passes; sp <= 16 * passes; ++sp) {
+      if (sp > passes && (long)kblocks / sp < 8) break;
+      const long waves = (tiles * sp + o->sms - 1) / o->sms;
+      const long cost = waves * ((kblocks + sp - 1) / sp + 8);
+      if (best < 0 || cost < best) {
+        best = cost;
+        splits = sp;
+      }
+    }
+  }
   const int per = (kblocks + splits - 1) / splits;   // <= KPASS / BK since splits >= passes
   OzArgs a{};
   a.M = (int)M;
   a.N2 = (int)(2 * N);
-  a.mtiles = (int)(mpad / BM);
-  a.npad = npad;
   a.kblocks = kblocks;
   a.per = per;
   a.tri = g.tri;
   a.rowexp = rowexp;
   a.colexp = colexp;
+  a.A = o->A;
+  a.B = o->B;
   a.C = g.C;
   a.ldc = g.ldc;
   a.alpha = g.alpha;
@@ -569,7 +598,7 @@ cudaError_t ozaki_gemm(OzakiGemm* o, const GemmArgs& g, cudaStream_t s, int* err
     a.partial = o->partial;
   }
   dim3 grid((unsigned)(mpad / BM), (unsigned)(npad / BN), (unsigned)splits);
-  ozaki_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(ta, tb, a);
+  ozaki_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(a);
   count_launch(1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (splits > 1) {
