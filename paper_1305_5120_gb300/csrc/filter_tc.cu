@@ -6,11 +6,11 @@
 //     [Re H' | Im H'] (K interleaved)  x  [[Re Y, Im Y], [-Im Y, Re Y]] (columns interleaved),
 // so M = n, N = 2k, K = 2n.  Each FP64 operand is split into three BF16 slices
 // (x = s0 + s1 + s2 + O(2^-24 |x|)) and the six slice products with s + t <= 2 accumulate in
-// one FP32 TMEM accumulator: an FP32-equivalent product on the BF16 tensor pipe.
+// FP32 TMEM accumulators, one per level s + t: an FP32-equivalent product on the BF16 pipe.
 //
 // Per CTA (one 128 x BN output tile): warp 0 issues TMA loads of the A and B slice tiles
-// (128-byte swizzle) into a 3-stage shared-memory ring; warp 1 owns the TMEM accumulator and
-// issues tcgen05.mma; warps 2-5 drain TMEM, apply the recurrence in FP64 against Y_j and
+// (128-byte swizzle) into a 3-stage shared-memory ring; warp 1 owns the TMEM accumulators and
+// issues tcgen05.mma (three per K step); warps 2-5 drain TMEM, apply the recurrence in FP64 against Y_j and
 // Y_{j-1}, store Y_{j+1} (FP64) and write its BF16 slices in the B layout of the next step.
 // Every mbarrier wait is bounded: on timeout the kernel records DEV_ERR_TIMEOUT and leaves.
 #include <cuda.h>
@@ -35,7 +35,7 @@ constexpr int A_TILE = BM * BK * 2;            // bytes per A slice tile (16 KB)
 constexpr int B_TILE = BN * BK * 2;            // bytes per B slice tile (8 KB)
 constexpr int STAGE_BYTES = NSLICE * (A_TILE + B_TILE);
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
-constexpr int TMEM_COLS = 2 * BN;  // fp32 accumulators: [0, BN) leading slice product, [BN, 2BN) corrections
+constexpr int TMEM_COLS = 256;     // fp32 accumulators of levels s + t = 0, 1, 2 at columns [L BN, (L+1) BN)
 constexpr int NTHREADS = 192;
 constexpr long WAIT_LIMIT = 1L << 24;
 
@@ -104,15 +104,17 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
   return d;
 }
 
-// instruction descriptor: kind::f16, A/B bf16, D f32, both K-major, M = 128, N = BN
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+// instruction descriptor: kind::f16, A/B bf16, D f32, both K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc_n,
+                                          uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate));
+      "l"(a), "l"(b), "r"(idesc_n), "r"(accumulate));
 }
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -192,9 +194,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // MMA issuer: six slice products per 16-wide K step into one accumulator
-      constexpr int prod_a[6] = {0, 0, 1, 0, 1, 2};
-      constexpr int prod_b[6] = {0, 1, 0, 2, 1, 0};
+      // MMA issuer.  The three B slice tiles of a stage lie one after another (slice t at rows
+      // 64 t of one K-major operand) and level L = s + t accumulates in TMEM columns [64 L,
+      // 64 L + 64), so the products of A slice s with B slices 0 .. 2 - s are one MMA of
+      // N = 64 (3 - s) into columns [64 s, 192): three instructions per 16-wide K step for
+      // the six slice products.  Each level has its own accumulator, so the per-instruction
+      // truncation of the FP32 accumulation acts on every level at that level's scale.
       bool ok = true;
       for (int kb = 0; kb < g.kblocks && ok; ++kb) {
         const int s = kb % STAGES;
@@ -205,19 +210,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t st = base + s * STAGE_BYTES;
-        // base descriptors once per stage; products and K steps are start-address offsets
+        // base descriptors once per stage; slices and K steps are start-address offsets
         const uint64_t da0 = umma_desc(st), db0 = umma_desc(st + NSLICE * A_TILE);
         const uint32_t later = kb != 0;
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk) {
 #pragma unroll
-          for (int p = 0; p < 6; ++p) {
-            const uint64_t da = da0 + (uint64_t)((prod_a[p] * A_TILE + kk * 32) >> 4);
-            const uint64_t db = db0 + (uint64_t)((prod_b[p] * B_TILE + kk * 32) >> 4);
-            // the leading product s = t = 0 and the five corrections accumulate apart: the
-            // accumulator's per-instruction truncation then acts on each at its own scale
-            if (p == 0) umma_bf16(tmem, da, db, (kk != 0) ? 1u : later);
-            else umma_bf16(tmem + BN, da, db, (kk != 0 || p > 1) ? 1u : later);
+          for (int sa = 0; sa < NSLICE; ++sa) {
+            const uint64_t da = da0 + (uint64_t)((sa * A_TILE + kk * 32) >> 4);
+            const uint64_t db = db0 + (uint64_t)((kk * 32) >> 4);
+            umma_bf16(tmem + (uint32_t)(sa * BN), da, db, idesc(BN * (NSLICE - sa)),
+                      (kk != 0 || sa != 0) ? 1u : later);
           }
         }
         umma_commit(empty(s));   // frees the stage once these MMAs have read it
@@ -233,47 +236,49 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
-      float acc[BN], cor[BN];
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16);
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {   // 16 real columns (8 complex) per pass
+        float l0[16], l1[16], l2[16];
+        tmem_ld16(taddr + c0, l0);
+        tmem_ld16(taddr + BN + c0, l1);
+        tmem_ld16(taddr + 2 * BN + c0, l2);
+        if (row < g.n) {
 #pragma unroll
-      for (int c = 0; c < BN; c += 16) {
-        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + c, acc + c);
-        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + BN + c, cor + c);
-      }
-      if (row < g.n) {
+          for (int jj = 0; jj < 8; ++jj) {
+            const int j = (n0 + c0) / 2 + jj;     // complex column
+            if (j >= g.ncols) continue;
+            const long e = (long)j * g.n + row;
+            const cplx y = g.Ycur[e];
+            const double hr = (double)l0[2 * jj] + ((double)l1[2 * jj] + (double)l2[2 * jj]);
+            const double hi = (double)l0[2 * jj + 1] + ((double)l1[2 * jj + 1] + (double)l2[2 * jj + 1]);
+            cplx o = cmk(g.fa * hr + g.fb * y.x, g.fa * hi + g.fb * y.y);
+            if (g.fg != 0.0) {
+              const cplx p = g.Yout[e];
+              o.x += g.fg * p.x;
+              o.y += g.fg * p.y;
+            }
+            if (g.fcol) {   // residual forcing of the corrected recurrence: + fa p_{j-1}(lam_j) R_j
+              const cplx r = g.R[e];
+              const double f = g.fcol[j];
+              o.x += f * r.x;
+              o.y += f * r.y;
+            }
+            g.Yout[e] = o;
+            if (g.Bnext) {
+              __nv_bfloat16 xr[3], xi[3];
+              split3(o.x, xr[0], xr[1], xr[2]);
+              split3(o.y, xi[0], xi[1], xi[2]);
 #pragma unroll
-        for (int jj = 0; jj < BN / 2; ++jj) {
-          const int j = n0 / 2 + jj;     // complex column
-          if (j >= g.ncols) continue;
-          const long e = (long)j * g.n + row;
-          const cplx y = g.Ycur[e];
-          const double hr = (double)acc[2 * jj] + (double)cor[2 * jj];
-          const double hi = (double)acc[2 * jj + 1] + (double)cor[2 * jj + 1];
-          cplx o = cmk(g.fa * hr + g.fb * y.x, g.fa * hi + g.fb * y.y);
-          if (g.fg != 0.0) {
-            const cplx p = g.Yout[e];
-            o.x += g.fg * p.x;
-            o.y += g.fg * p.y;
-          }
-          if (g.fcol) {   // residual forcing of the corrected recurrence: + fa p_{j-1}(lam_j) R_j
-            const cplx r = g.R[e];
-            const double f = g.fcol[j];
-            o.x += f * r.x;
-            o.y += f * r.y;
-          }
-          g.Yout[e] = o;
-          if (g.Bnext) {
-            __nv_bfloat16 xr[3], xi[3];
-            split3(o.x, xr[0], xr[1], xr[2]);
-            split3(o.y, xi[0], xi[1], xi[2]);
-#pragma unroll
-            for (int t = 0; t < NSLICE; ++t) {
-              __nv_bfloat16* rowRe = g.Bnext + (t * g.nslice_rows_b + 2L * j) * g.ldb_next;
-              __nv_bfloat16* rowIm = rowRe + g.ldb_next;
-              __nv_bfloat162 v0, v1;
-              v0.x = xr[t]; v0.y = __hneg(xi[t]);   // row 2j:   ( Re y, -Im y)
-              v1.x = xi[t]; v1.y = xr[t];           // row 2j+1: ( Im y,  Re y)
-              *(__nv_bfloat162*)(rowRe + 2L * row) = v0;
-              *(__nv_bfloat162*)(rowIm + 2L * row) = v1;
+              for (int t = 0; t < NSLICE; ++t) {
+                __nv_bfloat16* rowRe = g.Bnext + (t * g.nslice_rows_b + 2L * j) * g.ldb_next;
+                __nv_bfloat16* rowIm = rowRe + g.ldb_next;
+                __nv_bfloat162 v0, v1;
+                v0.x = xr[t]; v0.y = __hneg(xi[t]);   // row 2j:   ( Re y, -Im y)
+                v1.x = xi[t]; v1.y = xr[t];           // row 2j+1: ( Im y,  Re y)
+                *(__nv_bfloat162*)(rowRe + 2L * row) = v0;
+                *(__nv_bfloat162*)(rowIm + 2L * row) = v1;
+              }
             }
           }
         }
