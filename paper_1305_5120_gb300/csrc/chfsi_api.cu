@@ -508,6 +508,72 @@ chfsi_status cholqr_pass(chfsi_ctx* c, int n, int k, cplx* Y, bool shifted, bool
   return CHFSI_OK;
 }
 
+// In-solve QR, first pass in FP32.  The filtered block's columns differ in norm by orders of
+// magnitude while the column-scaled block is well conditioned (cond <= 4 on the benchmark
+// sequences past the cold start), so Y <- Y D L^{-H}, L L^H = D G D, with D = diag(2^-s_i)
+// bringing G's diagonal into [1, 4) and L from an FP32 Cholesky, leaves a block whose Gram
+// matrix is I + O(1e-6): the FP64 Loewdin pass that follows finishes the job.  The scaling
+// is exact (exponent arithmetic) and so is the FP32 <-> FP64 movement, so every FP64
+// instruction here is in the two products.
+__device__ __forceinline__ int half_exp(double gii) {   // s with gii 2^-2s in [1, 4)
+  const int e = (int)((__double_as_longlong(gii) >> 52) & 0x7FF) - 1023;
+  return e >> 1;
+}
+__global__ void scaled_gram_f32_kernel(int k, const cplx* G, float2* Gs) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)k * k; e += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % k), j = (int)(e / k);
+    const int sh = half_exp(G[i + (long)i * k].x) + half_exp(G[j + (long)j * k].x);
+    const cplx g = G[e];
+    Gs[e] = make_float2(to_f32(scale_pow2(g.x, sh)), to_f32(scale_pow2(g.y, sh)));
+  }
+}
+// F = D X^H (upper triangular): F[i, j] = 2^-s_i conj(X[j, i]) for i <= j
+__global__ void scaled_inv_factor_kernel(int k, const cplx* G, const float2* X, cplx* F) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)k * k; e += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % k), j = (int)(e / k);
+    cplx f = cmk(0.0, 0.0);
+    if (i <= j) {
+      const int sh = half_exp(G[i + (long)i * k].x);
+      const float2 x = X[j + (long)i * k];
+      f = cmk(scale_pow2(to_f64(x.x), sh), scale_pow2(to_f64(-x.y), sh));
+    }
+    F[e] = f;
+  }
+}
+
+chfsi_status cholqr32_pass(chfsi_ctx* c, int n, int k, cplx* Y, bool* ok) {
+  cplx *G, *F, *T;
+  float2 *Gs, *X32;
+  char* w;
+  TRY(buf(c, "qr_G", (size_t)k * k, &G));
+  TRY(buf(c, "qr_Ri", (size_t)k * k, &F));
+  TRY(buf(c, "qr_T", (size_t)n * k, &T));
+  TRY(buf(c, "qr_G32", (size_t)k * k, &Gs));
+  TRY(buf(c, "qr_X32", (size_t)k * k, &X32));
+  TRY(buf(c, "qr_cholinv", chol_inv_work_bytes(k), &w));
+  TRY(gemm64(c, gemm_args(k, k, n, OP_C, Y, n, OP_N, Y, n, G, k, ONE, ZERO)));
+  const unsigned gb = (unsigned)std::min<long>(((long)k * k + 255) / 256, 1024);
+  scaled_gram_f32_kernel<<<gb, 256, 0, c->stream>>>(k, G, Gs);
+  count_launch();
+  CU(cudaGetLastError());
+  CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  CU(chol_inv_small_f32(c->stream, k, Gs, X32, w, c->d_err));
+  int e = 0;
+  TRY(read_err(c, &e));
+  if (e != DEV_OK) {   // not positive definite in FP32: the caller falls back to FP64
+    CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    *ok = false;
+    return CHFSI_OK;
+  }
+  scaled_inv_factor_kernel<<<gb, 256, 0, c->stream>>>(k, G, X32, F);
+  count_launch();
+  CU(cudaGetLastError());
+  TRY(gemm64(c, gemm_args(n, k, k, OP_N, Y, n, OP_N, F, k, T, n, ONE, ZERO, TRI_B_UPPER)));
+  CU(copy_block(c->stream, n, k, T, n, Y, n));
+  *ok = true;
+  return CHFSI_OK;
+}
+
 // E = G - I in place; *fro2 = ||E||_F^2 (one CTA, fixed-order reduction)
 __global__ void sub_identity_kernel(int k, cplx* G, double* fro2) {
   __shared__ double sh[32];
@@ -585,6 +651,19 @@ chfsi_status orthonormalize(chfsi_ctx* c, int n, int nl, const cplx* Yl, int k, 
     }
   }
   bool ok = false;
+  if (!exact_qr && k <= CHOL_INV_KMAX) {
+    // inside the solve only the span and orthonormality matter (Rayleigh-Ritz follows): an
+    // FP32 first pass on the column-scaled block, then the FP64 Loewdin pass; a block that
+    // the FP32 factor cannot bring within reach of it takes a second FP32 pass, and failing
+    // that the FP64 passes below (on the block as it stands: same span)
+    for (int pass = 0; pass < 2; ++pass) {
+      bool ok32 = false;
+      TRY(cholqr32_pass(c, n, k, Y, &ok32));
+      if (!ok32) break;
+      TRY(lowdin_pass(c, n, k, Y, &ok));
+      if (ok) return CHFSI_OK;
+    }
+  }
   TRY(cholqr_pass(c, n, k, Y, false, &ok));
   if (!ok) {
     TRY(cholqr_pass(c, n, k, Y, true, &ok));

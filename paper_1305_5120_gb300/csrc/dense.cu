@@ -304,57 +304,95 @@ cudaError_t copy_block(cudaStream_t s, int n, int k, const cplx* src, long lds, 
 
 // ---- small Cholesky + inverse in one cooperative launch ----------------------------------
 // The k x k Gram matrices of CholQR (k = nev + nex) are too small for a launch-per-block
-// factorisation to keep more than a few SMs busy on the slow FP64 pipe.  Here every grid
-// barrier separates the three phases of a block step -- the 32 x 32 diagonal factor and its
-// inverse (one CTA), the panel L21 = A21 L11^{-H} (one warp per row), the trailing update of
-// the lower triangle (all threads) -- and then the block rows of X = L^{-1}.
+// factorisation to keep more than a few SMs busy.  Here every grid barrier separates the
+// three phases of a block step -- the 32 x 32 diagonal factor and its inverse (one CTA), the
+// panel L21 = A21 L11^{-H} (one warp per row), the trailing update of the lower triangle (all
+// threads) -- and then the block rows of X = L^{-1}.  The kernel is written for a real type
+// T: double (FP64 factors, the reduction of S and exact QR) and float (the first pass of the
+// in-solve QR, whose Gram matrix is column-scaled and well conditioned).
+//
+// Cost model of this GPU's FP64 pipe: a warp-wide FP64 instruction occupies a
+// sub-partition's FP64 unit for about 64 cycles whatever the number of active lanes, and a
+// division or square root costs 400-700 cycles.  So the pivot's rsqrt is taken by one thread
+// and shared, the diagonal block's trailing update enumerates the lower triangle densely, and
+// the dot products are split over eight accumulators.
 namespace {
+template <typename T> struct Cx;
+template <> struct Cx<double> {
+  typedef double2 C;
+  static __device__ __forceinline__ C mk(double a, double b) { return make_double2(a, b); }
+  static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+};
+template <> struct Cx<float> {
+  typedef float2 C;
+  static __device__ __forceinline__ C mk(float a, float b) { return make_float2(a, b); }
+  static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+};
+template <typename C> __device__ __forceinline__ C xadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C> __device__ __forceinline__ C xsub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename C, typename T> __device__ __forceinline__ C xscale(C a, T s) { C r; r.x = a.x * s; r.y = a.y * s; return r; }
+template <typename C> __device__ __forceinline__ C xmul(C a, C b) {
+  C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <typename C> __device__ __forceinline__ C xmulc(C a, C b) {   // a conj(b)
+  C r; r.x = a.x * b.x + a.y * b.y; r.y = a.y * b.x - a.x * b.y; return r;
+}
+template <typename C> __device__ __forceinline__ C xzero() { C r; r.x = 0; r.y = 0; return r; }
+
+template <typename T>
 struct CholInvArgs {
+  typedef typename Cx<T>::C C;
   int k;
-  cplx* A;
-  cplx* X;
-  cplx* Dinv;        // nb blocks of NB x NB: inverses of the diagonal blocks
-  cplx* Tmp;         // NB x k staging of one block row of X
+  C* A;
+  C* X;
+  C* Dinv;           // nb blocks of NB x NB: inverses of the diagonal blocks
+  C* Tmp;            // NB x k staging of one block row of X
   GridBarrier bar;
   int* err;
   int* fail;
 };
 
-// On this GPU a dependent FP64 FMA costs 64 cycles and an FP64 division or square root
-// 400-700, so every serial chain below is kept short: one rsqrt per pivot (no division),
-// computed redundantly by all threads; dot products split over eight accumulators.
 constexpr int ACC = 8;
 
 // The w x w (w <= 32) diagonal block at (j0, j0), by one CTA of 256 threads in shared memory:
 // L (lower) into A, L^{-1} into X's diagonal block and into Dinv.
-__device__ void diag_factor_cta(cplx* A, cplx* X, cplx* Dinv, int k, int j0, int w, int* fail, int* err,
-                                cplx (*T)[NB + 1], cplx (*Ti)[NB + 1], double* invd, int* bad) {
+template <typename T>
+__device__ void diag_factor_cta(typename Cx<T>::C* A, typename Cx<T>::C* X, typename Cx<T>::C* Dinv, int k, int j0,
+                                int w, int* fail, int* err, typename Cx<T>::C (*Tm)[NB + 1],
+                                typename Cx<T>::C (*Ti)[NB + 1], T* invd, int* bad, T* s_inv) {
+  typedef typename Cx<T>::C C;
   const int tid = threadIdx.x;
   for (int e = tid; e < w * w; e += blockDim.x) {
     const int r = e % w, c = e / w;
-    T[r][c] = A[(j0 + r) + (long)(j0 + c) * k];
+    Tm[r][c] = A[(j0 + r) + (long)(j0 + c) * k];
   }
   if (tid == 0) *bad = 0;
   __syncthreads();
   for (int c = 0; c < w; ++c) {
-    const double p = T[c][c].x;   // every thread reads the pivot and takes its rsqrt
-    const bool ok = p > 0.0 && isfinite(p);
-    const double inv = ok ? rsqrt(p) : 1.0;
-    __syncthreads();
-    if (!ok) {
-      if (tid == 0) *bad = 1;
-      break;
-    }
-    if (tid == 0) {
-      T[c][c] = cmk(p * inv, 0.0);
+    if (tid == 0) {   // the pivot's rsqrt once, shared through shared memory
+      const T p = Tm[c][c].x;
+      const bool ok = p > (T)0 && isfinite(p);
+      const T inv = ok ? Cx<T>::rsq(p) : (T)1;
+      *s_inv = inv;
+      if (!ok) *bad = 1;
+      Tm[c][c] = Cx<T>::mk(p * inv, (T)0);
       invd[c] = inv;
     }
-    for (int r = c + 1 + tid; r < w; r += blockDim.x) T[r][c] = cscale(T[r][c], inv);
     __syncthreads();
+    if (*bad) break;
+    const T inv = *s_inv;
+    for (int r = c + 1 + tid; r < w; r += blockDim.x) Tm[r][c] = xscale(Tm[r][c], inv);
+    __syncthreads();
+    // rank-1 update of the lower triangle of the trailing m x m block, enumerated densely
     const int m = w - c - 1;
-    for (int e = tid; e < m * m; e += blockDim.x) {
-      const int r = c + 1 + e % m, q = c + 1 + e / m;
-      if (r >= q) T[r][q] = csub(T[r][q], cmulc(T[r][c], T[q][c]));
+    for (int e = tid; e < m * (m + 1) / 2; e += blockDim.x) {
+      int q = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);   // column within the triangle
+      while (q * (q + 1) / 2 > e) --q;
+      while ((q + 1) * (q + 2) / 2 <= e) ++q;
+      const int rr = e - q * (q + 1) / 2;                              // rr <= q
+      // element (row c + 1 + (m - 1 - rr), col c + 1 + (m - 1 - q)): row >= col
+      const int row = c + 1 + (m - 1 - rr), col = c + 1 + (m - 1 - q);
+      Tm[row][col] = xsub(Tm[row][col], xmulc(Tm[row][c], Tm[col][c]));
     }
     __syncthreads();
   }
@@ -366,36 +404,39 @@ __device__ void diag_factor_cta(cplx* A, cplx* X, cplx* Dinv, int k, int j0, int
     }
     return;
   }
-  // Ti = T^{-1} row by row: Ti[r][c] = (delta_rc - sum_{c<=q<r} T[r][q] Ti[q][c]) invd[r];
+  // Ti = Tm^{-1} row by row: Ti[r][c] = (delta_rc - sum_{c<=q<r} Tm[r][q] Ti[q][c]) invd[r];
   // 8 threads per column split the sum (shuffle reduction), 32 columns per pass
   const int c = tid >> 3, part = tid & 7;
   for (int r = 0; r < w; ++r) {
-    cplx sacc = cmk(0.0, 0.0);
+    C sacc = xzero<C>();
     if (c < w)
-      for (int q = c + part; q < r; q += 8) sacc = cadd(sacc, cmul(T[r][q], Ti[q][c]));
+      for (int q = c + part; q < r; q += 8) sacc = xadd(sacc, xmul(Tm[r][q], Ti[q][c]));
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) {
       sacc.x += __shfl_xor_sync(0xffffffffu, sacc.x, o);
       sacc.y += __shfl_xor_sync(0xffffffffu, sacc.y, o);
     }
     if (part == 0 && c < w) {
-      const double d = (r == c) ? 1.0 : 0.0;
-      Ti[r][c] = (r < c) ? cmk(0.0, 0.0) : cmk((d - sacc.x) * invd[r], -sacc.y * invd[r]);
+      const T d = (r == c) ? (T)1 : (T)0;
+      Ti[r][c] = (r < c) ? xzero<C>() : Cx<T>::mk((d - sacc.x) * invd[r], -sacc.y * invd[r]);
     }
     __syncthreads();
   }
   for (int e = tid; e < w * w; e += blockDim.x) {
     const int r = e % w, cc = e / w;
-    A[(j0 + r) + (long)(j0 + cc) * k] = (r >= cc) ? T[r][cc] : cmk(0.0, 0.0);
+    A[(j0 + r) + (long)(j0 + cc) * k] = (r >= cc) ? Tm[r][cc] : xzero<C>();
     X[(j0 + r) + (long)(j0 + cc) * k] = Ti[r][cc];
     Dinv[r + cc * NB] = Ti[r][cc];
   }
 }
 
-__global__ void __launch_bounds__(256) chol_inv_kernel(CholInvArgs g) {
-  __shared__ cplx T[NB][NB + 1];
-  __shared__ cplx Ti[NB][NB + 1];
-  __shared__ double invd[NB];
+template <typename T>
+__global__ void __launch_bounds__(256) chol_inv_kernel(CholInvArgs<T> g) {
+  typedef typename Cx<T>::C C;
+  __shared__ C Tm[NB][NB + 1];
+  __shared__ C Ti[NB][NB + 1];
+  __shared__ T invd[NB];
+  __shared__ T s_inv;
   __shared__ int bad;
   const int k = g.k, nb = (k + NB - 1) / NB;
   const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -405,7 +446,7 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(CholInvArgs g) {
   for (int jb = 0; jb < nb; ++jb) {
     const int j0 = jb * NB, w = min(NB, k - j0);
     if (blockIdx.x == 0)
-      diag_factor_cta(g.A, g.X, g.Dinv + (long)jb * NB * NB, k, j0, w, g.fail, g.err, T, Ti, invd, &bad);
+      diag_factor_cta<T>(g.A, g.X, g.Dinv + (long)jb * NB * NB, k, j0, w, g.fail, g.err, Tm, Ti, invd, &bad, &s_inv);
     if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
     if (*(volatile int*)g.fail) return;
     // panel: rows below, L[r, j0+c] = sum_q A[r, j0+q] conj(Ti[c][q])  (one warp per row,
@@ -416,19 +457,19 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(CholInvArgs g) {
     }
     __syncthreads();
     for (long row = j0 + w + wid; row < k; row += nwarps) {
-      const cplx a = lane < w ? g.A[row + (long)(j0 + lane) * k] : cmk(0.0, 0.0);
-      cplx acc[ACC];
+      const C a = lane < w ? g.A[row + (long)(j0 + lane) * k] : xzero<C>();
+      C acc[ACC];
 #pragma unroll
-      for (int t = 0; t < ACC; ++t) acc[t] = cmk(0.0, 0.0);
+      for (int t = 0; t < ACC; ++t) acc[t] = xzero<C>();
 #pragma unroll
       for (int q = 0; q < NB; ++q) {
-        cplx aq;
+        C aq;
         aq.x = __shfl_sync(0xffffffffu, a.x, q);
         aq.y = __shfl_sync(0xffffffffu, a.y, q);
-        if (lane < w && q <= lane) acc[q % ACC] = cadd(acc[q % ACC], cmulc(aq, Ti[lane][q]));
+        if (lane < w && q <= lane) acc[q % ACC] = xadd(acc[q % ACC], xmulc(aq, Ti[lane][q]));
       }
 #pragma unroll
-      for (int t = 1; t < ACC; ++t) acc[0] = cadd(acc[0], acc[t]);
+      for (int t = 1; t < ACC; ++t) acc[0] = xadd(acc[0], acc[t]);
       if (lane < w) g.A[row + (long)(j0 + lane) * k] = acc[0];
     }
     if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
@@ -437,40 +478,40 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(CholInvArgs g) {
     for (long e = tid; e < (long)m * m; e += nth) {
       const int r = t0 + (int)(e % m), c = t0 + (int)(e / m);
       if (r < c) continue;
-      cplx acc[ACC];
+      C acc[ACC];
 #pragma unroll
-      for (int t = 0; t < ACC; ++t) acc[t] = cmk(0.0, 0.0);
+      for (int t = 0; t < ACC; ++t) acc[t] = xzero<C>();
 #pragma unroll
       for (int q = 0; q < NB; ++q)
-        if (q < w) acc[q % ACC] = cadd(acc[q % ACC], cmulc(g.A[r + (long)(j0 + q) * k], g.A[c + (long)(j0 + q) * k]));
+        if (q < w) acc[q % ACC] = xadd(acc[q % ACC], xmulc(g.A[r + (long)(j0 + q) * k], g.A[c + (long)(j0 + q) * k]));
 #pragma unroll
-      for (int t = 1; t < ACC; ++t) acc[0] = cadd(acc[0], acc[t]);
-      g.A[r + (long)c * k] = csub(g.A[r + (long)c * k], acc[0]);
+      for (int t = 1; t < ACC; ++t) acc[0] = xadd(acc[0], acc[t]);
+      g.A[r + (long)c * k] = xsub(g.A[r + (long)c * k], acc[0]);
     }
     if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
   }
   // strictly upper triangle of L
   for (long e = tid; e < (long)k * k; e += nth) {
     const long r = e % k, c = e / k;
-    if (r < c) g.A[e] = cmk(0.0, 0.0);
+    if (r < c) g.A[e] = xzero<C>();
   }
   // block rows of X = L^{-1}: X(i,0:i0) = -Ti (L(i,0:i0) X(0:i0,0:i0))
   for (int ib = 1; ib < nb; ++ib) {
     const int i0 = ib * NB, w = min(NB, k - i0);
     for (long e = tid; e < (long)w * i0; e += nth) {
       const int r = (int)(e % w), c = (int)(e / w);
-      cplx acc[ACC];
+      C acc[ACC];
 #pragma unroll
-      for (int t = 0; t < ACC; ++t) acc[t] = cmk(0.0, 0.0);
+      for (int t = 0; t < ACC; ++t) acc[t] = xzero<C>();
       int q = c;
       for (; q + ACC <= i0; q += ACC) {
 #pragma unroll
         for (int t = 0; t < ACC; ++t)
-          acc[t] = cadd(acc[t], cmul(g.A[(i0 + r) + (long)(q + t) * k], g.X[(q + t) + (long)c * k]));
+          acc[t] = xadd(acc[t], xmul(g.A[(i0 + r) + (long)(q + t) * k], g.X[(q + t) + (long)c * k]));
       }
-      for (; q < i0; ++q) acc[0] = cadd(acc[0], cmul(g.A[(i0 + r) + (long)q * k], g.X[q + (long)c * k]));
+      for (; q < i0; ++q) acc[0] = xadd(acc[0], xmul(g.A[(i0 + r) + (long)q * k], g.X[q + (long)c * k]));
 #pragma unroll
-      for (int t = 1; t < ACC; ++t) acc[0] = cadd(acc[0], acc[t]);
+      for (int t = 1; t < ACC; ++t) acc[0] = xadd(acc[0], acc[t]);
       g.X[(i0 + r) + (long)c * k] = acc[0];
     }
     if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
@@ -483,22 +524,22 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(CholInvArgs g) {
     for (long e = tid; e < (long)w * i0; e += nth) {
       const int r = (int)(e % w);
       const long c = e / w;
-      cplx acc[ACC];
+      C acc[ACC];
 #pragma unroll
-      for (int t = 0; t < ACC; ++t) acc[t] = cmk(0.0, 0.0);
+      for (int t = 0; t < ACC; ++t) acc[t] = xzero<C>();
 #pragma unroll
       for (int q = 0; q < NB; ++q)
-        if (q <= r) acc[q % ACC] = cadd(acc[q % ACC], cmul(Ti[r][q], g.X[(i0 + q) + c * k]));
+        if (q <= r) acc[q % ACC] = xadd(acc[q % ACC], xmul(Ti[r][q], g.X[(i0 + q) + c * k]));
 #pragma unroll
-      for (int t = 1; t < ACC; ++t) acc[0] = cadd(acc[0], acc[t]);
+      for (int t = 1; t < ACC; ++t) acc[0] = xadd(acc[0], acc[t]);
       g.Tmp[(long)r + c * NB] = acc[0];
     }
     if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
     for (long e = tid; e < (long)w * i0; e += nth) {
       const int r = (int)(e % w);
       const long c = e / w;
-      const cplx v = g.Tmp[(long)r + c * NB];
-      g.X[(i0 + r) + c * k] = cmk(-v.x, -v.y);
+      const C v = g.Tmp[(long)r + c * NB];
+      g.X[(i0 + r) + c * k] = Cx<T>::mk(-v.x, -v.y);
     }
     if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
   }
@@ -507,13 +548,37 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(CholInvArgs g) {
 int chol_inv_blocks() {
   static int cap = 0;
   if (cap == 0) {
-    int dev = 0, sms = 0, occ = 0;
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, chol_inv_kernel, 256, 0);
-    cap = sms * (occ < 1 ? 1 : 1);
+    cap = sms;   // one CTA per SM (co-resident for the grid barrier)
   }
   return cap;
+}
+
+template <typename T>
+cudaError_t chol_inv_launch(cudaStream_t s, int k, typename Cx<T>::C* A, typename Cx<T>::C* X, void* work, int* err) {
+  typedef typename Cx<T>::C C;
+  if (k <= 0) return cudaSuccess;
+  if (k > CHOL_INV_KMAX) return cudaErrorInvalidValue;
+  const int nb = (k + NB - 1) / NB;
+  CholInvArgs<T> g{};
+  g.k = k;
+  g.A = A;
+  g.X = X;
+  g.Dinv = (C*)work;
+  g.Tmp = g.Dinv + (size_t)nb * NB * NB;
+  unsigned* tail = (unsigned*)(g.Tmp + (size_t)NB * k);
+  g.bar.count = tail;
+  g.fail = (int*)(tail + 2);
+  g.err = err;
+  cudaError_t e = cudaMemsetAsync(tail, 0, 16, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(X, 0, sizeof(C) * (size_t)k * k, s);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&g};
+  e = coop_launch((const void*)chol_inv_kernel<T>, dim3(chol_inv_blocks()), dim3(256), args, s);
+  count_launch();
+  return e;
 }
 }  // namespace
 
@@ -523,25 +588,8 @@ size_t chol_inv_work_bytes(int k) {
 }
 
 cudaError_t chol_inv_small(cudaStream_t s, int k, cplx* A, cplx* X, void* work, int* err) {
-  if (k <= 0) return cudaSuccess;
-  if (k > CHOL_INV_KMAX) return cudaErrorInvalidValue;
-  const int nb = (k + NB - 1) / NB;
-  CholInvArgs g{};
-  g.k = k;
-  g.A = A;
-  g.X = X;
-  g.Dinv = (cplx*)work;
-  g.Tmp = g.Dinv + (size_t)nb * NB * NB;
-  unsigned* tail = (unsigned*)(g.Tmp + (size_t)NB * k);
-  g.bar.count = tail;
-  g.bar.gen = tail + 1;
-  g.fail = (int*)(tail + 2);
-  g.err = err;
-  cudaError_t e = cudaMemsetAsync(tail, 0, 16, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(X, 0, sizeof(cplx) * (size_t)k * k, s);
-  if (e != cudaSuccess) return e;
-  void* args[] = {&g};
-  e = coop_launch((const void*)chol_inv_kernel, dim3(chol_inv_blocks()), dim3(256), args, s);
-  count_launch();
-  return e;
+  return chol_inv_launch<double>(s, k, A, X, work, err);
+}
+cudaError_t chol_inv_small_f32(cudaStream_t s, int k, float2* A, float2* X, void* work, int* err) {
+  return chol_inv_launch<float>(s, k, A, X, work, err);
 }

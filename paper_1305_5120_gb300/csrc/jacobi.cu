@@ -134,10 +134,18 @@ __global__ void __launch_bounds__(256) jacobi_kernel(JacobiArgs g) {
 // (identical in every CTA), so the rotation table needs no grid-wide publication.  All CTAs
 // also count the round's rotations identically, which gives a consistent convergence test
 // without atomics.  Each round reads A_cur and writes every 2 x 2 block of A_next.
+//
+// Cost model of this GPU's FP64 pipe: one warp-wide FP64 instruction (including conversions
+// to or from FP64) occupies a sub-partition's FP64 unit for about 64 cycles, whatever the
+// number of active lanes.  So the rotations, which every CTA computes, keep their FP64
+// instruction count low (integer tests and format moves, an FP32 start for the tangent); and
+// the update computes each 2 x 2 block of the Hermitian A once (pair index a <= b),
+// enumerated densely so that every warp is full, writing the mirrored block as its conjugate
+// transpose.
 constexpr int JF_MAXPAIRS = 1024;
 struct RotS {
-  cplx upp, upq, uqp, uqq;   // the 2 x 2 unitary (upp = c, upq = s real; uqp = -s conj(ph), uqq = c conj(ph))
-  cplx phc;                  // conj(ph)
+  double c, s;      // U = [[c, s], [-s conj(ph), c conj(ph)]] (c, s real, c^2 + s^2 = 1)
+  double phx, phy;  // conj(ph), |ph| = 1
   int p, q, on, pad;
 };
 struct JacobiFastArgs {
@@ -152,36 +160,39 @@ struct JacobiFastArgs {
   int max_sweeps;
 };
 
-// Rotation of pair (p, q) from the current 2 x 2 diagonal block.  The tangent t starts in
-// FP32 (an FP64 division/square-root chain costs microseconds on this FP64 pipe) and one FP64
-// Newton step makes it FP64-accurate; the rotation built from it (c = 1/sqrt(1 + t^2),
-// s = t c, unit phase via rsqrt) is unitary to FP64 rounding.
-__device__ __forceinline__ RotS make_rot(const cplx* A, int k, int p, int q, double thresh) {
+
+// Rotation of pair (p, q) annihilating a_pq of the current 2 x 2 diagonal block: tangent t of
+// t^2 + 2 tau t - 1 = 0 (the smaller root), tau = (a_qq - a_pp) / (2 |a_pq|), c = 1 / sqrt(1 +
+// t^2), s = t c, ph = a_pq / |a_pq|.  The tangent starts in FP32 (values moved between the
+// formats by integer bit operations) and one FP64 Newton step, whose own reciprocal needs only
+// FP32 accuracy, makes it FP64-accurate, so that the sweeps keep their quadratic convergence;
+// c, s and ph come from FP64 rsqrt, so U is unitary to FP64 rounding.  About twenty FP64
+// instructions in all.  A pair rotates when |a_pq| > thresh; max(|Re a_pq|, |Im a_pq|) <=
+// thresh / sqrt(2), an integer test on the bit patterns, rules most others out first.  (The
+// threshold eps ||A||_F sits a few rounding units of the largest entry above the rounding
+// noise of the update, so it must not be tightened.)
+__device__ __forceinline__ RotS make_rot(const cplx* A, int k, int p, int q, long long thr_bits, double thresh2) {
   RotS R;
   if (p > q) { int t = p; p = q; q = t; }
   R.p = p; R.q = q; R.on = 0; R.pad = 0;
-  R.upp = cmk(1, 0); R.uqq = cmk(1, 0); R.upq = cmk(0, 0); R.uqp = cmk(0, 0); R.phc = cmk(1, 0);
+  R.c = 1.0; R.s = 0.0; R.phx = 1.0; R.phy = 0.0;
   if (q < k) {
     const cplx apq = A[p + (long)q * k];
-    const double ar2 = cabs2(apq);
-    if (ar2 > thresh * thresh) {
+    const double ar2 = (abs_bits(apq.x) > thr_bits || abs_bits(apq.y) > thr_bits) ? fma(apq.x, apq.x, apq.y * apq.y) : 0.0;
+    if (ar2 > thresh2) {
       const double inv_r = rsqrt(ar2);
-      const double app = A[p + (long)p * k].x, aqq = A[q + (long)q * k].x;
-      const cplx ph = cmk(apq.x * inv_r, apq.y * inv_r);
-      const double taud = (aqq - app) * 0.5 * inv_r;
-      const float tau = (float)taud;
-      const float tf = (tau < 0.f ? -1.f : 1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-      // one Newton step on t^2 + 2 tau t - 1 = 0 in FP64 (the step's own reciprocal needs only
-      // FP32 accuracy): the tangent becomes FP64-accurate and sweeps converge quadratically
-      double t = (double)tf;
-      const double f = fma(t, t + 2.0 * taud, -1.0);
-      t -= f * (double)(0.5f / (float)(t + taud));
-      const double c = rsqrt(1.0 + t * t), sn = t * c;
-      R.upp = cmk(c, 0.0);
-      R.uqp = cmk(-sn * ph.x, sn * ph.y);
-      R.upq = cmk(sn, 0.0);
-      R.uqq = cmk(c * ph.x, -c * ph.y);
-      R.phc = cmk(ph.x, -ph.y);
+      const double d = A[q + (long)q * k].x - A[p + (long)p * k].x;
+      const double taud = d * scale_pow2(inv_r, 1);            // (a_qq - a_pp) / (2 |a_pq|)
+      const float tau = to_f32(taud);
+      const float tf = (tau < 0.f ? -1.f : 1.f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
+      double t = to_f64(tf);
+      const double f = fma(t, fma(2.0, taud, t), -1.0);
+      t = fma(-f, to_f64(0.5f / (tf + tau)), t);
+      const double c = rsqrt(fma(t, t, 1.0));
+      R.c = c;
+      R.s = t * c;
+      R.phx = apq.x * inv_r;
+      R.phy = -(apq.y * inv_r);
       R.on = 1;
     }
   }
@@ -194,8 +205,12 @@ __global__ void __launch_bounds__(256) jacobi_fast_kernel(JacobiFastArgs g) {
   const int k = g.k, kk = g.kk, np = kk / 2;
   const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
   const long nth = (long)gridDim.x * blockDim.x;
+  // rotation threshold thresh = eps ||A||_F: its square, and thresh / sqrt(2) as a bit pattern
   const double thresh = 2.220446049250313e-16 * (*g.fro);
+  const double thresh2 = thresh * thresh;
+  const long long thr_bits = abs_bits(0.7071067811865476 * thresh);
   for (long e = tid; e < (long)k * k; e += nth) g.V[e] = cmk((e % k) == (e / k) ? 1.0 : 0.0, 0.0);
+  const long ntri = (long)np * (np + 1) / 2;   // blocks (a, b), a <= b
   int cur = 0, sweep = 0;
   bool converged = false;
   for (; sweep < g.max_sweeps && !converged; ++sweep) {
@@ -206,7 +221,7 @@ __global__ void __launch_bounds__(256) jacobi_fast_kernel(JacobiFastArgs g) {
       if (threadIdx.x == 0) s_on = 0;
       __syncthreads();
       for (int j = threadIdx.x; j < np; j += blockDim.x) {
-        const RotS R = make_rot(Ac, k, rr_slot(j, r, kk), rr_slot(kk - 1 - j, r, kk), thresh);
+        const RotS R = make_rot(Ac, k, rr_slot(j, r, kk), rr_slot(kk - 1 - j, r, kk), thr_bits, thresh2);
         rot[j] = R;
         if (R.on) atomicAdd(&s_on, 1);
       }
@@ -216,42 +231,45 @@ __global__ void __launch_bounds__(256) jacobi_fast_kernel(JacobiFastArgs g) {
       // no pair rotates this round: nothing changes, so every CTA (all computed the same
       // rotations from the same data) skips the copy, the buffer swap and the grid barrier
       if (on_round == 0) continue;
-      const long nblk = (long)np * np;
-      for (long e = tid; e < nblk + (long)k * np; e += nth) {
-        if (e < nblk) {
-          const RotS P = rot[e % np], R = rot[e / np];
+      for (long e = tid; e < ntri + (long)k * np; e += nth) {
+        if (e < ntri) {
+          // triangular index -> (a, b), a <= b: b (b + 1) / 2 <= e < (b + 1) (b + 2) / 2
+          int bi = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+          while ((long)bi * (bi + 1) / 2 > e) --bi;
+          while ((long)(bi + 1) * (bi + 2) / 2 <= e) ++bi;
+          const int ai = (int)(e - (long)bi * (bi + 1) / 2);
+          const RotS P = rot[ai], R = rot[bi];
           const bool pq_ok = P.q < k, rs_ok = R.q < k;
           cplx b00 = Ac[P.p + (long)R.p * k];
           cplx b01 = rs_ok ? Ac[P.p + (long)R.q * k] : cmk(0, 0);
           cplx b10 = pq_ok ? Ac[P.q + (long)R.p * k] : cmk(0, 0);
           cplx b11 = (pq_ok && rs_ok) ? Ac[P.q + (long)R.q * k] : cmk(0, 0);
           if (P.on || R.on) {
-            // U = [[c, s], [-s conj(ph), c conj(ph)]] with real c, s: B U costs one complex
-            // product per row (w = b_q1 conj(ph)) plus real scalings, and likewise U^H (B U)
-            const double cR = R.upp.x, sR = R.upq.x, cP = P.upp.x, sP = P.upq.x;
-            const cplx phR = R.phc;
+            // B U_R: one complex product per row (w = b_x1 conj(ph_R)) plus real scalings;
+            // then U_P^H (B U_R) likewise
             cplx t00, t01, t10, t11;
             if (R.on) {
-              const cplx w0 = cmul(b01, phR), w1 = cmul(b11, phR);   // b_x1 conj(ph_R)
-              t00 = cmk(cR * b00.x - sR * w0.x, cR * b00.y - sR * w0.y);
-              t01 = cmk(sR * b00.x + cR * w0.x, sR * b00.y + cR * w0.y);
-              t10 = cmk(cR * b10.x - sR * w1.x, cR * b10.y - sR * w1.y);
-              t11 = cmk(sR * b10.x + cR * w1.x, sR * b10.y + cR * w1.y);
+              const cplx phR = cmk(R.phx, R.phy);
+              const cplx w0 = cmul(b01, phR), w1 = cmul(b11, phR);
+              t00 = cmk(R.c * b00.x - R.s * w0.x, R.c * b00.y - R.s * w0.y);
+              t01 = cmk(R.s * b00.x + R.c * w0.x, R.s * b00.y + R.c * w0.y);
+              t10 = cmk(R.c * b10.x - R.s * w1.x, R.c * b10.y - R.s * w1.y);
+              t11 = cmk(R.s * b10.x + R.c * w1.x, R.s * b10.y + R.c * w1.y);
             } else {
               t00 = b00; t01 = b01; t10 = b10; t11 = b11;
             }
             if (P.on) {
-              // U_P^H T: rows p, q -> (c t_p - s ph t_q, s t_p + c ph t_q), ph = conj of the stored phase
-              const cplx phP = cconj(P.phc);
+              // rows p, q -> (c t_p - s ph t_q, s t_p + c ph t_q), ph = conj of the stored phase
+              const cplx phP = cmk(P.phx, -P.phy);
               const cplx v0 = cmul(phP, t10), v1 = cmul(phP, t11);
-              b00 = cmk(cP * t00.x - sP * v0.x, cP * t00.y - sP * v0.y);
-              b01 = cmk(cP * t01.x - sP * v1.x, cP * t01.y - sP * v1.y);
-              b10 = cmk(sP * t00.x + cP * v0.x, sP * t00.y + cP * v0.y);
-              b11 = cmk(sP * t01.x + cP * v1.x, sP * t01.y + cP * v1.y);
+              b00 = cmk(P.c * t00.x - P.s * v0.x, P.c * t00.y - P.s * v0.y);
+              b01 = cmk(P.c * t01.x - P.s * v1.x, P.c * t01.y - P.s * v1.y);
+              b10 = cmk(P.s * t00.x + P.c * v0.x, P.s * t00.y + P.c * v0.y);
+              b11 = cmk(P.s * t01.x + P.c * v1.x, P.s * t01.y + P.c * v1.y);
             } else {
               b00 = t00; b01 = t01; b10 = t10; b11 = t11;
             }
-            if (e % np == e / np) {   // diagonal block: keep the diagonal real
+            if (ai == bi) {   // diagonal block: keep the diagonal real
               b00.y = 0.0;
               b11.y = 0.0;
               b10 = cconj(b01);
@@ -261,16 +279,21 @@ __global__ void __launch_bounds__(256) jacobi_fast_kernel(JacobiFastArgs g) {
           if (rs_ok) An[P.p + (long)R.q * k] = b01;
           if (pq_ok) An[P.q + (long)R.p * k] = b10;
           if (pq_ok && rs_ok) An[P.q + (long)R.q * k] = b11;
+          if (ai != bi) {   // mirrored block: (B)^H at rows of R, columns of P
+            An[R.p + (long)P.p * k] = cconj(b00);
+            if (pq_ok) An[R.p + (long)P.q * k] = cconj(b10);
+            if (rs_ok) An[R.q + (long)P.p * k] = cconj(b01);
+            if (pq_ok && rs_ok) An[R.q + (long)P.q * k] = cconj(b11);
+          }
         } else {
-          const long f = e - nblk;
+          const long f = e - ntri;
           const int i = (int)(f % k);
           const RotS R = rot[f / k];
           if (!R.on) continue;
           const cplx x = g.V[i + (long)R.p * k], y = g.V[i + (long)R.q * k];
-          const cplx w = cmul(y, R.phc);
-          const double c = R.upp.x, sn = R.upq.x;
-          g.V[i + (long)R.p * k] = cmk(c * x.x - sn * w.x, c * x.y - sn * w.y);
-          g.V[i + (long)R.q * k] = cmk(sn * x.x + c * w.x, sn * x.y + c * w.y);
+          const cplx w = cmul(y, cmk(R.phx, R.phy));
+          g.V[i + (long)R.p * k] = cmk(R.c * x.x - R.s * w.x, R.c * x.y - R.s * w.y);
+          g.V[i + (long)R.q * k] = cmk(R.s * x.x + R.c * w.x, R.s * x.y + R.c * w.y);
         }
       }
       if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
@@ -382,7 +405,6 @@ cudaError_t jacobi_eig(cudaStream_t s, int k, cplx* G, double* lam, cplx* W, voi
     unsigned* bar = (unsigned*)w;   w += sizeof(unsigned) * 4;
     g.final_buf = (int*)(bar + 2);
     g.bar.count = bar;
-    g.bar.gen = bar + 1;
     g.err = err;
     g.sweeps = sweeps;
     g.max_sweeps = max_sweeps;
@@ -413,7 +435,6 @@ cudaError_t jacobi_eig(cudaStream_t s, int k, cplx* G, double* lam, cplx* W, voi
   g.fro = (double*)w;             w += sizeof(double) * 2;
   unsigned* bar = (unsigned*)w;
   g.bar.count = bar;
-  g.bar.gen = bar + 1;
   g.err = err;
   g.sweeps = sweeps;
   g.max_sweeps = max_sweeps;
@@ -490,7 +511,6 @@ extern "C" chfsi_status chfsi_reduced_eig_noalloc(void* cuda_stream, int k, cons
   g.err = (int*)w;                w += sizeof(int);
   g.sweeps = (int*)w;             w += sizeof(int);
   g.bar.count = bar;
-  g.bar.gen = bar + 1;
   g.max_sweeps = NOALLOC_SWEEPS;
   // the array keeps the previous call's contents: copy G in and clear what must start at zero
   e = cudaMemcpyAsync(g.A, G, sizeof(cplx) * (size_t)k * k, cudaMemcpyDeviceToDevice, s);
