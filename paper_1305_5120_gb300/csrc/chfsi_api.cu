@@ -293,8 +293,10 @@ chfsi_status transform(chfsi_ctx* c, int n, const cplx* H, const cplx* Linv, cpl
   cplx* W;
   TRY(buf(c, "tmp_nn", (size_t)n * n, &W));
   TRY(gemm64(c, gemm_args(n, n, n, OP_N, Linv, n, OP_N, H, n, W, n, ONE, ZERO, TRI_A_LOWER)));
-  TRY(gemm64(c, gemm_args(n, n, n, OP_N, W, n, OP_C, Linv, n, Hs, n, ONE, ZERO, TRI_B_UPPER)));
-  CU(hermitize(c->stream, n, Hs, n));
+  // H' is Hermitian: its lower triangle is computed (the digit GEMM skips the tiles above the
+  // diagonal) and mirrored
+  TRY(gemm64(c, gemm_args(n, n, n, OP_N, W, n, OP_C, Linv, n, Hs, n, ONE, ZERO, TRI_B_UPPER | TRI_C_LOWER)));
+  CU(herm_from_lower(c->stream, n, Hs, n));
   return CHFSI_OK;
 }
 

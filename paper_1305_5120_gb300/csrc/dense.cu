@@ -127,6 +127,15 @@ __global__ void hermitize_kernel(int n, cplx* A, long lda) {
   }
 }
 
+// upper triangle <- conjugate of the lower one, diagonal made real
+__global__ void herm_from_lower_kernel(int n, cplx* A, long lda) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)n * n; e += (long)gridDim.x * blockDim.x) {
+    const long r = e % n, c = e / n;
+    if (r < c) A[r + c * lda] = cconj(A[c + r * lda]);
+    else if (r == c) A[r + c * lda].y = 0.0;
+  }
+}
+
 __global__ void gather_columns_kernel(int n, int cnt, const int* perm, const cplx* src, long lds, cplx* dst, long ldd) {
   const int j = blockIdx.y;
   if (j >= cnt) return;
@@ -259,6 +268,11 @@ cudaError_t trtri_lower(cudaStream_t s, int n, const cplx* L, long ldl, cplx* X,
 
 cudaError_t hermitize(cudaStream_t s, int n, cplx* A, long lda) {
   hermitize_kernel<<<grid_for((long)n * n), 256, 0, s>>>(n, A, lda); count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t herm_from_lower(cudaStream_t s, int n, cplx* A, long lda) {
+  herm_from_lower_kernel<<<grid_for((long)n * n), 256, 0, s>>>(n, A, lda); count_launch();
   return cudaGetLastError();
 }
 

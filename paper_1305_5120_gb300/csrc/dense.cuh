@@ -10,6 +10,8 @@ cudaError_t chol_lower(cudaStream_t s, int n, cplx* A, long lda, int* err);
 cudaError_t trtri_lower(cudaStream_t s, int n, const cplx* L, long ldl, cplx* X, long ldx, int* err);
 // A <- (A + A^H) / 2 (diagonal made real).
 cudaError_t hermitize(cudaStream_t s, int n, cplx* A, long lda);
+// Upper triangle <- conjugate transpose of the lower one (diagonal made real).
+cudaError_t herm_from_lower(cudaStream_t s, int n, cplx* A, long lda);
 // dst[:, j] = src[:, perm[j]] for j < cnt (n rows); and lam_dst[j] = lam_src[perm[j]].
 cudaError_t gather_columns(cudaStream_t s, int n, int cnt, const int* perm, const cplx* src, long lds,
                            cplx* dst, long ldd);

@@ -186,6 +186,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (kc_end < (1 << 30)) kb1 = min(kb1, (2 * kc_end + BK - 1) / BK);
   }
   const int nkb = max(0, kb1 - kb0);
+  // output tile strictly above the diagonal of a lower-triangle-only product: nothing to do
+  // (uniform over the CTA, before any barrier or TMEM allocation)
+  if ((g.tri & TRI_C_LOWER) && m0 + BM - 1 < n0 / 2) return;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {

@@ -8,7 +8,9 @@ enum GemmTri {                        // zero structure of op(A) / op(B) (K-rang
   TRI_A_LOWER = 1,   // op(A)[i,k] = 0 for k > i
   TRI_A_UPPER = 2,   // op(A)[i,k] = 0 for k < i
   TRI_B_UPPER = 4,   // op(B)[k,j] = 0 for k > j
-  TRI_B_LOWER = 8    // op(B)[k,j] = 0 for k < j
+  TRI_B_LOWER = 8,   // op(B)[k,j] = 0 for k < j
+  TRI_C_LOWER = 16   // only C[i,j], i >= j, is wanted: tiles strictly above the diagonal may be
+                     // skipped (left unwritten) -- honoured by the digit-expansion GEMM
 };
 enum GemmEpi { EPI_GEMM = 0, EPI_FILTER = 1 };
 
