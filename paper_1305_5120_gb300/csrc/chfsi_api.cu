@@ -318,7 +318,9 @@ chfsi_status lanczos_run(chfsi_ctx* c, int n, int steps, int k, const cplx* v0, 
     TRY(op(v, w));
     CU(lanczos_step(c->stream, n, j, v, vp, w, alpha, beta));
   }
-  CU(lanczos_bounds(c->stream, steps, n, k, alpha, beta, bounds));
+  double* eig;
+  TRY(buf(c, "lz_eig", 2 * (size_t)steps, &eig));
+  CU(lanczos_bounds(c->stream, steps, n, k, alpha, beta, bounds, eig));
   return CHFSI_OK;
 }
 

@@ -65,21 +65,28 @@ __global__ void lanczos_step_kernel(int n, int j, cplx* v, cplx* vp, cplx* w, do
 }
 
 // Number of eigenvalues of tridiag(beta, alpha, beta) below x: sign changes of the Sturm
-// sequence p_0 = 1, p_i = (alpha_i - x) p_{i-1} - beta_{i-1}^2 p_{i-2} (no division: FP64
-// division is a long latency chain here); rescaled by 2^-256 when it grows past 2^256.
-__device__ int sturm_count(int m, const double* al, const double* be, double x) {
+// sequence p_0 = 1, p_i = (alpha_i - x) p_{i-1} - beta_{i-1}^2 p_{i-2} (b2[i] = beta_{i-1}^2,
+// b2[0] = 0).  Cost model of this GPU's FP64 pipe (a warp-wide FP64 instruction, compares
+// included, holds a sub-partition's FP64 unit for about 64 cycles): three FP64 instructions
+// per step; the sign tests, the zero fix-up and the rescaling by 2^-256 when |p| passes 2^256
+// are integer operations on the bit patterns.
+__device__ int sturm_count(int m, const double* al, const double* b2, double x) {
   int cnt = 0;
   double pm2 = 0.0, pm1 = 1.0;
   for (int i = 0; i < m; ++i) {
-    const double b2 = (i > 0) ? be[i - 1] * be[i - 1] : 0.0;
-    double p = (al[i] - x) * pm1 - b2 * pm2;
-    if (p == 0.0) p = -1e-300 * (pm1 < 0.0 ? -1.0 : 1.0);   // a zero takes the sign opposite to p_{i-1}
-    if ((p < 0.0) != (pm1 < 0.0)) ++cnt;
+    double p = fma(al[i] - x, pm1, -(b2[i] * pm2));
+    long long pb = __double_as_longlong(p);
+    const long long qb = __double_as_longlong(pm1);
+    if ((pb & 0x7FFFFFFFFFFFFFFFLL) == 0) {   // a zero takes the sign opposite to p_{i-1}
+      pb = (~qb & (long long)0x8000000000000000ULL) | __double_as_longlong(1e-300);
+      p = __longlong_as_double(pb);
+    }
+    cnt += (int)(((unsigned long long)(pb ^ qb)) >> 63);
     pm2 = pm1;
     pm1 = p;
-    if (fabs(pm1) > 0x1.0p256) {
-      pm1 *= 0x1.0p-256;
-      pm2 *= 0x1.0p-256;
+    if ((int)((pb >> 52) & 0x7FF) > 1023 + 256) {
+      pm1 = scale_pow2(pm1, 256);
+      pm2 = scale_pow2(pm2, 256);
     }
   }
   return cnt;
@@ -87,7 +94,7 @@ __device__ int sturm_count(int m, const double* al, const double* be, double x) 
 
 // index-th smallest eigenvalue (0-based) by warp multisection: each step the 32 lanes count
 // at 32 interior points of [lo, hi] and the bracket shrinks 33-fold (the whole warp calls it)
-__device__ double tridiag_eig_multisect(int m, const double* al, const double* be, int index) {
+__device__ double tridiag_eig_multisect(int m, const double* al, const double* be, const double* b2, int index) {
   const int lane = threadIdx.x & 31;
   double lo = al[0], hi = al[0];
   for (int i = 0; i < m; ++i) {
@@ -96,14 +103,15 @@ __device__ double tridiag_eig_multisect(int m, const double* al, const double* b
     hi = fmax(hi, al[i] + r);
   }
   lo -= 1e-300;
+  const double cl = to_f64((float)(lane + 1));   // exact small integers without a conversion
   for (int it = 0; it < 14; ++it) {
-    const double h = (hi - lo) / 33.0;
-    const double x = lo + h * (lane + 1);
-    const bool below = sturm_count(m, al, be, x) <= index;   // eigenvalue index is >= x
+    const double h = (hi - lo) * (1.0 / 33.0);
+    const double x = fma(h, cl, lo);
+    const bool below = sturm_count(m, al, b2, x) <= index;   // eigenvalue index is >= x
     const unsigned bal = __ballot_sync(0xffffffffu, below);
-    const int j = __popc(bal);                              // points at or below the eigenvalue
-    const double nlo = (j == 0) ? lo : lo + h * j;
-    const double nhi = (j == 32) ? hi : lo + h * (j + 1);
+    const int j = __popc(bal);                                // points at or below the eigenvalue
+    const double nlo = (j == 0) ? lo : fma(h, to_f64((float)j), lo);
+    const double nhi = (j == 32) ? hi : fma(h, to_f64((float)(j + 1)), lo);
     if (!(nhi - nlo < hi - lo)) break;
     lo = nlo;
     hi = nhi;
@@ -111,37 +119,61 @@ __device__ double tridiag_eig_multisect(int m, const double* al, const double* b
   return 0.5 * (lo + hi);
 }
 
-__global__ void lanczos_bounds_kernel(int steps, int n, int k, const double* alpha, const double* beta,
-                                      double* out) {
-  __shared__ double al[256], be[256], mu[256], th[256], w[256];
-  const int m = steps;
+// All Ritz values mu (eigenvalues of T) and the eigenvalues theta of its trailing block
+// T(2:m, 2:m): one single-warp CTA per eigenvalue, so that each search has a sub-partition's
+// FP64 unit to itself.  eig[0 .. m) = mu, eig[m .. 2m-1) = theta.
+__global__ void tridiag_eigs_kernel(int m, const double* alpha, const double* beta, double* eig) {
+  __shared__ double al[256], be[256], b2[256];
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     al[i] = alpha[i];
     be[i] = beta[i];
   }
   __syncthreads();
-  // all Ritz values (eigenvalues of T) and the eigenvalues of its trailing block T(2:m, 2:m),
-  // one warp per eigenvalue
-  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
-  for (int idx = warp; idx < 2 * m - 1; idx += nw) {
-    if (idx < m) {
-      const double v = tridiag_eig_multisect(m, al, be, idx);
-      if (lane == 0) mu[idx] = v;
-    } else {
-      const double v = tridiag_eig_multisect(m - 1, al + 1, be + 1, idx - m);
-      if (lane == 0) th[idx - m] = v;
-    }
-  }
+  const int idx = blockIdx.x;
+  const int off = idx < m ? 0 : 1;   // trailing block: alpha_2.., beta_2..
+  const int mm = m - off;
+  for (int i = threadIdx.x; i < mm; i += blockDim.x) b2[i] = (i > 0) ? be[off + i - 1] * be[off + i - 1] : 0.0;
   __syncthreads();
+  const double v = tridiag_eig_multisect(mm, al + off, be + off, b2, idx < m ? idx : idx - m);
+  if (threadIdx.x == 0) eig[idx] = v;
+}
+
+// x = m 2^e kept with m in [1, 2): products of many factors without logarithms or overflow
+struct MantExp {
+  double m;
+  int e;
+};
+__device__ __forceinline__ void me_mul(MantExp& a, double f) {   // f > 0, normal
+  const long long b = __double_as_longlong(f);
+  a.e += (int)((b >> 52) & 0x7FF) - 1023;
+  a.m *= __longlong_as_double((b & 0x000FFFFFFFFFFFFFLL) | (1023LL << 52));
+  const long long mb = __double_as_longlong(a.m);   // m in [1, 4): renormalise
+  const int me = (int)((mb >> 52) & 0x7FF) - 1023;
+  a.e += me;
+  a.m = __longlong_as_double((mb & 0x000FFFFFFFFFFFFFLL) | (1023LL << 52));
+}
+
+__global__ void lanczos_bounds_kernel(int steps, int n, int k, const double* alpha, const double* beta,
+                                      const double* eig, double* out) {
+  __shared__ double al[256], be[256], rb[256], w[256];
+  const int m = steps;
+  const double* mu = eig;
+  const double* th = eig + m;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    al[i] = alpha[i];
+    be[i] = beta[i];
+    rb[i] = 1.0 / beta[i];   // reciprocals in parallel: the recurrence below then multiplies
+  }
   // Gauss weights w_i = z_1(mu_i)^2 = prod_j (mu_i - theta_j) / prod_{j != i} (mu_i - mu_j)
   // (the squared first component of the i-th eigenvector of T, from the interlacing
-  // eigenvalues of the trailing block; positive by interlacing)
+  // eigenvalues of the trailing block; positive by interlacing), as mantissa-exponent products
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    double lg = 0.0;
-    for (int j = 0; j < m - 1; ++j) lg += log(fabs(mu[i] - th[j]) + 1e-300);
+    MantExp num{1.0, 0}, den{1.0, 0};
+    const double mi = mu[i];
+    for (int j = 0; j < m - 1; ++j) me_mul(num, fabs(mi - th[j]) + 1e-300);
     for (int j = 0; j < m; ++j)
-      if (j != i) lg -= log(fabs(mu[i] - mu[j]) + 1e-300);
-    w[i] = exp(lg);
+      if (j != i) me_mul(den, fabs(mi - mu[j]) + 1e-300);
+    w[i] = ldexp(num.m / den.m, num.e - den.e);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -152,7 +184,7 @@ __global__ void lanczos_bounds_kernel(int steps, int n, int k, const double* alp
     // top Ritz pair) plus 1e-3 of the Ritz spread
     double zm1 = 0.0, z = 1.0, ss = 1.0;
     for (int i = 0; i + 1 < m; ++i) {
-      const double zn = ((mu_max - al[i]) * z - (i > 0 ? be[i - 1] * zm1 : 0.0)) / be[i];
+      const double zn = ((mu_max - al[i]) * z - (i > 0 ? be[i - 1] * zm1 : 0.0)) * rb[i];
       zm1 = z;
       z = zn;
       ss += z * z;
@@ -217,9 +249,10 @@ cudaError_t lanczos_step(cudaStream_t s, int n, int j, cplx* v, cplx* v_prev, cp
 }
 
 cudaError_t lanczos_bounds(cudaStream_t s, int steps, int n, int k, const double* alpha, const double* beta,
-                           double* out) {
+                           double* out, double* scratch) {
   if (steps < 2 || steps > 256) return cudaErrorInvalidValue;
-  lanczos_bounds_kernel<<<1, 1024, 0, s>>>(steps, n, k, alpha, beta, out); count_launch();
+  tridiag_eigs_kernel<<<2 * steps - 1, 32, 0, s>>>(steps, alpha, beta, scratch); count_launch();
+  lanczos_bounds_kernel<<<1, 256, 0, s>>>(steps, n, k, alpha, beta, scratch, out); count_launch();
   return cudaGetLastError();
 }
 

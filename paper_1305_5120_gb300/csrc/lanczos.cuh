@@ -14,9 +14,11 @@ cudaError_t lanczos_step(cudaStream_t s, int n, int j, cplx* v, cplx* v_prev, cp
 // From T = tridiag(beta, alpha, beta) of `steps` steps: out[0] = b_sup = mu_max + |beta_last| |z_last|
 // + 1e-3 (mu_max - mu_min); out[1] = a, the Lanczos density-of-states estimate of lambda_{k+1}
 // (first Ritz value from the second on whose cumulative Gauss weight reaches k / n);
-// out[2] = a0 = mu_min; out[3] = mu_max.  Eigenvalues of T by Sturm-count multisection.
+// out[2] = a0 = mu_min; out[3] = mu_max.  Eigenvalues of T by Sturm-count multisection, one
+// CTA per eigenvalue; scratch holds 2 steps doubles (the eigenvalues of T and of its trailing
+// block).
 cudaError_t lanczos_bounds(cudaStream_t s, int steps, int n, int k, const double* alpha, const double* beta,
-                           double* out);
+                           double* out, double* scratch);
 // m_i = clamp(ceil(ln(tol / r_i) / ln(rho_i)), m_min, m_max), rho_i = 1 / (|t_i| + sqrt(t_i^2 - 1)),
 // t_i = (lam_i - c) / e; m_min for converged vectors, m_max inside the damped interval.
 cudaError_t vector_degrees(cudaStream_t s, int k, const double* lam, const double* res, double a, double b,
