@@ -347,9 +347,13 @@ chfsi_status kappa_L(chfsi_ctx* c, int n, const cplx* S, const cplx* Linv, doubl
     return CHFSI_OK;
   };
   TRY(lanczos_run(c, n, steps, 1, nullptr, 1, opS, al, be, bd));
+  // S^{-1} v = L^{-H} (L^{-1} v): a chunked lower-triangular GEMV, then the column-per-warp
+  // GEMV, which gives L^{-H} t from L^{-1}'s columns
+  cplx* part;
+  TRY(buf(c, "lz_part", (size_t)n * ((n + 63) / 64), &part));
   auto opSi = [&](const cplx* v, cplx* w) -> chfsi_status {
-    TRY(gemm(c, gemm_args(n, 1, n, OP_N, Linv, n, OP_N, v, n, t, n, ONE, ZERO, TRI_A_LOWER)));
-    TRY(gemm(c, gemm_args(n, 1, n, OP_C, Linv, n, OP_N, t, n, w, n, ONE, ZERO, TRI_A_UPPER)));
+    CU(lower_gemv(c->stream, n, Linv, n, v, t, part));
+    CU(herm_gemv(c->stream, n, Linv, n, t, w));
     return CHFSI_OK;
   };
   TRY(lanczos_run(c, n, steps, 1, nullptr, 1, opSi, al, be, bd + 4));

@@ -26,6 +26,36 @@ __global__ void herm_gemv_kernel(int n, const cplx* __restrict__ H, long ldh, co
   if (lane == 0) w[col] = cmk(re, im);
 }
 
+// w = A v for a lower-triangular A (column-major): CTA (rb, cb) takes 128 rows and a chunk of
+// GEMV_CHUNK columns (thread = row, coalesced column reads), writing a partial sum that
+// gemv_reduce_kernel adds in a fixed order; chunks wholly above the diagonal are skipped.
+constexpr int GEMV_ROWS = 128, GEMV_CHUNK = 64;
+__global__ void lower_gemv_partial_kernel(int n, const cplx* __restrict__ A, long lda, const cplx* __restrict__ v,
+                                          cplx* __restrict__ part) {
+  const long row = blockIdx.x * (long)GEMV_ROWS + threadIdx.x;
+  const int c0 = blockIdx.y * GEMV_CHUNK;
+  const long rmax = blockIdx.x * (long)GEMV_ROWS + GEMV_ROWS - 1;
+  double re = 0.0, im = 0.0;
+  if (row < n && c0 <= rmax) {
+    const int c1 = min(n, c0 + GEMV_CHUNK);
+    for (int c = c0; c < c1 && c <= row; ++c) {
+      const cplx a = __ldg(A + row + (long)c * lda), x = __ldg(v + c);
+      re = fma(a.x, x.x, re);
+      re = fma(-a.y, x.y, re);
+      im = fma(a.x, x.y, im);
+      im = fma(a.y, x.x, im);
+    }
+  }
+  if (row < n) part[(long)blockIdx.y * n + row] = cmk(re, im);
+}
+__global__ void gemv_reduce_kernel(int n, int chunks, const cplx* part, cplx* w) {
+  const long row = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  cplx s = cmk(0.0, 0.0);
+  for (int q = 0; q < chunks; ++q) s = cadd(s, part[(long)q * n + row]);
+  w[row] = s;
+}
+
 __global__ void normalize_kernel(int n, cplx* v) {
   __shared__ double sh[32];
   double s = 0.0;
@@ -234,6 +264,14 @@ __global__ void vector_degrees_kernel(int k, const double* lam, const double* re
 cudaError_t herm_gemv(cudaStream_t s, int n, const cplx* H, long ldh, const cplx* v, cplx* w) {
   const long threads = 32L * n;
   herm_gemv_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(n, H, ldh, v, w); count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t lower_gemv(cudaStream_t s, int n, const cplx* A, long lda, const cplx* v, cplx* w, cplx* part) {
+  const int chunks = (n + GEMV_CHUNK - 1) / GEMV_CHUNK;
+  dim3 grid((unsigned)((n + GEMV_ROWS - 1) / GEMV_ROWS), (unsigned)chunks);
+  lower_gemv_partial_kernel<<<grid, GEMV_ROWS, 0, s>>>(n, A, lda, v, part); count_launch();
+  gemv_reduce_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, chunks, part, w); count_launch();
   return cudaGetLastError();
 }
 

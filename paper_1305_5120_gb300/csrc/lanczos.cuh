@@ -3,8 +3,12 @@
 #include "common.cuh"
 
 // w = H v for Hermitian H (column-major): w_i = sum_r conj(H[r, i]) v_r, one warp per column
-// (each warp streams one contiguous column with 16-byte loads).
+// (each warp streams one contiguous column with 16-byte loads).  For any square H the same
+// call gives w = H^H v.
 cudaError_t herm_gemv(cudaStream_t s, int n, const cplx* H, long ldh, const cplx* v, cplx* w);
+// w = A v for lower-triangular A (column-major): partial sums over 64-column chunks (coalesced
+// column reads, chunks above the diagonal skipped) added in a fixed order.  part: n * ceil(n / 64).
+cudaError_t lower_gemv(cudaStream_t s, int n, const cplx* A, long lda, const cplx* v, cplx* w, cplx* part);
 // v <- v / ||v||   (single CTA)
 cudaError_t normalize_vec(cudaStream_t s, int n, cplx* v);
 // One Lanczos recurrence step on (v, v_prev, w = Op v):  alpha_j = Re(v^H w);
