@@ -94,10 +94,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_source_hash():
+# the sources a kernel's DRAM traffic depends on
+KERNEL_SOURCES = {
+    "ozaki_kernel": ["ozaki.cu", "ozaki.cuh", "zgemm.cuh", "common.cuh"],
+    "tc_filter_step_kernel": ["filter_tc.cu", "filter_tc.cuh", "common.cuh"],
+}
+
+
+def kernel_source_hash(kernel: str):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1305_5120_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -105,13 +112,14 @@ def kernel_source_hash():
 
 def traffic_for(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, when it was taken
-    on the current kernel sources (else None)."""
+    on the kernel's current sources (else None)."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
-        if t.get("source_hash") != kernel_source_hash():
+        e = t["kernels"][kernel]
+        if e.get("source_hash") != kernel_source_hash(kernel):
             return None
-        return t["kernels"][kernel]["bytes_per_launch"]
+        return e["bytes_per_launch"]
     except Exception:
         return None
 
