@@ -1061,8 +1061,11 @@ size_t chfsi_workspace_bytes(int n, int nev, int nex, int precision) {
   if (precision == CHFSI_PREC_MIXED) {
     const double np = std::ceil(N / 128) * 128, kp = std::ceil(2 * N / 64) * 64, kk = 2 * K + 64;
     b += 2.0 * 3 * np * kp + 2.0 * 2 * 3 * kk * kp + c16 * 3 * N * K;      // filter slices and state
-    // emulated GEMM digits (the n x n x n transform is the largest): 13 slices of A and of B
-    b += 2.0 * 13 * (np * kp + 2 * N * kp) + c16 * 4 * N * K;
+    // emulated GEMM digits (the n x n x n transform is the largest): 12 slices of A and of B;
+    // split-K partial sums: one n x n (or up to 16 n x k) FP64 product per exact K pass of
+    // 3584 real terms
+    const double passes = std::ceil(2 * N / 3584.0);
+    b += 2.0 * 12 * (np * kp + 2 * N * kp) + c16 * 4 * N * K + c16 * passes * std::max(N * N, 16 * N * K);
   }
   return (size_t)b;
 }
