@@ -157,6 +157,7 @@ struct JacobiFastArgs {
   int* err;
   int* sweeps;
   int* final_buf;
+  int* offcount;     // per sweep: off-diagonal entries above the threshold after it (zeroed)
   int max_sweeps;
 };
 
@@ -300,9 +301,26 @@ __global__ void __launch_bounds__(256) jacobi_fast_kernel(JacobiFastArgs g) {
       cur ^= 1;
     }
     converged = on_sweep == 0;
+    if (!converged && sweep + 1 < g.max_sweeps) {
+      // Convergence test without a rotation-free sweep: a sweep in which no pair rotates
+      // leaves A unchanged, so it rotates nothing exactly when no off-diagonal entry passes
+      // the rotation test now.  One scan (integer pre-filter, FP64 only for candidates), one
+      // counter, one grid barrier.
+      const cplx* Ac = g.A[cur];
+      int cnt = 0;
+      for (long e = tid; e < (long)k * k; e += nth) {
+        const int i = (int)(e % k), j = (int)(e / k);
+        if (i >= j) continue;
+        const cplx a = Ac[e];
+        if ((abs_bits(a.x) > thr_bits || abs_bits(a.y) > thr_bits) && fma(a.x, a.x, a.y * a.y) > thresh2) ++cnt;
+      }
+      if (cnt) atomicAdd(&g.offcount[sweep], cnt);
+      if (!grid_barrier(g.bar, gridDim.x, g.err)) return;
+      converged = *(volatile int*)&g.offcount[sweep] == 0;
+    }
   }
   if (tid == 0) {
-    *g.sweeps = sweep;
+    *g.sweeps = sweep;   // sweeps that rotated
     *g.final_buf = cur;
     if (!converged) atomicExch(g.err, DEV_ERR_NO_CONV);
   }
@@ -400,7 +418,7 @@ cudaError_t jacobi_eig(cudaStream_t s, int k, cplx* G, double* lam, cplx* W, voi
     g.A[1] = (cplx*)w;              w += sizeof(cplx) * (size_t)k * k;
     w += sizeof(Rot) * (size_t)(kk / 2);
     char* zero_begin = w;
-    w += sizeof(int) * max_sweeps;
+    g.offcount = (int*)w;           w += sizeof(int) * max_sweeps;
     g.fro = (double*)w;             w += sizeof(double) * 2;
     unsigned* bar = (unsigned*)w;   w += sizeof(unsigned) * 4;
     g.final_buf = (int*)(bar + 2);
