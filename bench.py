@@ -472,6 +472,102 @@ def run_ours(args):
     return 0 if not bad else 1
 
 
+# ----------------------------------------------------------------------------------------
+# Sequence-correlation study (the analogue of the paper's seeding experiment, Section 4 / Fig. 1b:
+# solving each problem of a sequence from the previous problem's Ritz vectors instead of a
+# random block), plus the angles between consecutive eigenvector subspaces (Section 2.2).
+def s_angles(X, Y, S):
+    """Angles between matched columns of X and Y in the S-inner product (radians)."""
+    SX, SY = S @ X, S @ Y
+    num = np.abs(np.sum(X.conj() * SY, axis=0))
+    den = np.sqrt(np.real(np.sum(X.conj() * SX, axis=0)) * np.real(np.sum(Y.conj() * SY, axis=0)))
+    return np.arccos(np.clip(num / den, 0.0, 1.0))
+
+
+def s_principal_angles(X, Y, S):
+    """Principal angles between span(X) and span(Y) in the S-inner product (radians,
+    ascending): orthonormalise L^H X and L^H Y (S = L L^H) and take arccos of the singular
+    values of their cross product."""
+    L = np.linalg.cholesky(S)
+    qx, _ = np.linalg.qr(L.conj().T @ X)
+    qy, _ = np.linalg.qr(L.conj().T @ Y)
+    sv = np.linalg.svd(qx.conj().T @ qy, compute_uv=False)
+    return np.sort(np.arccos(np.clip(sv, 0.0, 1.0)))
+
+
+def run_seeding(args):
+    """The n = 2000 sequence (20 problems) solved twice by the GPU path: (seeded) each problem
+    from the previous one's Ritz block and filter bounds (chfsi_next_in_sequence), (random)
+    each problem from the same random block (chfsi_solve).  Per problem: outer iterations,
+    filter column steps, device time (CUDA events on the solver stream), and the angles
+    between this problem's eigenvectors and the previous one's.  A second pair of runs lets S
+    vary along the sequence (S_l = S + 1e-2 0.7^l E_S, E_S Hermitian with ||E_S||_2 = 1; the
+    seeded run carries the block over as L_l^H L_{l-1}^{-H} Y)."""
+    import torch
+    from paper_1305_5120_gb300 import chfsi, synth
+    torch.cuda.set_device(0)
+    w = synth.SEQ_N2000
+    prec = chfsi.CHFSI_PREC_MIXED if args.precision == "mixed" else chfsi.CHFSI_PREC_FP64
+    Hs, S, X0 = make_inputs(w, w.seed)
+    n, nev, nex = w.n, w.nev, w.nex
+    ES = synth.hermitian_part(synth.complex_gaussian(synth.rng_for(w.seed, 77), (n, n)))
+    ES /= np.abs(np.linalg.eigvalsh(ES)).max()
+    S_var = [S + 1e-2 * 0.7 ** l * ES for l in range(len(Hs))]
+    Hd = [chfsi.colmajor(H) for H in Hs]
+    X0_d = chfsi.colmajor(X0)
+    ctx = chfsi.Context(device=0, precision=prec)
+    evals = torch.empty(nev, dtype=torch.float64, device="cuda")
+    X = torch.empty((nev, n), dtype=torch.complex128, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def run(seeded, Slist):
+        Sd = [chfsi.colmajor(Sm) for Sm in Slist]
+        rows, Xs = [], []
+        for l in range(len(Hd)):
+            torch.cuda.synchronize()
+            e0.record(ctx.stream)
+            if l == 0 or not seeded:
+                st, _, _, info = ctx.solve(Hd[l], Sd[l], n, nev, nex, X0_d, w.tol, w.degree, evals, X)
+            else:
+                st, _, _, info = ctx.next_in_sequence(Hd[l], Sd[l] if Slist is not S_fixed else None, evals, X)
+            e1.record(ctx.stream)
+            torch.cuda.synchronize()
+            Xh = chfsi.to_numpy(X)
+            lam = evals.cpu().numpy()
+            HX = Hs[l] @ Xh
+            res = float((np.linalg.norm(HX - (Slist[l] @ Xh) * lam[None, :], axis=0) / np.linalg.norm(HX, axis=0)).max())
+            rows.append({"status": int(st), "iterations": int(info.iterations), "ms": e0.elapsed_time(e1),
+                         "ms_reduce": float(info.ms_stage[0]), "filter_col_steps": int(info.filter_col_steps),
+                         "max_resid": res})
+            Xs.append(Xh)
+        return rows, Xs
+
+    S_fixed = [S] * len(Hs)
+    run(True, S_fixed)   # warm-up (allocations, first-use costs)
+    out = {"workload": "seeding study: sequence n=2000 x20 nev=200 nex=40 m=20", "precision": args.precision}
+    for name, Slist in (("S_fixed", S_fixed), ("S_varying", S_var)):
+        seeded, Xs = run(True, Slist)
+        rnd, _ = run(False, Slist)
+        ang = []
+        for l in range(1, len(Xs)):
+            a = s_angles(Xs[l - 1], Xs[l], Slist[l])
+            pa = s_principal_angles(Xs[l - 1], Xs[l], Slist[l])
+            ang.append({"median_vector_angle": float(np.median(a)), "max_vector_angle": float(a.max()),
+                        "max_principal_angle": float(pa[-1])})
+        sp_ms = [r["ms"] / s_["ms"] for r, s_ in zip(rnd[1:], seeded[1:])]
+        # without the reduction to standard form (the random solves also factor S again)
+        sp_it = [(r["ms"] - r["ms_reduce"]) / (s_["ms"] - s_["ms_reduce"]) for r, s_ in zip(rnd[1:], seeded[1:])]
+        sp_cs = [r["filter_col_steps"] / s_["filter_col_steps"] for r, s_ in zip(rnd[1:], seeded[1:])]
+        out[name] = {"seeded": seeded, "random": rnd, "angles": ang,
+                     "speedup_time_median": float(np.median(sp_ms)), "speedup_time_last5": float(np.median(sp_ms[-5:])),
+                     "speedup_iteration_time_median": float(np.median(sp_it)),
+                     "speedup_filter_steps_median": float(np.median(sp_cs)),
+                     "all_converged": all(r["status"] == 0 and r["max_resid"] <= 1e-10 for r in seeded + rnd)}
+    ctx.close()
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -480,7 +576,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--kernel-case", choices=["filter", "ozaki", "zgemm"], default=None)
-    ap.add_argument("--workload", choices=["sequence", "kpoints"], default="sequence")
+    ap.add_argument("--workload", choices=["sequence", "kpoints", "seeding"], default="sequence")
     ap.add_argument("--kpoints", type=int, default=64)
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--n", type=int, default=2000)
@@ -492,6 +588,8 @@ def main():
         return kernel_case(args)
     if args.workload == "kpoints":
         return run_kpoints(args)
+    if args.workload == "seeding":
+        return run_seeding(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
