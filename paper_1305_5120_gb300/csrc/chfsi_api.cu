@@ -1126,7 +1126,9 @@ chfsi_status chfsi_create(chfsi_ctx** out, int device, void* cuda_stream, const 
   if (s == CHFSI_OK) s = cu(cudaMalloc(&c->d_err, 2 * sizeof(int)), "err");
   if (s == CHFSI_OK) {
     c->d_sweeps = c->d_err + 1;
-    s = cu(cudaMemset(c->d_err, 0, 2 * sizeof(int)), "err");
+    // on the context's stream (which may be non-blocking), then waited for
+    s = cu(cudaMemsetAsync(c->d_err, 0, 2 * sizeof(int), c->stream), "err");
+    if (s == CHFSI_OK) s = cu(cudaStreamSynchronize(c->stream), "err");
   }
   for (int i = 0; i < 16 && s == CHFSI_OK; ++i) s = cu(cudaEventCreate(&c->ev[i]), "event");
   if (s == CHFSI_OK) s = cu(cudaMallocHost((void**)&c->sweeps_host, 64 * sizeof(int)), "pinned");

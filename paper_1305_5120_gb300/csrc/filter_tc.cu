@@ -445,7 +445,7 @@ void tc_filter_free(TcFilter* f) {
   delete f;
 }
 
-static chfsi_status tc_ensure(TcFilter* f, int n, int k) {
+static chfsi_status tc_ensure(TcFilter* f, int n, int k, cudaStream_t s) {
   if (n == f->n && k <= f->k && f->A) return CHFSI_OK;
   cudaFree(f->A);
   cudaFree(f->B[0]);
@@ -463,7 +463,9 @@ static chfsi_status tc_ensure(TcFilter* f, int n, int k) {
   CHFSI_CUDA_TRY(cudaMalloc(&f->A, sizeof(__nv_bfloat16) * 3 * f->mpad * f->kpad));
   for (int i = 0; i < 2; ++i) {
     CHFSI_CUDA_TRY(cudaMalloc(&f->B[i], sizeof(__nv_bfloat16) * 3 * f->npad * f->kpad));
-    CHFSI_CUDA_TRY(cudaMemset(f->B[i], 0, sizeof(__nv_bfloat16) * 3 * f->npad * f->kpad));
+    // stream-ordered: the caller's stream may be a non-blocking one, which the legacy default
+    // stream (a plain cudaMemset) does not order against the filter launches that follow
+    CHFSI_CUDA_TRY(cudaMemsetAsync(f->B[i], 0, sizeof(__nv_bfloat16) * 3 * f->npad * f->kpad, s));
   }
   for (int i = 0; i < 2; ++i) CHFSI_CUDA_TRY(cudaMalloc(&f->D[i], sizeof(cplx) * (size_t)n * k));
   CHFSI_CUDA_TRY(cudaMalloc(&f->R, sizeof(cplx) * (size_t)n * k));
@@ -482,7 +484,7 @@ chfsi_status tc_filter_run(TcFilter* f, cudaStream_t s, int n, const cplx* H, cp
                            const double* fa, const double* fb, const double* fg, const TcRefine* ref) {
   if (mmax < 1 || cnt[1] < 1) return CHFSI_OK;
   const int k = cnt[1];
-  chfsi_status st = tc_ensure(f, n, k);
+  chfsi_status st = tc_ensure(f, n, k, s);
   if (st != CHFSI_OK) return st;
   CHFSI_CUDA_TRY(cudaMemsetAsync(f->err, 0, sizeof(int), s));
   {
