@@ -102,11 +102,18 @@ KERNEL_SOURCES = {
 
 
 def kernel_source_hash(kernel: str):
+    """Hash of the kernel's sources with comments and blank space removed (a comment edit
+    does not change the kernel)."""
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1305_5120_gb300", "csrc")
     for f in KERNEL_SOURCES[kernel]:
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+        with open(os.path.join(csrc, f), "r") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        text = re.sub(r"\s+", " ", text)
+        h.update(f.encode() + text.encode())
     return h.hexdigest()[:16]
 
 

@@ -17,8 +17,9 @@
 //    real terms per pass every partial sum is an integer below 2^24 (level 0: 64 * 64 per
 //    term; level L: at most 2 * 64 * 16 + (L - 1) * 256), so the FP32 accumulation is exact
 //    even though the tensor core truncates;
-//  * the epilogue combines the 12 levels in FP64 and applies the scales: each entry carries
-//    61 bits relative to its row (column) scale before the final FP64 rounding -- the
+//  * the epilogue combines the 12 levels exactly in two 64-bit integers and rounds once to
+//    FP64 with the scales applied: each entry carries 61 bits relative to its row (column)
+//    scale before that rounding -- the
 //    expansion's error is relative to the largest entry of the row, not to the entry, and
 //    Hermitian matrices with a wide spectrum (large diagonal, small off-diagonal) need the
 //    extra digits to stay at FP64 accuracy.  Longer K runs in passes (split-K) whose FP64
