@@ -79,7 +79,7 @@ typedef struct {
   double ms_gemm_tc;       /* device time of the FP64-accurate tensor-core GEMMs (all stages) */
   double gemm_tc_flop;     /* their algorithmic work: 8 M N K_eff real flops per complex product */
   double ms_eig;           /* device time of the reduced eigensolver (Rayleigh-Ritz) */
-  int eig_sweeps;          /* Jacobi sweeps summed over the call */
+  int eig_sweeps;          /* Jacobi sweeps that rotated, summed over the call */
 } chfsi_info;
 
 /* Fills *p with the defaults listed above. */
@@ -134,9 +134,10 @@ unsigned long long chfsi_kernel_launches(void);
  * op = 'N' (as stored) or 'C' (conjugate transpose); op(A) is M x K, op(B) K x N, all
  * column-major with leading dimensions lda, ldb, ldc.  alpha, beta: host (re, im) pairs.
  * CHFSI_PREC_FP64 runs it on the FP64 pipe; CHFSI_PREC_MIXED as an error-free expansion in
- * BF16 digits on the tensor cores (13 digits of 5 bits per entry relative to its row or
- * column scale, exact integer accumulation per significance level, levels combined in
- * FP64: 65 bits of the row/column scale before the final FP64 rounding). */
+ * BF16 digits on the tensor cores (12 digits per entry relative to its row or column
+ * scale -- a 7-bit top digit and eleven of 5 bits --, exact integer accumulation per
+ * significance level, levels combined exactly in 64-bit integers: 61 bits of the
+ * row/column scale before the single FP64 rounding). */
 chfsi_status chfsi_gemm(chfsi_ctx *c, char opA, char opB, int M, int N, int K, const double *alpha,
                         const void *A, int lda, const void *B, int ldb, const double *beta, void *C,
                         int ldc, int precision);
