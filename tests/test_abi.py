@@ -35,3 +35,24 @@ def test_status_strings_without_gpu():
     assert b"positive definite" in lib.chfsi_status_string(2)
     p = chfsi.default_params()
     assert (p.degree, p.degree_min, p.degree_max, p.max_iter, p.lanczos_steps) == (20, 10, 25, 50, 20)
+
+
+def test_workspace_estimate_without_gpu():
+    """chfsi_workspace_bytes is host arithmetic (the serving loop admits sequences by it):
+    invalid sizes give 0; it grows with n and with the block; the mixed path needs more than
+    the FP64 one; and it covers what a mixed solve must hold at once -- the four n x n FP64
+    matrices (L, L^-1, H', the transform's temporary), the 12 BF16 digit planes of both
+    operands of the n x n x n transform (12 * (n * 2n + 2n * 2n) * 2 bytes) and its split-K
+    partial sums (one FP64 n x n product per 3584-term pass of the 2n real K terms)."""
+    ws = chfsi.workspace_bytes
+    fp64, mixed = chfsi.CHFSI_PREC_FP64, chfsi.CHFSI_PREC_MIXED
+    assert ws(0, 10, 2) == 0 and ws(100, 0, 2) == 0 and ws(100, 10, -1) == 0
+    for prec in (fp64, mixed):
+        assert ws(1000, 100, 20, prec) <= ws(2000, 100, 20, prec) <= ws(4000, 100, 20, prec)
+        assert ws(2000, 100, 20, prec) <= ws(2000, 200, 40, prec)
+    for n, nev, nex in [(512, 32, 16), (2000, 200, 40), (13000, 1300, 260)]:
+        k = nev + nex
+        assert ws(n, nev, nex, mixed) > ws(n, nev, nex, fp64) >= 16 * (4 * n * n + 2 * n * k)
+        passes = -(-2 * n // 3584)
+        need = 16 * 4 * n * n + 2 * 12 * (n * 2 * n + 2 * n * 2 * n) + 16 * passes * n * n
+        assert ws(n, nev, nex, mixed) >= need
