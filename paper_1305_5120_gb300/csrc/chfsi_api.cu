@@ -690,10 +690,12 @@ chfsi_status orthonormalize(chfsi_ctx* c, int n, int nl, const cplx* Yl, int k, 
 }
 
 // a7 ---------------------------------------------------------------------------------------
+// The device error word is not reset here: inside a solve it is zero at this point unless an
+// earlier kernel (a bounded wait in a GEMM) failed, and that failure must reach the solve's
+// check rather than be erased; the stage entry points reset it on entry.
 chfsi_status reduced_eig(chfsi_ctx* c, int k, cplx* G, double* lam, cplx* W) {
   char* work;
   TRY(buf(c, "jac_work", jacobi_work_bytes(k), &work));
-  CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   span_begin(c, 1, 0.0);
   CU(jacobi_eig(c->stream, k, G, lam, W, work, c->d_err, c->d_sweeps));
   span_end(c);
@@ -966,6 +968,9 @@ chfsi_status solve_common(chfsi_ctx* c, const cplx* H, const cplx* S, const cplx
   const int n = c->n, k = c->nev + c->nex;
   cudaEvent_t t0 = c->ev[14], t1 = c->ev[15];
   CU(cudaEventRecord(t0, c->stream));
+  // every solve starts with a clear device error word (a failed earlier call may have left
+  // one); within the solve it is only cleared after an expected Cholesky failure
+  CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   cplx *L, *Linv, *Hs, *Y;
   TRY(buf(c, "L", (size_t)n * n, &L));
   TRY(buf(c, "Linv", (size_t)n * n, &Linv));
@@ -1284,6 +1289,7 @@ chfsi_status chfsi_orthonormalize(chfsi_ctx* c, int n, int nl, const void* Ylock
 chfsi_status chfsi_rayleigh_ritz(chfsi_ctx* c, int n, int k, const void* Hs, void* Y, double* lam, void* Z) {
   if (!c || !valid_ptrs({Hs, Y, lam, Z}) || n < 1 || k < 1 || k > n) return CHFSI_ERR_ARG;
   TRY(setup_device(c));
+  CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   TRY(rayleigh_ritz(c, n, k, (const cplx*)Hs, (cplx*)Y, lam, (cplx*)Z));
   int e = 0;
   TRY(read_err(c, &e));
@@ -1293,6 +1299,7 @@ chfsi_status chfsi_rayleigh_ritz(chfsi_ctx* c, int n, int k, const void* Hs, voi
 chfsi_status chfsi_reduced_eig(chfsi_ctx* c, int k, const void* G, double* lam, void* W) {
   if (!c || !valid_ptrs({G, lam, W}) || k < 1) return CHFSI_ERR_ARG;
   TRY(setup_device(c));
+  CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   cplx* Gc;
   TRY(buf(c, "eig_G", (size_t)k * k, &Gc));
   CU(cudaMemcpyAsync(Gc, G, sizeof(cplx) * (size_t)k * k, cudaMemcpyDeviceToDevice, c->stream));
