@@ -221,33 +221,40 @@ def aggregate_replicas(ms_local: float, problems_local: int, device: str):
     return ms, problems, problems / (ms / 1000.0)
 
 
-def kernel_rooflines(infos, n):
+def kernel_rooflines(infos, n, fp64_peak):
     """Achieved rate of each kernel family over the timed region (device time from CUDA
-    events the library records on its own stream around the launches) against its peak;
-    the roofline line is the family with the largest device time."""
+    events the library records on its own stream around the launches) against its peak.
+    The roofline object describes the hot path -- the Chebyshev filter's tensor-core step
+    kernel -- and names the kernel family with the most device time."""
     pk, pk_kind = peaks()
     bf16 = pk["bf16_tflops_sustained"]
-    fp64_peak = pk["bf16_tflops"] * (1.25 / 2250.0)
     f_low = sum(i.ms_filter_lowp for _, i in infos)
     f_all = sum(i.ms_stage[2] for _, i in infos)
     cs_all = sum(i.filter_col_steps for _, i in infos)
     cs_low = sum(i.filter_col_steps_lowp for _, i in infos)
+    f_steps_ms = sum(i.ms_filter_steps for _, i in infos)
+    f_steps_cols = sum(i.filter_step_cols for _, i in infos)
     g_ms = sum(i.ms_gemm_tc for _, i in infos)
     g_flop = sum(i.gemm_tc_flop for _, i in infos)
     e_ms = sum(i.ms_eig for _, i in infos)
+    e_flop = sum(i.eig_flop for _, i in infos)
+    c_ms = sum(i.ms_chol for _, i in infos)
+    c_flop = sum(i.chol_flop for _, i in infos)
     per_col = 8.0 * n * n          # one column through one recurrence step (complex n x n times n)
+    fp64_note = "measured DFMA peak of this GPU (chfsi_fp64_peak: eight FMA chains per thread, all SMs)"
     k = {}
     if f_all - f_low > 0 and cs_all > cs_low:
         a = per_col * (cs_all - cs_low) / ((f_all - f_low) / 1e3) / 1e12
-        k["zgemm_kernel"] = {"role": "FP64 filter step", "bound": "tensor", "achieved": a, "peak": fp64_peak,
-                             "unit": "TFLOP/s", "frac": a / fp64_peak, "ms": f_all - f_low,
-                             "peak_note": f"FP64 = {pk_kind} bf16 burst x 1.25/2250 (nominal ratio)"}
-    if f_low > 0:
-        a = 6.0 * per_col * cs_low / (f_low / 1e3) / 1e12
-        k["tc_filter_step_kernel"] = {"role": "Chebyshev filter step, split-BF16", "bound": "tensor", "achieved": a,
-                                      "peak": bf16, "unit": "TFLOP/s", "frac": a / bf16, "ms": f_low,
-                                      "algorithmic_tflops": a / 6.0,
-                                      "peak_note": f"{pk_kind} bf16 sustained; 6 executed slice products"}
+        k["zgemm_kernel"] = {"role": "FP64 filter step (DFMA)", "bound": "alu", "achieved": a, "peak": fp64_peak,
+                             "unit": "TFLOP/s", "frac": a / fp64_peak, "ms": f_all - f_low, "peak_note": fp64_note}
+    if f_steps_ms > 0:
+        a = 6.0 * per_col * f_steps_cols / (f_steps_ms / 1e3) / 1e12
+        k["tc_filter_step_kernel"] = {"role": "Chebyshev filter step, split-BF16 (hot path)", "bound": "tensor",
+                                      "achieved": a, "peak": bf16, "unit": "TFLOP/s", "frac": a / bf16,
+                                      "ms": f_steps_ms, "column_steps": int(f_steps_cols),
+                                      "algorithmic_tflops": a / 6.0, "filter_stage_ms": f_low,
+                                      "peak_note": f"{pk_kind} bf16 sustained; 6 executed slice products "
+                                                   "(48 n^2 flops per column-step)"}
     if g_ms > 0:
         a = 78.0 * g_flop / (g_ms / 1e3) / 1e12
         k["ozaki_kernel"] = {"role": "FP64-accurate GEMM (12-digit BF16 expansion)", "bound": "tensor",
@@ -255,18 +262,25 @@ def kernel_rooflines(infos, n):
                              "fp64_equivalent_tflops": a / 78.0,
                              "peak_note": f"{pk_kind} bf16 sustained; 78 executed digit products"}
     if e_ms > 0:
+        a = e_flop / (e_ms / 1e3) / 1e12
         k["jacobi_fast_kernel"] = {"role": "reduced eigensolver (FP64, grid barriers)", "bound": "alu",
+                                   "achieved": a, "peak": fp64_peak, "unit": "TFLOP/s", "frac": a / fp64_peak,
                                    "ms": e_ms, "sweeps": int(sum(i.eig_sweeps for _, i in infos)),
-                                   "peak": fp64_peak, "unit": "TFLOP/s"}
+                                   "rounds": int(sum(i.eig_rounds for _, i in infos)),
+                                   "work_note": "28 k^2 flops per rotating round (A's Hermitian half and the "
+                                                "eigenvector accumulator)", "peak_note": fp64_note}
+    if c_ms > 0:
+        a = c_flop / (c_ms / 1e3) / 1e12
+        k["chol_inv_kernel"] = {"role": "Cholesky of S and its inverse (FP64)", "bound": "alu", "achieved": a,
+                                "peak": fp64_peak, "unit": "TFLOP/s", "frac": a / fp64_peak, "ms": c_ms,
+                                "work_note": "(8/3) n^3 flops per factorisation", "peak_note": fp64_note}
     roof = None
-    rated = {name: v for name, v in k.items() if "achieved" in v}
-    if rated:
-        dom = max(k, key=lambda name: k[name]["ms"])
-        pick = dom if dom in rated else max(rated, key=lambda name: rated[name]["ms"])
-        roof = {x: v for x, v in k[pick].items() if x in ("bound", "achieved", "peak", "unit", "frac")}
-        roof["kernel"] = pick
-        roof["dominant_by_time"] = dom
-        roof["traffic"] = traffic_for(pick)
+    hot = "tc_filter_step_kernel" if "tc_filter_step_kernel" in k else ("zgemm_kernel" if "zgemm_kernel" in k else None)
+    if hot:
+        roof = {x: v for x, v in k[hot].items() if x in ("bound", "achieved", "peak", "unit", "frac")}
+        roof["kernel"] = hot
+        roof["dominant_by_time"] = max(k, key=lambda name: k[name]["ms"])
+        roof["traffic"] = traffic_for(hot) if hot in KERNEL_SOURCES else None
     return k, roof
 
 
@@ -322,7 +336,7 @@ def run_kpoints(args):
 
     lines = {}
     for slots in sorted({1, args.slots}):
-        srv = serve.Server(device=0, slots=slots, keep_vectors=False,
+        srv = serve.Server(device=0, slots=slots, keep_vectors=False, check_inertia=args.check_inertia,
                            precision=chfsi.CHFSI_PREC_MIXED if args.precision == "mixed" else chfsi.CHFSI_PREC_FP64)
         srv.run(requests()[: min(4, len(probs))], realtime=False)          # warm-up
         recs = srv.run(requests(), realtime=False)
@@ -337,7 +351,10 @@ def run_kpoints(args):
                               "iterations": r.info["iterations"], "locked": r.info["locked"]})
         lines[slots] = dict(summ, wrong=bad, failures=fails[:8],
                             iterations=int(sum(r.info["iterations"] for r in recs)),
-                            eig_ms=float(sum(r.info["ms_eig"] for r in recs)))
+                            eig_ms=float(sum(r.info["ms_eig"] for r in recs)),
+                            completeness={str(v): int(sum(1 for r in recs if r.info["completeness"] == v))
+                                          for v in sorted({r.info["completeness"] for r in recs})},
+                            pairs_under_floor=int(sum(r.info["n_floor"] for r in recs)))
     best = lines[max(lines)]
     line = {"metric": METRIC, "value": best["eigenproblems_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1,
             "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -388,6 +405,8 @@ def run_ours(args):
     for _ in range(args.warmup):
         one_sequence(dev, S_d, [])
     torch.cuda.synchronize()
+    fp64_peak = chfsi.fp64_peak(local)
+    torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     if world > 1:
@@ -416,7 +435,7 @@ def run_ours(args):
     ms, problems, value = aggregate_replicas(ms, args.steps * w.steps, "cuda")
 
     # per-kernel accounting from the library's stream-ordered CUDA events
-    kernels, roof = kernel_rooflines(infos, n)
+    kernels, roof = kernel_rooflines(infos, n, fp64_peak)
     cs_all = sum(i.filter_col_steps for _, i in infos)
     cs_low = sum(i.filter_col_steps_lowp for _, i in infos)
     stages = np.sum([list(i.ms_stage) for _, i in infos], axis=0).tolist()
@@ -452,6 +471,32 @@ def run_ours(args):
         e2e = {"value": problems / (ms_e2e / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "wall_s": time.perf_counter() - t0}
 
+    # the plain-FP64 arm on the same sequence (every product on the DFMA pipe): one sequence
+    # after one warm-up problem, CUDA events on the same stream
+    fp64 = None
+    if not args.no_fp64_path and prec == chfsi.CHFSI_PREC_MIXED:
+        ctx64 = chfsi.Context(device=local, precision=chfsi.CHFSI_PREC_FP64)
+        ctx64.solve(dev[0], S_d, n, nev, nex, X0_d, w.tol, w.degree, evals, X)
+        infos64 = []
+        torch.cuda.synchronize()
+        e0.record(ctx64.stream)
+        st, *_, info = ctx64.solve(dev[0], S_d, n, nev, nex, X0_d, w.tol, w.degree, evals, X)
+        infos64.append((st, info))
+        for l in range(1, w.steps):
+            st, *_, info = ctx64.next_in_sequence(dev[l], None, evals, X)
+            infos64.append((st, info))
+        e1.record(ctx64.stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        k64, _ = kernel_rooflines(infos64, n, fp64_peak)
+        v64 = w.steps / (ms64 / 1000.0)
+        lam64 = evals.cpu().numpy()
+        fp64 = {"value": v64, "unit": UNIT, "ms_per_sequence": ms64, "problems": w.steps,
+                "failed_solves": int(sum(1 for st, _ in infos64 if st != 0)),
+                "iterations": int(sum(i.iterations for _, i in infos64)),
+                "filter_kernel": k64.get("zgemm_kernel"), "mixed_over_fp64": None,
+                "last_problem_evals_match_mixed": None}
+        ctx64.close()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, parts = oracle_sample(w)
@@ -471,7 +516,12 @@ def run_ours(args):
                 "iterations": int(sum(i.iterations for _, i in infos)), "failed_solves": len(bad),
                 "eig_sweeps": int(sum(i.eig_sweeps for _, i in infos)),
                 "last_problem_max_resid": resid,
-                "filter_col_steps": int(cs_all), "filter_col_steps_lowp": int(cs_low)}
+                "pairs_under_residual_floor": int(sum(i.n_floor for _, i in infos)),
+                "filter_col_steps": int(cs_all), "filter_col_steps_lowp": int(cs_low),
+                "fp64_peak_tflops": fp64_peak, "fp64_path": fp64}
+        if fp64:
+            fp64["mixed_over_fp64"] = value / fp64["value"]
+            fp64["last_problem_evals_match_mixed"] = float(np.abs(lam64 - lam).max())
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -590,6 +640,9 @@ def main():
     ap.add_argument("--k", type=int, default=240)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-path", action="store_true", help="skip the plain-FP64 arm of the default run")
+    ap.add_argument("--check-inertia", type=int, default=1, choices=[0, 1],
+                    help="k-points: count the eigenvalues below the gap after every solve")
     args = ap.parse_args()
     if args.kernel_case:
         return kernel_case(args)

@@ -39,7 +39,12 @@ typedef enum {
   CHFSI_ERR_CUDA = 5,      /* a CUDA runtime call failed (context unusable) */
   CHFSI_ERR_TIMEOUT = 6,   /* a bounded device-side wait ran out (kernel returned early) */
   CHFSI_ERR_STATE = 7,     /* call out of order (e.g. next_in_sequence before solve) */
-  CHFSI_ERR_NUMERIC = 8    /* NaN/Inf met in a residual or a filtered block */
+  CHFSI_ERR_NUMERIC = 8,   /* NaN/Inf met in a residual or a filtered block */
+  CHFSI_ERR_INCOMPLETE = 9 /* nev pairs passed the residual test but the completeness check
+                              failed: a Ritz value outside the returned set lies below the
+                              largest returned eigenvalue, or (check_inertia) the count of
+                              eigenvalues below the gap differs from nev.  Outputs are filled
+                              as for CHFSI_OK but are not the lowest nev eigenpairs. */
 } chfsi_status;
 
 enum {
@@ -62,6 +67,15 @@ typedef struct {
                               per pass (default 1e-6) */
   unsigned long long seed; /* SplitMix64 seed of the Lanczos start vectors and of the random
                               start block (default 0) */
+  int check_inertia;       /* 0 (default): after convergence, only the Ritz-value test below;
+                              1: also count the eigenvalues of H' below the gap sigma between the
+                              largest returned eigenvalue and the smallest other Ritz value
+                              (Sylvester: H' - sigma I + tau Y Y^H, Y the returned vectors, must
+                              be positive definite -- an FP32 Cholesky, valid while the gap
+                              exceeds the factorisation's backward error; smaller gaps are
+                              reported as inconclusive, not as failures).  Every solve checks
+                              that no unreturned Ritz value of the block lies below the largest
+                              returned eigenvalue. */
 } chfsi_params;
 
 typedef struct {
@@ -80,6 +94,19 @@ typedef struct {
   double gemm_tc_flop;     /* their algorithmic work: 8 M N K_eff real flops per complex product */
   double ms_eig;           /* device time of the reduced eigensolver (Rayleigh-Ritz) */
   int eig_sweeps;          /* Jacobi sweeps that rotated, summed over the call */
+  long long eig_rounds;    /* Jacobi rounds that rotated (each updates the whole k x k matrix and
+                              its eigenvector accumulator), summed over the call */
+  double eig_flop;         /* their algorithmic FP64 work: 28 k^2 real flops per rotating round */
+  int n_floor;             /* returned pairs whose residual was tested against the absolute floor
+                              (|lambda| < 1e-4 ||H'||: Res = ||H'y - lam y|| / (1e-4 ||H'||)) */
+  int completeness;        /* 1: Ritz-value test passed; 2: inertia count passed too; -1: inertia
+                              count inconclusive (gap below its resolution); 0: not reached */
+  double ms_filter_steps;  /* device time of the tensor-core recurrence steps alone (the step
+                              kernels of ms_filter_lowp, without operand slicing) */
+  long long filter_step_cols; /* column-steps those kernels processed (each: one complex column
+                              times the n x n H', 48 n^2 executed / 8 n^2 algorithmic flops) */
+  double ms_chol;          /* device time of the Cholesky factorisation of S and its inverse */
+  double chol_flop;        /* its algorithmic work: (8/3) n^3 real flops (factor and inverse) */
 } chfsi_info;
 
 /* Fills *p with the defaults listed above. */
@@ -127,6 +154,11 @@ const char *chfsi_status_string(chfsi_status s);
 /* Number of CUDA kernels this library has launched in this process (all contexts).  A
  * diagnostic for benchmarks; the paper has no counterpart. */
 unsigned long long chfsi_kernel_launches(void);
+
+/* Measured FP64 (DFMA) throughput of `device` in TFLOP/s (host double): eight independent FMA
+ * chains per thread on every SM, best of three timed launches.  The roofline denominator of
+ * the FP64 kernels; a diagnostic, the paper has no counterpart. */
+chfsi_status chfsi_fp64_peak(int device, double *tflops);
 
 /* ---- Stage entry points (each step of the solve on its own; device pointers) -------- */
 
@@ -198,8 +230,10 @@ chfsi_status chfsi_reduced_eig(chfsi_ctx *c, int k, const void *G, double *lam, 
  * legacy default stream) of the current device and the call returns when it is complete.
  * Scratch lives in one fixed device array of this library, sized for k <= 256
  * (CHFSI_NOALLOC_KMAX); larger k returns CHFSI_ERR_ARG.  The first call on a device looks
- * up that array's device address (a one-time set-up with the device current); make that
- * first call before any stream capture.  Every call on a device shares the array and
+ * up that array's device address (a one-time set-up with the device current).  Every call
+ * is synchronous: it reads the status word back to host memory and waits for the stream,
+ * so it must not be called while the stream is being captured into a CUDA graph.  Every
+ * call on a device shares the array and
  * re-initialises it, so calls whose work overlaps on the GPU (other streams, other host
  * threads) race and must be serialised by the caller; the same holds against solves of
  * other contexts running at that time, since both use grid-wide barriers.  Nothing is

@@ -13,7 +13,9 @@ Readings of the paper used here (each is also listed in the design notes):
   up to that scalar normalisation.  The shift is the "update of the diagonal" of Section 3.
 * Lanczos (Algorithm 1 line "Estimating the largest eigenvalue"; Zhou & Li 2011): k_L
   steps, no reorthogonalisation, start vector from the SplitMix64 generator; upper bound
-  b = max Ritz value + |beta_{k_L}|.
+  b = top Ritz value + |beta_{k_L}| |z_last| (the residual norm of the top Ritz pair, z its
+  eigenvector of T) + 1e-3 of the Ritz spread.  The condition estimate of L (kappa_L_estimate)
+  keeps the plainer bound max Ritz value + |beta_{k_L}|, which is never smaller.
 * The block holds nev + nex vectors; the lower end a of the damped interval is the largest
   Ritz value of the block, a0 (the normalisation point) the smallest.
 * Res(y, lam) is the relative residual ||H y - lam y|| / max(||H y||, 1e-4 ||H||) (||H||
@@ -301,7 +303,11 @@ def chfsi(H: np.ndarray, nev: int, nex: int, Y0: np.ndarray, tol: float, degree:
 
 def kappa_L_estimate(L: np.ndarray, seed: int = 0, steps: int = 20) -> float:
     """Upper estimate of cond_2(L) = sqrt(lam_max(S) / lam_min(S)) from two Lanczos runs:
-    on S = L L^H and on S^{-1} = L^{-H} L^{-1} (each bound = max Ritz value + |beta|)."""
+    on S = L L^H and on S^{-1} = L^{-H} L^{-1} (each bound = max Ritz value + |beta|).
+
+    Pinned (tests/test_oracle_kappa.py) on S with cond(S) = 10 exactly: sqrt(10) <= estimate
+    <= 2 sqrt(10) for any step count (each bound lies in [lam_max, 2 lam_max] since
+    |beta| <= ||S||), and the estimate equals sqrt(10) when Lanczos runs to exhaustion."""
     n = L.shape[0]
     v0 = splitmix_complex_block(seed, n, 1, stream=1)[:, 0]
 

@@ -2,7 +2,7 @@
  * Oracle (test infrastructure only): dense Hermitian eigen-kernels in plain C, FP64.
  *
  * Nothing in the CUDA library links, includes or calls this file; only the test suite,
- * the benchmark's CPU-baseline leg and the smoke check load it (through oracle/eig.py).
+ * the benchmark's CPU-baseline leg and the smoke check load it (through oracle/direct.py).
  *
  *  - oracle_tridiag_qr: eigenvalues (and optionally eigenvectors) of a real symmetric
  *    tridiagonal matrix by the implicit symmetric QR step with Wilkinson shift and

@@ -21,7 +21,8 @@ CHFSI_PREC_FP64 = 0
 CHFSI_PREC_MIXED = 1
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "S not HPD", 3: "not converged", 4: "out of memory",
-          5: "CUDA error", 6: "device wait timed out", 7: "call out of order", 8: "non-finite value"}
+          5: "CUDA error", 6: "device wait timed out", 7: "call out of order", 8: "non-finite value",
+          9: "completeness check failed"}
 
 
 class ChfsiError(RuntimeError):
@@ -33,7 +34,8 @@ class ChfsiError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("degree", ctypes.c_int), ("degree_min", ctypes.c_int), ("degree_max", ctypes.c_int),
                 ("per_vector_degree", ctypes.c_int), ("max_iter", ctypes.c_int), ("lanczos_steps", ctypes.c_int),
-                ("precision", ctypes.c_int), ("mixed_switch", ctypes.c_double), ("seed", ctypes.c_ulonglong)]
+                ("precision", ctypes.c_int), ("mixed_switch", ctypes.c_double), ("seed", ctypes.c_ulonglong),
+                ("check_inertia", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -41,14 +43,22 @@ class Info(ctypes.Structure):
                 ("filter_col_steps_lowp", ctypes.c_longlong), ("max_resid", ctypes.c_double),
                 ("kappa_L", ctypes.c_double), ("bounds", ctypes.c_double * 3), ("ms_stage", ctypes.c_double * 8),
                 ("ms_filter_lowp", ctypes.c_double), ("ms_gemm_tc", ctypes.c_double),
-                ("gemm_tc_flop", ctypes.c_double), ("ms_eig", ctypes.c_double), ("eig_sweeps", ctypes.c_int)]
+                ("gemm_tc_flop", ctypes.c_double), ("ms_eig", ctypes.c_double), ("eig_sweeps", ctypes.c_int),
+                ("eig_rounds", ctypes.c_longlong), ("eig_flop", ctypes.c_double), ("n_floor", ctypes.c_int),
+                ("completeness", ctypes.c_int), ("ms_filter_steps", ctypes.c_double),
+                ("filter_step_cols", ctypes.c_longlong), ("ms_chol", ctypes.c_double),
+                ("chol_flop", ctypes.c_double)]
 
     def as_dict(self):
         return {"iterations": self.iterations, "locked": self.locked, "filter_col_steps": self.filter_col_steps,
                 "filter_col_steps_lowp": self.filter_col_steps_lowp, "max_resid": self.max_resid,
                 "kappa_L": self.kappa_L, "bounds": list(self.bounds), "ms_stage": list(self.ms_stage),
                 "ms_filter_lowp": self.ms_filter_lowp, "ms_gemm_tc": self.ms_gemm_tc,
-                "gemm_tc_flop": self.gemm_tc_flop, "ms_eig": self.ms_eig, "eig_sweeps": self.eig_sweeps}
+                "gemm_tc_flop": self.gemm_tc_flop, "ms_eig": self.ms_eig, "eig_sweeps": self.eig_sweeps,
+                "eig_rounds": self.eig_rounds, "eig_flop": self.eig_flop, "n_floor": self.n_floor,
+                "completeness": self.completeness, "ms_filter_steps": self.ms_filter_steps,
+                "filter_step_cols": self.filter_step_cols,
+                "ms_chol": self.ms_chol, "chol_flop": self.chol_flop}
 
 
 _lib = None
@@ -64,6 +74,7 @@ _SIGS = {
     "chfsi_destroy": [_P],
     "chfsi_status_string": [_I],
     "chfsi_kernel_launches": [],
+    "chfsi_fp64_peak": [_I, ctypes.POINTER(_D)],
     "chfsi_workspace_bytes": [_I, _I, _I, _I],
     "chfsi_gemm": [_P, ctypes.c_char, ctypes.c_char, _I, _I, _I, ctypes.POINTER(_D), _P, _I, _P, _I,
                    ctypes.POINTER(_D), _P, _I, _I],
@@ -85,6 +96,13 @@ _SIGS = {
 
 def kernel_launches() -> int:
     return int(load().chfsi_kernel_launches())
+
+
+def fp64_peak(device: int = 0) -> float:
+    """Measured DFMA throughput of the device (TFLOP/s)."""
+    out = _D()
+    _check(load().chfsi_fp64_peak(device, ctypes.byref(out)), "chfsi_fp64_peak")
+    return float(out.value)
 
 
 def workspace_bytes(n, nev, nex, precision=CHFSI_PREC_MIXED) -> int:

@@ -109,9 +109,19 @@ struct chfsi_ctx {
   double* h_d = nullptr;    // 4 * kcap doubles
   int* h_i = nullptr;       // 2 * kcap ints
   int kcap = 0;
-  // device scalars
+  // device scalars: the solve's error word, the last eigensolve's sweep and round counts, and
+  // the status word of the QR's own Cholesky factorisations (a non-positive-definite Gram
+  // matrix there is an expected event that selects a fallback, so it must not share the word
+  // that carries the bounded-wait failures of every other kernel)
   int* d_err = nullptr;
   int* d_sweeps = nullptr;
+  int* d_rounds = nullptr;
+  int* d_err_qr = nullptr;
+  // host-side fault injection for tests (environment CHFSI_INJECT_GEMM_TIMEOUT=N when a solve
+  // starts): the N-th FP64-accurate product of that solve reports a bounded-wait timeout in
+  // the error word, as the kernel itself would
+  int fault_gemm = 0;
+  int gemm_calls = 0;
   // sequence state
   bool have_seq = false;
   int n = 0, nev = 0, nex = 0, degree = 20;
@@ -122,15 +132,18 @@ struct chfsi_ctx {
   // the next synchronisation point
   struct Span {
     cudaEvent_t a, b;
-    int kind;   // 0 tensor-core GEMM, 1 reduced eigensolver
+    int kind;   // 0 tensor-core GEMM, 1 reduced eigensolver, 2 Cholesky of S (and inverse)
     double flop;
   };
   std::vector<Span> spans;
   std::vector<cudaEvent_t> ev_pool;
-  double acc_ms[2] = {0, 0}, acc_flop = 0;
+  double acc_ms[3] = {0, 0, 0}, acc_flop = 0, acc_chol_flop = 0;
   int acc_sweeps = 0;
-  int* sweeps_host = nullptr;     // pinned ring of sweep counts copied after each eigensolve
+  long long acc_rounds = 0;
+  double acc_eig_flop = 0;
+  int* sweeps_host = nullptr;     // pinned ring of (sweeps, rounds) copied after each eigensolve
   int n_sweeps_pending = 0;
+  int pending_k[64] = {};         // matrix order of each pending eigensolve
 };
 
 namespace {
@@ -167,17 +180,29 @@ chfsi_status ensure_host(chfsi_ctx* c, int k) {
 }
 
 void spans_flush(chfsi_ctx* c);
+void sweeps_flush(chfsi_ctx* c);
 
-chfsi_status read_err(chfsi_ctx* c, int* dev_err) {
+// after a stream synchronisation: adds the pending eigensolves' sweep and round counts
+void sweeps_flush(chfsi_ctx* c) {
+  for (int q = 0; q < c->n_sweeps_pending && q < 64; ++q) {
+    const double k = c->pending_k[q];
+    c->acc_sweeps += c->sweeps_host[2 * q];
+    c->acc_rounds += c->sweeps_host[2 * q + 1];
+    c->acc_eig_flop += 28.0 * k * k * c->sweeps_host[2 * q + 1];
+  }
+  c->n_sweeps_pending = 0;
+}
+
+chfsi_status read_word(chfsi_ctx* c, const int* word, int* out) {
   int h = 0;
-  CU(cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(&h, word, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
   spans_flush(c);
-  for (int q = 0; q < c->n_sweeps_pending && q < 64; ++q) c->acc_sweeps += c->sweeps_host[q];
-  c->n_sweeps_pending = 0;
-  *dev_err = h;
+  sweeps_flush(c);
+  *out = h;
   return CHFSI_OK;
 }
+chfsi_status read_err(chfsi_ctx* c, int* dev_err) { return read_word(c, c->d_err, dev_err); }
 
 chfsi_status map_dev_err(int e) {
   switch (e) {
@@ -239,6 +264,7 @@ void spans_flush(chfsi_ctx* c) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, sp.a, sp.b) == cudaSuccess) c->acc_ms[sp.kind] += ms;
     if (sp.kind == 0) c->acc_flop += sp.flop;
+    if (sp.kind == 2) c->acc_chol_flop += sp.flop;
     c->ev_pool.push_back(sp.a);
     c->ev_pool.push_back(sp.b);
   }
@@ -256,6 +282,8 @@ double gemm_flop(const GemmArgs& g) {
 
 // FP64-accurate product: in mixed-precision mode the large ones run as the error-free digit
 // expansion on the tensor cores (ozaki.cu); otherwise, and for small shapes, on the DFMA pipe.
+__global__ void set_word_kernel(int* w, int v) { *w = v; }
+
 chfsi_status gemm64(chfsi_ctx* c, const GemmArgs& g) {
   if (c->prm.precision == CHFSI_PREC_MIXED && g.epi == EPI_GEMM && g.N > 1 && g.M > 1 &&
       (double)g.M * g.N * g.K >= 4.0e6) {
@@ -263,15 +291,23 @@ chfsi_status gemm64(chfsi_ctx* c, const GemmArgs& g) {
     span_begin(c, 0, gemm_flop(g));
     CU(ozaki_gemm(c->oz, g, c->stream, c->d_err));
     span_end(c);
-    return CHFSI_OK;
+  } else {
+    TRY(gemm(c, g));
   }
-  return gemm(c, g);
+  if (c->fault_gemm > 0 && ++c->gemm_calls == c->fault_gemm) {
+    set_word_kernel<<<1, 1, 0, c->stream>>>(c->d_err, DEV_ERR_TIMEOUT);
+    count_launch();
+    CU(cudaGetLastError());
+  }
+  return CHFSI_OK;
 }
 
 // a1 + inverse: L and Linv from S --------------------------------------------------------
+// The error word is not reset here: inside a solve a GEMM before it (the carry-over of the
+// block when S changes) may have recorded a bounded-wait failure; the entry points reset it.
 chfsi_status factor_S(chfsi_ctx* c, int n, const cplx* S, cplx* L, cplx* Linv) {
-  CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   CU(cudaMemcpyAsync(L, S, sizeof(cplx) * (size_t)n * n, cudaMemcpyDeviceToDevice, c->stream));
+  span_begin(c, 2, (8.0 / 3.0) * (double)n * n * n);
   if (n <= CHOL_INV_KMAX) {
     // one cooperative launch for L and L^{-1} over all SMs
     cplx* X = Linv;
@@ -283,6 +319,7 @@ chfsi_status factor_S(chfsi_ctx* c, int n, const cplx* S, cplx* L, cplx* Linv) {
     CU(chol_lower(c->stream, n, L, n, c->d_err));
     if (Linv) CU(trtri_lower(c->stream, n, L, n, Linv, n, c->d_err));
   }
+  span_end(c);
   int e = 0;
   TRY(read_err(c, &e));
   return map_dev_err(e);
@@ -419,9 +456,6 @@ chfsi_status run_filter(chfsi_ctx* c, int n, int k, const cplx* Hs, cplx* Y, con
   long long steps = 0;
   for (int j = 1; j <= mmax; ++j) steps += cnt[j];
   if (col_steps) *col_steps += steps;
-  cplx* Y2;
-  TRY(buf(c, "filter_y2", (size_t)n * k, &Y2));
-  cplx* bufs[2] = {Y, Y2};
   if (precision == CHFSI_PREC_MIXED) {
     if (!c->tc) c->tc = tc_filter_new();
     if (ritz) {
@@ -439,11 +473,17 @@ chfsi_status run_filter(chfsi_ctx* c, int n, int k, const cplx* Hs, cplx* Y, con
         }
       }
       TcRefine ref{ritz->Z, ritz->lam_dev, ptab.data(), deg};
-      TRY(tc_filter_run(c->tc, c->stream, n, Hs, bufs, cnt.data(), mmax, fa.data(), fb.data(), fg.data(), &ref));
-      return CHFSI_OK;   // result already in Y for every column
+      TRY(tc_filter_run(c->tc, c->stream, n, Hs, Y, cnt.data(), mmax, fa.data(), fb.data(), fg.data(), &ref));
+      return CHFSI_OK;
     }
-    TRY(tc_filter_run(c->tc, c->stream, n, Hs, bufs, cnt.data(), mmax, fa.data(), fb.data(), fg.data()));
-  } else {
+    // every column's result lands in Y at its last step
+    TRY(tc_filter_run(c->tc, c->stream, n, Hs, Y, cnt.data(), mmax, fa.data(), fb.data(), fg.data()));
+    return CHFSI_OK;
+  }
+  cplx* Y2;
+  TRY(buf(c, "filter_y2", (size_t)n * k, &Y2));
+  cplx* bufs[2] = {Y, Y2};
+  {
     for (int j = 1; j <= mmax; ++j) {
       GemmArgs g = gemm_args(n, cnt[j], n, OP_N, Hs, n, OP_N, bufs[(j - 1) & 1], n, bufs[j & 1], n, ONE, ZERO);
       g.epi = EPI_FILTER;
@@ -493,22 +533,23 @@ chfsi_status cholqr_pass(chfsi_ctx* c, int n, int k, cplx* Y, bool shifted, bool
     add_shift_kernel<<<1, 256, 0, c->stream>>>(k, n, G); count_launch();
     CU(cudaGetLastError());
   }
-  CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  CU(cudaMemsetAsync(c->d_err_qr, 0, sizeof(int), c->stream));
   const bool small = k <= CHOL_INV_KMAX;
   if (small) {
     char* w;
     TRY(buf(c, "qr_cholinv", chol_inv_work_bytes(k), &w));
-    CU(chol_inv_small(c->stream, k, G, Ri, w, c->d_err));
+    CU(chol_inv_small(c->stream, k, G, Ri, w, c->d_err_qr));
   } else {
-    CU(chol_lower(c->stream, k, G, k, c->d_err));
+    CU(chol_lower(c->stream, k, G, k, c->d_err_qr));
   }
   int e = 0;
-  TRY(read_err(c, &e));
+  TRY(read_word(c, c->d_err_qr, &e));
+  if (e == DEV_ERR_TIMEOUT) return CHFSI_ERR_TIMEOUT;
   if (e != DEV_OK) {
     *ok = false;
     return CHFSI_OK;
   }
-  if (!small) CU(trtri_lower(c->stream, k, G, k, Ri, k, c->d_err));
+  if (!small) CU(trtri_lower(c->stream, k, G, k, Ri, k, c->d_err_qr));
   // Y <- Y R^{-1}, R = Lg^H  =>  R^{-1} = (Lg^{-1})^H (upper triangular)
   TRY(gemm64(c, gemm_args(n, k, k, OP_N, Y, n, OP_C, Ri, k, T, n, ONE, ZERO, TRI_B_UPPER)));
   CU(copy_block(c->stream, n, k, T, n, Y, n));
@@ -564,12 +605,12 @@ chfsi_status cholqr32_pass(chfsi_ctx* c, int n, int k, cplx* Y, bool* ok) {
   scaled_gram_f32_kernel<<<gb, 256, 0, c->stream>>>(k, G, Gs);
   count_launch();
   CU(cudaGetLastError());
-  CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
-  CU(chol_inv_small_f32(c->stream, k, Gs, X32, w, c->d_err));
+  CU(cudaMemsetAsync(c->d_err_qr, 0, sizeof(int), c->stream));
+  CU(chol_inv_small_f32(c->stream, k, Gs, X32, w, c->d_err_qr));
   int e = 0;
-  TRY(read_err(c, &e));
+  TRY(read_word(c, c->d_err_qr, &e));
+  if (e == DEV_ERR_TIMEOUT) return CHFSI_ERR_TIMEOUT;
   if (e != DEV_OK) {   // not positive definite in FP32: the caller falls back to FP64
-    CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     *ok = false;
     return CHFSI_OK;
   }
@@ -697,11 +738,14 @@ chfsi_status reduced_eig(chfsi_ctx* c, int k, cplx* G, double* lam, cplx* W) {
   char* work;
   TRY(buf(c, "jac_work", jacobi_work_bytes(k), &work));
   span_begin(c, 1, 0.0);
-  CU(jacobi_eig(c->stream, k, G, lam, W, work, c->d_err, c->d_sweeps));
+  CU(jacobi_eig(c->stream, k, G, lam, W, work, c->d_err, c->d_sweeps, c->d_rounds));
   span_end(c);
-  if (c->n_sweeps_pending < 64)
-    CU(cudaMemcpyAsync(&c->sweeps_host[c->n_sweeps_pending++], c->d_sweeps, sizeof(int), cudaMemcpyDeviceToHost,
-                       c->stream));
+  if (c->n_sweeps_pending < 64) {
+    const int q = c->n_sweeps_pending++;
+    c->pending_k[q] = k;
+    // d_sweeps and d_rounds are adjacent
+    CU(cudaMemcpyAsync(&c->sweeps_host[2 * q], c->d_sweeps, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  }
   return CHFSI_OK;
 }
 
@@ -719,6 +763,55 @@ chfsi_status rayleigh_ritz(chfsi_ctx* c, int n, int k, const cplx* Hs, cplx* Y, 
   CU(copy_block(c->stream, n, k, T, n, Y, n));
   TRY(gemm64(c, gemm_args(n, k, k, OP_N, Z, n, OP_N, W, k, T, n, ONE, ZERO)));
   CU(copy_block(c->stream, n, k, T, n, Z, n));
+  return CHFSI_OK;
+}
+
+// Completeness of the returned set (Algorithm 1 returns the LOWEST nev pairs): Sylvester's
+// law of inertia on M = H' - sigma I + tau Yl Yl^H, sigma in the gap between the largest
+// returned eigenvalue lmax and the smallest other Ritz value lnext, Yl the nl returned
+// (orthonormal, converged) vectors and tau = sigma - lmin + gap / 2.  The returned eigenpairs
+// move to lam - sigma + tau >= gap / 2 and every other eigenvalue of H' stays at lam - sigma,
+// so M is positive definite exactly when H' has no eigenvalue below sigma besides the
+// returned ones.  Positive definiteness is decided by an FP32 Cholesky, whose backward error
+// (about n u ||M||, u = 2^-24) must stay below gap / 2: smaller gaps are reported as
+// inconclusive rather than decided.
+__global__ void shift_to_f32_kernel(int n, const cplx* T, double sigma, float2* M) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)n * n; e += (long)gridDim.x * blockDim.x) {
+    const cplx t = T[e];
+    const double re = (e % n == e / n) ? t.x - sigma : t.x;
+    M[e] = make_float2(to_f32(re), to_f32(t.y));
+  }
+}
+
+chfsi_status inertia_check(chfsi_ctx* c, int n, const cplx* Hs, const cplx* Yl, int nl, double lmin, double lmax,
+                           double lnext, double hnorm, int* completeness, chfsi_status* status) {
+  const double gap = lnext - lmax;
+  const double sigma = 0.5 * (lmax + lnext);
+  const double tau = (sigma - lmin) + 0.5 * gap;
+  const double mnorm = hnorm + fabs(sigma) + tau;
+  if (!(0.5 * gap > 4.0 * n * 5.9604644775390625e-8 * mnorm) || n > CHOL_INV_KMAX) {
+    *completeness = -1;
+    return CHFSI_OK;
+  }
+  cplx* T;
+  float2* M;
+  char* w;
+  TRY(buf(c, "tmp_nn", (size_t)n * n, &T));
+  TRY(buf(c, "inertia_M32", (size_t)n * n, &M));
+  TRY(buf(c, "inertia_work", chol_inv_work_bytes(n), &w));
+  CU(cudaMemcpyAsync(T, Hs, sizeof(cplx) * (size_t)n * n, cudaMemcpyDeviceToDevice, c->stream));
+  TRY(gemm64(c, gemm_args(n, n, nl, OP_N, Yl, n, OP_C, Yl, n, T, n, cmk(tau, 0.0), ONE)));
+  const unsigned gb = (unsigned)std::min<long>(((long)n * n + 255) / 256, 152L * 16);
+  shift_to_f32_kernel<<<gb, 256, 0, c->stream>>>(n, T, sigma, M);
+  count_launch();
+  CU(cudaGetLastError());
+  CU(cudaMemsetAsync(c->d_err_qr, 0, sizeof(int), c->stream));
+  CU(chol_inv_small_f32(c->stream, n, M, nullptr, w, c->d_err_qr));   // factor only
+  int e = 0;
+  TRY(read_word(c, c->d_err_qr, &e));
+  if (e == DEV_ERR_TIMEOUT) return CHFSI_ERR_TIMEOUT;
+  if (e == DEV_OK) *completeness = 2;
+  else *status = CHFSI_ERR_INCOMPLETE;
   return CHFSI_OK;
 }
 
@@ -843,8 +936,7 @@ chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, 
     CU(cudaStreamSynchronize(c->stream));
     tm.flush();
     spans_flush(c);
-    for (int q = 0; q < c->n_sweeps_pending && q < 64; ++q) c->acc_sweeps += c->sweeps_host[q];
-    c->n_sweeps_pending = 0;
+    sweeps_flush(c);
     if (h_err != DEV_OK) return map_dev_err(h_err);
     for (int i = 0; i < ka; ++i)
       if (!isfinite(h_res[i]) || !isfinite(h_lam[i])) return CHFSI_ERR_NUMERIC;
@@ -901,6 +993,26 @@ chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, 
     if (nl >= nev || it >= c->prm.max_iter || ka == 0) break;
   }
   if (nl < nev) status = CHFSI_ERR_NO_CONV;
+  // pairs whose lock test was absolute (|lam| below the residual floor)
+  int n_floor = 0;
+  for (double l : lam_locked)
+    if (fabs(l) < 1e-4 * hnorm) ++n_floor;
+  // completeness: no Ritz value of the block outside the returned set may lie below the
+  // largest returned eigenvalue (a lower unreturned one means a wanted eigenvalue was passed
+  // over); optionally the exact count below the gap (inertia)
+  int completeness = 0;
+  if (status == CHFSI_OK && nl > 0) {
+    const double lmax = *std::max_element(lam_locked.begin(), lam_locked.end());
+    const double lmin = *std::min_element(lam_locked.begin(), lam_locked.end());
+    double lnext = a;   // largest Ritz value of the last block (the filter's lower end)
+    for (double l : lam_active) lnext = std::min(lnext, l);
+    if (lmax > lnext + 1e-8 * hnorm) {
+      status = CHFSI_ERR_INCOMPLETE;
+    } else {
+      completeness = 1;
+      if (c->prm.check_inertia) TRY(inertia_check(c, n, Hs, Y, nl, lmin, lmax, lnext, hnorm, &completeness, &status));
+    }
+  }
   tm.start();
   tm.mark(0);
   // outputs: locked pairs by ascending eigenvalue (then the lowest active ones on NO_CONV)
@@ -933,8 +1045,10 @@ chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, 
   CU(cudaMemcpyAsync(perm, h_perm, sizeof(int) * k, cudaMemcpyHostToDevice, c->stream));
   CU(gather_columns(c->stream, n, k, perm, Y, n, Y2, n));
   CU(copy_block(c->stream, n, k, Y2, n, Y, n));
-  CU(cudaStreamSynchronize(c->stream));
+  int e_end = 0;
+  TRY(read_err(c, &e_end));   // failures of the products after the last iteration's check
   tm.flush();
+  if (e_end != DEV_OK) status = map_dev_err(e_end);
   if (info) {
     info->iterations = it;
     info->locked = nl;
@@ -948,6 +1062,8 @@ chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, 
     for (int s = 0; s < 7; ++s) info->ms_stage[s] += ms[s];
     info->ms_stage[2] += ms[8];
     info->ms_filter_lowp += ms[8];
+    info->n_floor = n_floor;
+    info->completeness = completeness;
   }
   return status;
 }
@@ -981,9 +1097,16 @@ chfsi_status solve_common(chfsi_ctx* c, const cplx* H, const cplx* S, const cplx
   TRY(buf(c, "lz_beta", 256, &be));
   TRY(buf(c, "lz_bounds", 16, &bd));
   if (info) memset(info, 0, sizeof(*info));
-  c->acc_ms[0] = c->acc_ms[1] = 0.0;
+  c->acc_ms[0] = c->acc_ms[1] = c->acc_ms[2] = 0.0;
   c->acc_flop = 0.0;
+  c->acc_chol_flop = 0.0;
+  if (c->tc) tc_filter_take_ms(c->tc);
   c->acc_sweeps = 0;
+  c->acc_rounds = 0;
+  c->acc_eig_flop = 0.0;
+  c->gemm_calls = 0;
+  const char* inject = getenv("CHFSI_INJECT_GEMM_TIMEOUT");
+  c->fault_gemm = inject ? atoi(inject) : 0;
   cudaEvent_t r0 = c->ev[12], r1 = c->ev[13];
   CU(cudaEventRecord(r0, c->stream));
   if (S) {
@@ -1035,8 +1158,7 @@ chfsi_status solve_common(chfsi_ctx* c, const cplx* H, const cplx* S, const cplx
   CU(cudaEventRecord(t1, c->stream));
   CU(cudaEventSynchronize(t1));
   spans_flush(c);
-  for (int q = 0; q < c->n_sweeps_pending && q < 64; ++q) c->acc_sweeps += c->sweeps_host[q];
-  c->n_sweeps_pending = 0;
+  sweeps_flush(c);
   if (info) {
     float tot = 0.f;
     cudaEventElapsedTime(&tot, t0, t1);
@@ -1047,8 +1169,15 @@ chfsi_status solve_common(chfsi_ctx* c, const cplx* H, const cplx* S, const cplx
     info->gemm_tc_flop = c->acc_flop;
     info->ms_eig = c->acc_ms[1];
     info->eig_sweeps = c->acc_sweeps;
+    info->eig_rounds = c->acc_rounds;
+    info->eig_flop = c->acc_eig_flop;
+    info->ms_chol = c->acc_ms[2];
+    info->chol_flop = c->acc_chol_flop;
+    long long cols = 0;
+    info->ms_filter_steps = c->tc ? tc_filter_take_ms(c->tc, &cols) : 0.0;
+    info->filter_step_cols = cols;
   }
-  if (st == CHFSI_OK || st == CHFSI_ERR_NO_CONV) c->have_seq = true;
+  if (st == CHFSI_OK || st == CHFSI_ERR_NO_CONV || st == CHFSI_ERR_INCOMPLETE) c->have_seq = true;
   return st;
 }
 
@@ -1062,7 +1191,8 @@ size_t chfsi_workspace_bytes(int n, int nev, int nex, int precision) {
   const double N = n, K = nev + nex, c16 = 16.0;
   // FP64 matrices: L, L^{-1}, H', transform temporary; blocks Y, Z and five n x k temporaries;
   // k x k Gram/Ritz/eigensolver matrices; split-K partial sums (at most 16 k^2)
-  double b = c16 * (4 * N * N + 8 * N * K + 24 * K * K) + 2 * N * c16 * 8 + (1 << 20);
+  // plus the FP32 n x n matrix of the optional inertia count
+  double b = c16 * (4 * N * N + 8 * N * K + 24 * K * K) + 8.0 * N * N + 2 * N * c16 * 8 + (1 << 20);
   if (precision == CHFSI_PREC_MIXED) {
     const double np = std::ceil(N / 128) * 128, kp = std::ceil(2 * N / 64) * 64, kk = 2 * K + 64;
     b += 2.0 * 3 * np * kp + 2.0 * 2 * 3 * kk * kp + c16 * 3 * N * K;      // filter slices and state
@@ -1073,6 +1203,57 @@ size_t chfsi_workspace_bytes(int n, int nev, int nex, int precision) {
     b += 2.0 * 12 * (np * kp + 2 * N * kp) + c16 * 4 * N * K + c16 * passes * std::max(N * N, 16 * N * K);
   }
   return (size_t)b;
+}
+
+// FP64 pipe probe: every thread runs eight independent FMA chains (x <- x * b + c), so the
+// FP64 unit, not the dependency latency, limits the rate; flops = 2 per FMA.
+__global__ void dfma_probe_kernel(int iters, double b, double c, double* out) {
+  double x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = threadIdx.x * 1e-3 + i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = fma(x[i], b, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += x[i];
+  if (s == 12345.678) out[0] = s;   // keeps the chains live; practically never stores
+}
+
+chfsi_status chfsi_fp64_peak(int device, double* tflops) {
+  if (!tflops) return CHFSI_ERR_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return CHFSI_ERR_ARG;
+  CU(cudaSetDevice(device));
+  int sms = 0;
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  double* sink = nullptr;
+  CU(cudaMalloc(&sink, sizeof(double)));
+  cudaStream_t st;
+  CU(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  const int blocks = sms * 4, threads = 256, iters = 2048;
+  double best = 0.0;
+  for (int rep = 0; rep < 4; ++rep) {   // the first launch warms up
+    CU(cudaEventRecord(e0, st));
+    dfma_probe_kernel<<<blocks, threads, 0, st>>>(iters, 0.999999, 1e-6, sink);
+    count_launch();
+    CU(cudaEventRecord(e1, st));
+    CU(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, e0, e1));
+    const double flop = 2.0 * 8.0 * iters * (double)blocks * threads;
+    if (rep > 0 && ms > 0.f) best = std::max(best, flop / (ms * 1e-3) / 1e12);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  cudaFree(sink);
+  *tflops = best;
+  return CHFSI_OK;
 }
 
 unsigned long long chfsi_kernel_launches(void) {
@@ -1091,6 +1272,7 @@ const char* chfsi_status_string(chfsi_status s) {
     case CHFSI_ERR_TIMEOUT: return "device wait timed out";
     case CHFSI_ERR_STATE: return "call out of order";
     case CHFSI_ERR_NUMERIC: return "non-finite value or breakdown";
+    case CHFSI_ERR_INCOMPLETE: return "completeness check failed (a lower eigenvalue was missed)";
   }
   return "unknown status";
 }
@@ -1107,6 +1289,7 @@ chfsi_status chfsi_default_params(chfsi_params* p) {
   p->precision = CHFSI_PREC_FP64;
   p->mixed_switch = 1e-6;
   p->seed = 0;
+  p->check_inertia = 0;
   return CHFSI_OK;
 }
 
@@ -1118,7 +1301,8 @@ chfsi_status chfsi_create(chfsi_ctx** out, int device, void* cuda_stream, const 
   else chfsi_default_params(&prm);
   if (prm.degree < 1 || prm.max_iter < 1 || prm.lanczos_steps < 2 || prm.lanczos_steps > 256 ||
       prm.degree_min < 1 || prm.degree_max < prm.degree_min ||
-      (prm.precision != CHFSI_PREC_FP64 && prm.precision != CHFSI_PREC_MIXED))
+      (prm.precision != CHFSI_PREC_FP64 && prm.precision != CHFSI_PREC_MIXED) ||
+      (prm.check_inertia != 0 && prm.check_inertia != 1))
     return CHFSI_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return CHFSI_ERR_ARG;
@@ -1128,15 +1312,17 @@ chfsi_status chfsi_create(chfsi_ctx** out, int device, void* cuda_stream, const 
   c->prm = prm;
   c->degree = prm.degree;
   chfsi_status s = setup_device(c);
-  if (s == CHFSI_OK) s = cu(cudaMalloc(&c->d_err, 2 * sizeof(int)), "err");
+  if (s == CHFSI_OK) s = cu(cudaMalloc(&c->d_err, 4 * sizeof(int)), "err");
   if (s == CHFSI_OK) {
     c->d_sweeps = c->d_err + 1;
+    c->d_rounds = c->d_err + 2;
+    c->d_err_qr = c->d_err + 3;
     // on the context's stream (which may be non-blocking), then waited for
-    s = cu(cudaMemsetAsync(c->d_err, 0, 2 * sizeof(int), c->stream), "err");
+    s = cu(cudaMemsetAsync(c->d_err, 0, 4 * sizeof(int), c->stream), "err");
     if (s == CHFSI_OK) s = cu(cudaStreamSynchronize(c->stream), "err");
   }
   for (int i = 0; i < 16 && s == CHFSI_OK; ++i) s = cu(cudaEventCreate(&c->ev[i]), "event");
-  if (s == CHFSI_OK) s = cu(cudaMallocHost((void**)&c->sweeps_host, 64 * sizeof(int)), "pinned");
+  if (s == CHFSI_OK) s = cu(cudaMallocHost((void**)&c->sweeps_host, 128 * sizeof(int)), "pinned");
   if (s != CHFSI_OK) {
     chfsi_destroy(c);
     return s;
@@ -1217,6 +1403,7 @@ chfsi_status chfsi_gemm(chfsi_ctx* c, char opA, char opB, int M, int N, int K, c
 chfsi_status chfsi_cholesky(chfsi_ctx* c, int n, const void* S, void* L) {
   if (!c || !valid_ptrs({S, L}) || n < 1) return CHFSI_ERR_ARG;
   TRY(setup_device(c));
+  CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   return factor_S(c, n, (const cplx*)S, (cplx*)L, nullptr);
 }
 

@@ -439,7 +439,7 @@ __device__ void diag_factor_cta(typename Cx<T>::C* A, typename Cx<T>::C* X, type
   for (int e = tid; e < w * w; e += blockDim.x) {
     const int r = e % w, cc = e / w;
     A[(j0 + r) + (long)(j0 + cc) * k] = (r >= cc) ? Tm[r][cc] : xzero<C>();
-    X[(j0 + r) + (long)(j0 + cc) * k] = Ti[r][cc];
+    if (X) X[(j0 + r) + (long)(j0 + cc) * k] = Ti[r][cc];
     Dinv[r + cc * NB] = Ti[r][cc];
   }
 }
@@ -509,6 +509,7 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(CholInvArgs<T> g) {
     const long r = e % k, c = e / k;
     if (r < c) g.A[e] = xzero<C>();
   }
+  if (!g.X) return;   // factor only
   // block rows of X = L^{-1}: X(i,0:i0) = -Ti (L(i,0:i0) X(0:i0,0:i0))
   for (int ib = 1; ib < nb; ++ib) {
     const int i0 = ib * NB, w = min(NB, k - i0);
@@ -587,7 +588,7 @@ cudaError_t chol_inv_launch(cudaStream_t s, int k, typename Cx<T>::C* A, typenam
   g.fail = (int*)(tail + 2);
   g.err = err;
   cudaError_t e = cudaMemsetAsync(tail, 0, 16, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(X, 0, sizeof(C) * (size_t)k * k, s);
+  if (e == cudaSuccess && X) e = cudaMemsetAsync(X, 0, sizeof(C) * (size_t)k * k, s);
   if (e != cudaSuccess) return e;
   void* args[] = {&g};
   e = coop_launch((const void*)chol_inv_kernel<T>, dim3(chol_inv_blocks()), dim3(256), args, s);

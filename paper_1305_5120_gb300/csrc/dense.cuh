@@ -32,6 +32,7 @@ cudaError_t copy_block(cudaStream_t s, int n, int k, const cplx* src, long lds, 
 // Hermitian positive definite A (k x k, k <= CHOL_INV_KMAX): lower L (in place, upper zeroed) with
 // A = L L^H and X = L^{-1}, in one cooperative launch over all SMs (blocked right-looking,
 // 32-wide blocks).  A non-positive pivot sets *err = DEV_ERR_NOT_HPD.  work: chol_inv_work_bytes(k).
+// X == NULL factors only (A is still overwritten by L).
 constexpr int CHOL_INV_KMAX = 8192;
 size_t chol_inv_work_bytes(int k);
 cudaError_t chol_inv_small(cudaStream_t s, int k, cplx* A, cplx* X, void* work, int* err);

@@ -1,18 +1,25 @@
 // Chebyshev filter step on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
 // One step of the scaled three-term recurrence (Eq. (3term) with shift and scale, Section 3)
-//     Y_{j+1} = fa * H' Y_j + fb * Y_j + fg * Y_{j-1}
-// is one launch.  The complex product H' Y_j runs as a real GEMM through the embedding
+//     Y_j = fa_j H' Y_{j-1} + fb_j Y_{j-1} + fg_j Y_{j-2}
+// is one launch.  The complex product H' Y_{j-1} runs as a real GEMM through the embedding
 //     [Re H' | Im H'] (K interleaved)  x  [[Re Y, Im Y], [-Im Y, Re Y]] (columns interleaved),
-// so M = n, N = 2k, K = 2n.  Each FP64 operand is split into three BF16 slices
-// (x = s0 + s1 + s2 + O(2^-24 |x|)) and the six slice products with s + t <= 2 accumulate in
-// FP32 TMEM accumulators, one per level s + t: an FP32-equivalent product on the BF16 pipe.
+// so M = n, N = 2k, K = 2n.  Each operand is held as three BF16 slices (x = s0 + s1 + s2 to
+// about 2^-24 |x|) and the six slice products with s + t <= 2 accumulate in FP32 TMEM
+// accumulators, one per level s + t: an FP32-equivalent product on the BF16 pipe.
+//
+// The recurrence state lives only in the slices.  The B operand of step j holds the slices of
+// Y_{j-1}; the epilogue rebuilds Y_{j-1} and Y_{j-2} from them in FP32, forms Y_j in FP32 and
+// writes its slices over those of Y_{j-2} -- the next step's operand.  A column whose last step
+// this is writes its FP64 result instead.  So a step executes no FP64 instruction: this GPU's
+// FP64 pipe issues a warp instruction per 64 cycles per sub-partition, the FP32 pipe one per
+// cycle, and an FP64 epilogue had cost more than the tensor-core main loop.
 //
 // Per CTA (one 128 x BN output tile): warp 0 issues TMA loads of the A and B slice tiles
 // (128-byte swizzle) into a 3-stage shared-memory ring; warp 1 owns the TMEM accumulators and
-// issues tcgen05.mma (three per K step); warps 2-5 drain TMEM, apply the recurrence in FP64 against Y_j and
-// Y_{j-1}, store Y_{j+1} (FP64) and write its BF16 slices in the B layout of the next step.
-// Every mbarrier wait is bounded: on timeout the kernel records DEV_ERR_TIMEOUT and leaves.
+// issues tcgen05.mma (three per K step); warps 2-5 drain TMEM and run the recurrence.  Every
+// mbarrier wait is bounded: on timeout the kernel records DEV_ERR_TIMEOUT, waits (bounded) for
+// the copies and products it has issued, frees its TMEM and leaves.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -44,15 +51,16 @@ static_assert(STAGE_BYTES % 1024 == 0, "stage alignment");
 struct StepArgs {
   int n, mtiles;                 // rows, row tiles
   int ncols;                     // complex columns this step (cnt[j])
+  int ncols_next;                // of which continue to step j + 1 (cnt[j + 1]; 0 on the last step)
   int kblocks;                   // K_pad / BK
-  long ldb_next;                 // K_pad (elements per B row)
-  long nslice_rows_b;            // N_pad (rows per B slice)
-  const cplx* Ycur;              // n x ncols, ld n
-  cplx* Yout;                    // in: Y_{j-1} (if fg != 0), out: Y_{j+1}
-  __nv_bfloat16* Bnext;          // next step's B slices (NULL on the last step)
-  double fa, fb, fg;
-  const cplx* R;                 // corrected recurrence: R = H Yhat - Yhat diag(lam) (n x ncols)
-  const double* fcol;            // per column fa * p_{j-1}(lam_col); NULL for the plain recurrence
+  long kpad;                     // bf16 elements per B row
+  long npad;                     // rows per B slice
+  const __nv_bfloat16* Bcur;     // slices of Y_{j-1}: this step's B operand
+  __nv_bfloat16* Bnext;          // in: slices of Y_{j-2} (read when fg != 0); out: slices of Y_j
+  cplx* Yfinal;                  // FP64 result of the columns whose last step this is (ld n)
+  float fa, fb, fg;
+  const float2* R;               // corrected recurrence: R = H Yhat - Yhat diag(lam) (n x ncols), else NULL
+  const float* fcol;             // per column fa_j p_{j-1}(lam_col); NULL for the plain recurrence
   int* err;
 };
 
@@ -82,6 +90,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* er
     if ((i & 255) == 255 && *(volatile int*)err != DEV_OK) return false;
   }
   atomicExch(err, DEV_ERR_TIMEOUT);
+  return false;
+}
+// bounded wait for work already issued (used on the way out after a failure): does not give
+// up early when the error word is set, only after the limit
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity) {
+  for (long i = 0; i < WAIT_LIMIT; ++i)
+    if (mbar_try(bar, parity)) return true;
   return false;
 }
 
@@ -132,13 +147,55 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// three-way BF16 split: x ~= s0 + s1 + s2 (each rounded to nearest)
-__device__ __forceinline__ void split3(double x, __nv_bfloat16& s0, __nv_bfloat16& s1, __nv_bfloat16& s2) {
-  s0 = __double2bfloat16(x);
-  double r = x - (double)__bfloat162float(s0);
-  s1 = __double2bfloat16(r);
-  r -= (double)__bfloat162float(s1);
-  s2 = __double2bfloat16(r);
+// FP64 -> FP32 rounded to nearest (half an FP32 unit added before truncation; a carry into
+// the exponent field is the correct rounding), by integer operations on the bit pattern.
+// Values below FP32's normal range become zero; infinities and NaNs keep their class.
+__device__ __forceinline__ float f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const unsigned long long m = b & 0x7FFFFFFFFFFFFFFFull;
+  if ((m >> 52) == 0x7FF) return __uint_as_float(sign | 0x7F800000u | ((m << 12) ? 0x400000u : 0u));
+  const unsigned long long r = m + (1ull << 28);
+  const int e = (int)(r >> 52) - 1023 + 127;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | ((unsigned)e << 23) | (unsigned)((r >> 29) & 0x7FFFFF));
+}
+
+// three-way BF16 split of an FP32 value: x = s0 + s1 + s2 + O(2^-27 |x|); both subtractions
+// are exact
+__device__ __forceinline__ void split3f(float x, uint32_t& s0, uint32_t& s1, uint32_t& s2) {
+  const __nv_bfloat16 b0 = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(b0);
+  const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(b1);
+  const __nv_bfloat16 b2 = __float2bfloat16_rn(r2);
+  s0 = __bfloat16_as_ushort(b0);
+  s1 = __bfloat16_as_ushort(b1);
+  s2 = __bfloat16_as_ushort(b2);
+}
+
+// The B operand layout of one complex entry y in slice t: row 2j holds the pair (Re y, -Im y)
+// and row 2j + 1 the pair (Im y, Re y), each pair one 32-bit word (first element low).
+__device__ __forceinline__ uint32_t pack_lo_hi(uint32_t lo, uint32_t hi) { return lo | (hi << 16); }
+__device__ __forceinline__ void store_slices(uint32_t* B32, long slice_words, long w2j, long w2j1, float re,
+                                             float im) {
+  uint32_t r0, r1, r2, i0, i1, i2;
+  split3f(re, r0, r1, r2);
+  split3f(im, i0, i1, i2);
+  const uint32_t rs[3] = {r0, r1, r2}, is[3] = {i0, i1, i2};
+#pragma unroll
+  for (int t = 0; t < NSLICE; ++t) {
+    B32[t * slice_words + w2j] = pack_lo_hi(rs[t], is[t] ^ 0x8000u);   // (Re, -Im)
+    B32[t * slice_words + w2j1] = pack_lo_hi(is[t], rs[t]);            // (Im,  Re)
+  }
+}
+// Y from the three words of row 2j: Re = s0 + (s1 + s2) (the inner sum is exact), Im likewise
+__device__ __forceinline__ float2 join_slices(const uint32_t w[3]) {
+  const float re = __uint_as_float(w[0] << 16) + (__uint_as_float(w[1] << 16) + __uint_as_float(w[2] << 16));
+  const float nim = __uint_as_float(w[0] & 0xFFFF0000u) +
+                    (__uint_as_float(w[1] & 0xFFFF0000u) + __uint_as_float(w[2] & 0xFFFF0000u));
+  return make_float2(re, -nim);
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -179,7 +236,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      // producer: A slice s at rows s*mtiles*BM + m0, B slice t at rows t*N_pad + n0
+      // producer: A slice s at rows s*mtiles*BM + m0, B slice t at rows t*npad + n0
+      int issued = 0;
       for (int kb = 0; kb < g.kblocks; ++kb) {
         const int s = kb % STAGES;
         const uint32_t ph = (kb / STAGES) & 1;
@@ -189,8 +247,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int q = 0; q < NSLICE; ++q)
           tma_load_2d(st + q * A_TILE, &tmA, full(s), kb * BK, q * g.mtiles * BM + m0);
         for (int q = 0; q < NSLICE; ++q)
-          tma_load_2d(st + NSLICE * A_TILE + q * B_TILE, &tmB, full(s), kb * BK, (int)(q * g.nslice_rows_b) + n0);
+          tma_load_2d(st + NSLICE * A_TILE + q * B_TILE, &tmB, full(s), kb * BK, (int)(q * g.npad) + n0);
+        issued = kb + 1;
       }
+      // After a failure the consumer may have abandoned stages whose copies are still in
+      // flight into this CTA's shared memory: wait until each issued stage has landed (each
+      // stage's latest phase is the one checked) before the CTA may exit.
+      if (*(volatile int*)g.err != DEV_OK)
+        for (int kb = std::max(0, issued - STAGES); kb < issued; ++kb)
+          mbar_drain(full(kb % STAGES), (kb / STAGES) & 1);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -200,14 +265,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // N = 64 (3 - s) into columns [64 s, 192): three instructions per 16-wide K step for
       // the six slice products.  Each level has its own accumulator, so the per-instruction
       // truncation of the FP32 accumulation acts on every level at that level's scale.
-      bool ok = true;
-      for (int kb = 0; kb < g.kblocks && ok; ++kb) {
+      for (int kb = 0; kb < g.kblocks; ++kb) {
         const int s = kb % STAGES;
         const uint32_t ph = (kb / STAGES) & 1;
-        if (!mbar_wait(full(s), ph, g.err)) {
-          ok = false;
-          break;
-        }
+        if (!mbar_wait(full(s), ph, g.err)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t st = base + s * STAGE_BYTES;
         // base descriptors once per stage; slices and K steps are start-address offsets
@@ -225,7 +286,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         umma_commit(empty(s));   // frees the stage once these MMAs have read it
       }
-      umma_commit(accum);        // accumulator complete (or abandoned on error)
+      umma_commit(accum);        // arrives when every product issued above has completed
     }
   } else {
     // epilogue: warps 2..5 -> TMEM lane quarter (warp % 4)
@@ -237,48 +298,57 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16);
+      const uint32_t* Bc32 = (const uint32_t*)g.Bcur;
+      uint32_t* Bn32 = (uint32_t*)g.Bnext;
+      const long kw = g.kpad / 2;                 // 32-bit words per B row
+      const long slice_words = g.npad * kw;
+      const bool use_prev = g.fg != 0.0f;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 16) {   // 16 real columns (8 complex) per pass
         float l0[16], l1[16], l2[16];
         tmem_ld16(taddr + c0, l0);
         tmem_ld16(taddr + BN + c0, l1);
         tmem_ld16(taddr + 2 * BN + c0, l2);
+        const int jb = (n0 + c0) / 2;
         if (row < g.n) {
+          // every load of the 8 columns first, then the arithmetic and the stores
+          uint32_t wc[8][3], wp[8][3];
+          float2 rr[8];
 #pragma unroll
           for (int jj = 0; jj < 8; ++jj) {
-            const int j = (n0 + c0) / 2 + jj;     // complex column
+            const int j = jb + jj;
+            const long w2j = 2L * j * kw + row;
+#pragma unroll
+            for (int t = 0; t < NSLICE; ++t) {
+              wc[jj][t] = j < g.ncols ? Bc32[t * slice_words + w2j] : 0u;
+              wp[jj][t] = (use_prev && j < g.ncols) ? Bn32[t * slice_words + w2j] : 0u;
+            }
+            rr[jj] = (g.R && j < g.ncols) ? g.R[(long)j * g.n + row] : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const int j = jb + jj;
             if (j >= g.ncols) continue;
-            const long e = (long)j * g.n + row;
-            const cplx y = g.Ycur[e];
-            const double hr = (double)l0[2 * jj] + ((double)l1[2 * jj] + (double)l2[2 * jj]);
-            const double hi = (double)l0[2 * jj + 1] + ((double)l1[2 * jj + 1] + (double)l2[2 * jj + 1]);
-            cplx o = cmk(g.fa * hr + g.fb * y.x, g.fa * hi + g.fb * y.y);
-            if (g.fg != 0.0) {
-              const cplx p = g.Yout[e];
-              o.x += g.fg * p.x;
-              o.y += g.fg * p.y;
+            const float hr = l0[2 * jj] + (l1[2 * jj] + l2[2 * jj]);
+            const float hi = l0[2 * jj + 1] + (l1[2 * jj + 1] + l2[2 * jj + 1]);
+            const float2 y = join_slices(wc[jj]);
+            float ore = fmaf(g.fa, hr, g.fb * y.x);
+            float oim = fmaf(g.fa, hi, g.fb * y.y);
+            if (use_prev) {
+              const float2 p = join_slices(wp[jj]);
+              ore = fmaf(g.fg, p.x, ore);
+              oim = fmaf(g.fg, p.y, oim);
             }
             if (g.fcol) {   // residual forcing of the corrected recurrence: + fa p_{j-1}(lam_j) R_j
-              const cplx r = g.R[e];
-              const double f = g.fcol[j];
-              o.x += f * r.x;
-              o.y += f * r.y;
+              const float f = g.fcol[j];
+              ore = fmaf(f, rr[jj].x, ore);
+              oim = fmaf(f, rr[jj].y, oim);
             }
-            g.Yout[e] = o;
-            if (g.Bnext) {
-              __nv_bfloat16 xr[3], xi[3];
-              split3(o.x, xr[0], xr[1], xr[2]);
-              split3(o.y, xi[0], xi[1], xi[2]);
-#pragma unroll
-              for (int t = 0; t < NSLICE; ++t) {
-                __nv_bfloat16* rowRe = g.Bnext + (t * g.nslice_rows_b + 2L * j) * g.ldb_next;
-                __nv_bfloat16* rowIm = rowRe + g.ldb_next;
-                __nv_bfloat162 v0, v1;
-                v0.x = xr[t]; v0.y = __hneg(xi[t]);   // row 2j:   ( Re y, -Im y)
-                v1.x = xi[t]; v1.y = xr[t];           // row 2j+1: ( Im y,  Re y)
-                *(__nv_bfloat162*)(rowRe + 2L * row) = v0;
-                *(__nv_bfloat162*)(rowIm + 2L * row) = v1;
-              }
+            if (j < g.ncols_next) {
+              const long w2j = 2L * j * kw + row;
+              store_slices(Bn32, slice_words, w2j, w2j + kw, ore, oim);
+            } else {
+              g.Yfinal[(long)j * g.n + row] = cmk(to_f64(ore), to_f64(oim));
             }
           }
         }
@@ -287,32 +357,33 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (*(volatile int*)g.err != DEV_OK) __nanosleep(200000);   // let abandoned copies land
   if (warp == 1) {
+    // after a failure the products may still be running: the accumulator barrier arrives when
+    // they have completed (bounded), and only then is the TMEM returned
+    if (*(volatile int*)g.err != DEV_OK && lane == 0) mbar_drain(accum, 0);
+    __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
   }
 }
 
-// H' (column-major, Hermitian) -> A slices: A_s[r][2c] = s_s(Re H'[r,c]), A_s[r][2c+1] = s_s(Im H'[r,c]),
-// read through the Hermitian symmetry (row r of H' = conj of column r, contiguous).  Padding zero.
+// Slices of H' (column-major, Hermitian) as the A operand: A_s[r][2c] = s_s(Re H'[r,c]),
+// A_s[r][2c+1] = s_s(Im H'[r,c]), read through the Hermitian symmetry (row r of H' = conj of
+// column r, contiguous).  Each entry is rounded to FP32 (integer operations) and split there;
+// padding zero.
 __global__ void slice_H_kernel(int n, long kpad, long mpad, const cplx* __restrict__ H, __nv_bfloat16* __restrict__ A) {
   const long r = blockIdx.y;
+  uint32_t* A32 = (uint32_t*)A;
+  const long slice_words = mpad * kpad / 2;
   for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < kpad / 2; c += (long)gridDim.x * blockDim.x) {
-    __nv_bfloat16 re[3], im[3];
+    uint32_t re[3] = {0, 0, 0}, im[3] = {0, 0, 0};
     if (r < n && c < n) {
       const cplx h = H[c + r * (long)n];   // H'[c, r] = conj(H'[r, c])
-      split3(h.x, re[0], re[1], re[2]);
-      split3(-h.y, im[0], im[1], im[2]);
-    } else {
-      for (int t = 0; t < 3; ++t) re[t] = im[t] = __float2bfloat16(0.f);
+      split3f(f32_rn(h.x), re[0], re[1], re[2]);
+      split3f(f32_rn(-h.y), im[0], im[1], im[2]);
     }
-    for (int t = 0; t < 3; ++t) {
-      __nv_bfloat162 v;
-      v.x = re[t];
-      v.y = im[t];
-      *(__nv_bfloat162*)(A + (t * mpad + r) * kpad + 2 * c) = v;
-    }
+#pragma unroll
+    for (int t = 0; t < 3; ++t) A32[t * slice_words + r * (kpad / 2) + c] = pack_lo_hi(re[t], im[t]);
   }
 }
 
@@ -320,62 +391,50 @@ __global__ void slice_H_kernel(int n, long kpad, long mpad, const cplx* __restri
 __global__ void slice_Y_kernel(int n, int ncols, long kpad, long npad, const cplx* __restrict__ Y,
                                __nv_bfloat16* __restrict__ B) {
   const long j = blockIdx.y;   // complex column, < npad / 2
-  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < kpad / 2; c += (long)gridDim.x * blockDim.x) {
-    __nv_bfloat16 xr[3], xi[3];
+  uint32_t* B32 = (uint32_t*)B;
+  const long kw = kpad / 2, slice_words = npad * kw;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < kw; c += (long)gridDim.x * blockDim.x) {
     if (j < ncols && c < n) {
       const cplx y = Y[c + j * (long)n];
-      split3(y.x, xr[0], xr[1], xr[2]);
-      split3(y.y, xi[0], xi[1], xi[2]);
+      store_slices(B32, slice_words, 2 * j * kw + c, (2 * j + 1) * kw + c, f32_rn(y.x), f32_rn(y.y));
     } else {
-      for (int t = 0; t < 3; ++t) xr[t] = xi[t] = __float2bfloat16(0.f);
-    }
-    for (int t = 0; t < 3; ++t) {
-      __nv_bfloat16* rowRe = B + (t * npad + 2 * j) * kpad;
-      __nv_bfloat162 v0, v1;
-      v0.x = xr[t]; v0.y = __hneg(xi[t]);
-      v1.x = xi[t]; v1.y = xr[t];
-      *(__nv_bfloat162*)(rowRe + 2 * c) = v0;
-      *(__nv_bfloat162*)(rowRe + kpad + 2 * c) = v1;
-    }
-  }
-}
-
-// R = Z - Yhat diag(lam);  D_1 = fa1 * R; B slices of D_1 for the next product
-__global__ void refine_first_kernel(int n, int ncols, long kpad, long npad, const cplx* __restrict__ Z,
-                                    const cplx* __restrict__ Y, const double* __restrict__ lam, double fa1,
-                                    cplx* __restrict__ R, cplx* __restrict__ D1, __nv_bfloat16* __restrict__ B) {
-  const long j = blockIdx.y;
-  const double l = lam[j];
-  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
-    const long e = j * n + c;
-    const cplx z = Z[e], y = Y[e];
-    const cplx r = cmk(z.x - l * y.x, z.y - l * y.y);
-    R[e] = r;
-    const cplx d = cmk(fa1 * r.x, fa1 * r.y);
-    D1[e] = d;
-    if (B) {
-      __nv_bfloat16 xr[3], xi[3];
-      split3(d.x, xr[0], xr[1], xr[2]);
-      split3(d.y, xi[0], xi[1], xi[2]);
+#pragma unroll
       for (int t = 0; t < 3; ++t) {
-        __nv_bfloat16* rowRe = B + (t * npad + 2 * j) * kpad;
-        __nv_bfloat162 v0, v1;
-        v0.x = xr[t]; v0.y = __hneg(xi[t]);
-        v1.x = xi[t]; v1.y = xr[t];
-        *(__nv_bfloat162*)(rowRe + 2 * c) = v0;
-        *(__nv_bfloat162*)(rowRe + kpad + 2 * c) = v1;
+        B32[t * slice_words + 2 * j * kw + c] = 0u;
+        B32[t * slice_words + (2 * j + 1) * kw + c] = 0u;
       }
     }
   }
 }
 
-// Yhat_j <- Yhat_j p_{m_j}(lam_j) + D_{m_j}, D_m in Dbuf[m & 1]
-__global__ void refine_combine_kernel(int n, cplx* __restrict__ Y, const cplx* __restrict__ D0,
-                                      const cplx* __restrict__ D1, const double* __restrict__ pm,
-                                      const int* __restrict__ deg) {
+// R = Z - Yhat diag(lam) (FP64, then kept in FP32: it only ever forces D, which is as small as
+// R); D_1 = fa_1 R: its slices for the next product, or its FP64 value for a degree-1 column.
+__global__ void refine_first_kernel(int n, int ncols, long kpad, long npad, const cplx* __restrict__ Z,
+                                    const cplx* __restrict__ Y, const double* __restrict__ lam, float fa1,
+                                    const int* __restrict__ deg, float2* __restrict__ R, cplx* __restrict__ Dout,
+                                    __nv_bfloat16* __restrict__ B) {
   const long j = blockIdx.y;
+  const double l = lam[j];
+  const bool more = deg[j] > 1;
+  uint32_t* B32 = (uint32_t*)B;
+  const long kw = kpad / 2, slice_words = npad * kw;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
+    const long e = j * n + c;
+    const cplx z = Z[e], y = Y[e];
+    const float2 r = make_float2(f32_rn(z.x - l * y.x), f32_rn(z.y - l * y.y));
+    R[e] = r;
+    const float dre = fa1 * r.x, dim = fa1 * r.y;
+    if (more) store_slices(B32, slice_words, 2 * j * kw + c, (2 * j + 1) * kw + c, dre, dim);
+    else Dout[e] = cmk(to_f64(dre), to_f64(dim));
+  }
+}
+
+// Yhat_j <- Yhat_j p_{m_j}(lam_j) + D_{m_j}
+__global__ void refine_combine_kernel(int n, cplx* __restrict__ Y, const cplx* __restrict__ D,
+                                      const double* __restrict__ pm, const int* __restrict__ deg) {
+  const long j = blockIdx.y;
+  if (deg[j] < 1) return;
   const double p = pm[j];
-  const cplx* D = (deg[j] & 1) ? D1 : D0;
   for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
     const long e = j * n + c;
     const cplx y = Y[e], d = D[e];
@@ -419,15 +478,27 @@ struct TcFilter {
   long kpad = 0, mpad = 0, npad = 0;
   __nv_bfloat16* A = nullptr;
   __nv_bfloat16* B[2] = {nullptr, nullptr};
-  cplx* D[2] = {nullptr, nullptr};   // corrected recurrence state
-  cplx* R = nullptr;
-  double* tab = nullptr;             // forcing scales per step and column, final p_m per column
+  cplx* Dout = nullptr;              // corrected recurrence: D_{m_j} of every column
+  float2* R = nullptr;               // corrected recurrence forcing
+  float* tabf = nullptr;             // forcing scales per step and column
+  double* pm = nullptr;              // final p_{m_j}(lam_j) per column
   int* deg = nullptr;
-  int tab_cap = 0;
+  int tab_cap = 0, k_cap = 0;
   int* err = nullptr;
   CUtensorMap mapA, mapB[2];
   bool attr = false;
+  cudaEvent_t ev[2] = {nullptr, nullptr};   // around the step launches
+  double ms_steps = 0.0;
+  long long col_steps = 0;
 };
+
+double tc_filter_take_ms(TcFilter* f, long long* col_steps) {
+  const double ms = f->ms_steps;
+  if (col_steps) *col_steps = f->col_steps;
+  f->ms_steps = 0.0;
+  f->col_steps = 0;
+  return ms;
+}
 
 TcFilter* tc_filter_new() { return new TcFilter(); }
 
@@ -436,12 +507,14 @@ void tc_filter_free(TcFilter* f) {
   cudaFree(f->A);
   cudaFree(f->B[0]);
   cudaFree(f->B[1]);
-  cudaFree(f->D[0]);
-  cudaFree(f->D[1]);
+  cudaFree(f->Dout);
   cudaFree(f->R);
-  cudaFree(f->tab);
+  cudaFree(f->tabf);
+  cudaFree(f->pm);
   cudaFree(f->deg);
   cudaFree(f->err);
+  for (int i = 0; i < 2; ++i)
+    if (f->ev[i]) cudaEventDestroy(f->ev[i]);
   delete f;
 }
 
@@ -450,11 +523,11 @@ static chfsi_status tc_ensure(TcFilter* f, int n, int k, cudaStream_t s) {
   cudaFree(f->A);
   cudaFree(f->B[0]);
   cudaFree(f->B[1]);
-  cudaFree(f->D[0]);
-  cudaFree(f->D[1]);
+  cudaFree(f->Dout);
   cudaFree(f->R);
   f->A = f->B[0] = f->B[1] = nullptr;
-  f->D[0] = f->D[1] = f->R = nullptr;
+  f->Dout = nullptr;
+  f->R = nullptr;
   f->n = n;
   f->k = k;
   f->kpad = round_up(2L * n, BK);
@@ -467,8 +540,8 @@ static chfsi_status tc_ensure(TcFilter* f, int n, int k, cudaStream_t s) {
     // stream (a plain cudaMemset) does not order against the filter launches that follow
     CHFSI_CUDA_TRY(cudaMemsetAsync(f->B[i], 0, sizeof(__nv_bfloat16) * 3 * f->npad * f->kpad, s));
   }
-  for (int i = 0; i < 2; ++i) CHFSI_CUDA_TRY(cudaMalloc(&f->D[i], sizeof(cplx) * (size_t)n * k));
-  CHFSI_CUDA_TRY(cudaMalloc(&f->R, sizeof(cplx) * (size_t)n * k));
+  CHFSI_CUDA_TRY(cudaMalloc(&f->Dout, sizeof(cplx) * (size_t)n * k));
+  CHFSI_CUDA_TRY(cudaMalloc(&f->R, sizeof(float2) * (size_t)n * k));
   if (!f->err) CHFSI_CUDA_TRY(cudaMalloc(&f->err, sizeof(int)));
   if (!make_map(&f->mapA, f->A, 3 * f->mpad, f->kpad, BM)) return CHFSI_ERR_CUDA;
   for (int i = 0; i < 2; ++i)
@@ -480,7 +553,7 @@ static chfsi_status tc_ensure(TcFilter* f, int n, int k, cudaStream_t s) {
   return CHFSI_OK;
 }
 
-chfsi_status tc_filter_run(TcFilter* f, cudaStream_t s, int n, const cplx* H, cplx* bufs[2], const int* cnt, int mmax,
+chfsi_status tc_filter_run(TcFilter* f, cudaStream_t s, int n, const cplx* H, cplx* Y, const int* cnt, int mmax,
                            const double* fa, const double* fb, const double* fg, const TcRefine* ref) {
   if (mmax < 1 || cnt[1] < 1) return CHFSI_OK;
   const int k = cnt[1];
@@ -493,70 +566,82 @@ chfsi_status tc_filter_run(TcFilter* f, cudaStream_t s, int n, const cplx* H, cp
     count_launch(1);
   }
   const unsigned cgrid = (unsigned)std::min<long>((n + 255) / 256, 16);
-  std::vector<double> htab;
+  std::vector<float> htab;
+  std::vector<double> hpm;
   if (ref) {
-    // device table: rows j = 0..mmax of fa[j] p_{j-1}(lam_i) (row 0 unused), then p_{m_i}(lam_i)
-    const int rows = mmax + 2;
-    if (f->tab_cap < rows * k) {
-      cudaFree(f->tab);
-      cudaFree(f->deg);
-      f->tab = nullptr;
-      f->deg = nullptr;
-      CHFSI_CUDA_TRY(cudaMalloc(&f->tab, sizeof(double) * (size_t)rows * k));
-      CHFSI_CUDA_TRY(cudaMalloc(&f->deg, sizeof(int) * (size_t)k));
-      f->tab_cap = rows * k;
+    // device tables: rows j = 1..mmax of fa[j] p_{j-1}(lam_i) (FP32), and p_{m_i}(lam_i) (FP64)
+    if (f->tab_cap < (mmax + 1) * k) {
+      cudaFree(f->tabf);
+      f->tabf = nullptr;
+      CHFSI_CUDA_TRY(cudaMalloc(&f->tabf, sizeof(float) * (size_t)(mmax + 1) * k));
+      f->tab_cap = (mmax + 1) * k;
     }
-    htab.assign((size_t)rows * k, 0.0);
+    if (f->k_cap < k) {
+      cudaFree(f->pm);
+      cudaFree(f->deg);
+      f->pm = nullptr;
+      f->deg = nullptr;
+      CHFSI_CUDA_TRY(cudaMalloc(&f->pm, sizeof(double) * (size_t)k));
+      CHFSI_CUDA_TRY(cudaMalloc(&f->deg, sizeof(int) * (size_t)k));
+      f->k_cap = k;
+    }
+    htab.assign((size_t)(mmax + 1) * k, 0.0f);
+    hpm.assign(k, 0.0);
     for (int j = 1; j <= mmax; ++j)
-      for (int i = 0; i < k; ++i) htab[(size_t)j * k + i] = fa[j] * ref->ptab[(size_t)(j - 1) * k + i];
-    for (int i = 0; i < k; ++i) htab[(size_t)(mmax + 1) * k + i] = ref->ptab[(size_t)ref->deg[i] * k + i];
-    CHFSI_CUDA_TRY(cudaMemcpyAsync(f->tab, htab.data(), sizeof(double) * htab.size(), cudaMemcpyHostToDevice, s));
+      for (int i = 0; i < k; ++i) htab[(size_t)j * k + i] = (float)(fa[j] * ref->ptab[(size_t)(j - 1) * k + i]);
+    for (int i = 0; i < k; ++i) hpm[i] = ref->ptab[(size_t)ref->deg[i] * k + i];
+    CHFSI_CUDA_TRY(cudaMemcpyAsync(f->tabf, htab.data(), sizeof(float) * htab.size(), cudaMemcpyHostToDevice, s));
+    CHFSI_CUDA_TRY(cudaMemcpyAsync(f->pm, hpm.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
     CHFSI_CUDA_TRY(cudaMemcpyAsync(f->deg, ref->deg, sizeof(int) * k, cudaMemcpyHostToDevice, s));
     dim3 g1(cgrid, (unsigned)k);
-    refine_first_kernel<<<g1, 256, 0, s>>>(n, k, f->kpad, f->npad, ref->Z, bufs[0], ref->lam, fa[1], f->R, f->D[1],
-                                           mmax > 1 ? f->B[1] : nullptr);
+    refine_first_kernel<<<g1, 256, 0, s>>>(n, k, f->kpad, f->npad, ref->Z, Y, ref->lam, (float)fa[1], f->deg, f->R,
+                                           f->Dout, f->B[1]);
     count_launch(1);
   } else {
     dim3 gy((unsigned)((f->kpad / 2 + 255) / 256), (unsigned)(f->npad / 2));
-    slice_Y_kernel<<<gy, 256, 0, s>>>(n, k, f->kpad, f->npad, bufs[0], f->B[0]);
+    slice_Y_kernel<<<gy, 256, 0, s>>>(n, k, f->kpad, f->npad, Y, f->B[0]);
     count_launch(1);
   }
+  if (!f->ev[0]) {
+    CHFSI_CUDA_TRY(cudaEventCreate(&f->ev[0]));
+    CHFSI_CUDA_TRY(cudaEventCreate(&f->ev[1]));
+  }
+  CHFSI_CUDA_TRY(cudaEventRecord(f->ev[0], s));
   for (int j = ref ? 2 : 1; j <= mmax; ++j) {
     StepArgs g{};
     g.n = n;
     g.mtiles = (int)(f->mpad / BM);
     g.ncols = cnt[j];
+    g.ncols_next = j < mmax ? cnt[j + 1] : 0;
     g.kblocks = (int)(f->kpad / BK);
-    g.ldb_next = f->kpad;
-    g.nslice_rows_b = f->npad;
-    if (ref) {
-      g.Ycur = f->D[(j - 1) & 1];
-      g.Yout = f->D[j & 1];
-      g.fg = (j >= 3) ? fg[j] : 0.0;      // D_0 = 0
-      g.R = f->R;
-      g.fcol = f->tab + (size_t)j * k;
-    } else {
-      g.Ycur = bufs[(j - 1) & 1];
-      g.Yout = bufs[j & 1];
-      g.fg = (j >= 2) ? fg[j] : 0.0;
-    }
-    g.Bnext = (j < mmax) ? f->B[j & 1] : nullptr;
-    g.fa = fa[j];
-    g.fb = fb[j];
+    g.kpad = f->kpad;
+    g.npad = f->npad;
+    g.Bcur = f->B[(j - 1) & 1];
+    g.Bnext = f->B[j & 1];
+    g.Yfinal = ref ? f->Dout : Y;
+    g.fa = (float)fa[j];
+    g.fb = (float)fb[j];
+    g.fg = (float)((j >= (ref ? 3 : 2)) ? fg[j] : 0.0);   // Y_{-1} = 0; in the corrected form D_0 = 0
+    g.R = ref ? f->R : nullptr;
+    g.fcol = ref ? f->tabf + (size_t)j * k : nullptr;
     g.err = f->err;
+    f->col_steps += cnt[j];
     dim3 grid((unsigned)g.mtiles, (unsigned)((2L * cnt[j] + BN - 1) / BN));
     tc_filter_step_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(f->mapA, f->mapB[(j - 1) & 1], g);
     count_launch(1);
     CHFSI_CUDA_TRY(cudaGetLastError());
   }
+  CHFSI_CUDA_TRY(cudaEventRecord(f->ev[1], s));
   if (ref) {
     dim3 g2(cgrid, (unsigned)k);
-    refine_combine_kernel<<<g2, 256, 0, s>>>(n, bufs[0], f->D[0], f->D[1], f->tab + (size_t)(mmax + 1) * k, f->deg);
+    refine_combine_kernel<<<g2, 256, 0, s>>>(n, Y, f->Dout, f->pm, f->deg);
     count_launch(1);
   }
   int h = 0;
   CHFSI_CUDA_TRY(cudaMemcpyAsync(&h, f->err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CHFSI_CUDA_TRY(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, f->ev[0], f->ev[1]) == cudaSuccess) f->ms_steps += ms;
   if (h == DEV_ERR_TIMEOUT) return CHFSI_ERR_TIMEOUT;
   if (h != DEV_OK) return CHFSI_ERR_NUMERIC;
   return CHFSI_OK;

@@ -20,8 +20,12 @@ struct TcRefine {
 };
 
 // Runs mmax recurrence steps: Y_j = fa[j] H Y_{j-1} + fb[j] Y_{j-1} + fg[j] Y_{j-2} on the
-// first cnt[j] columns; Y_j lands in bufs[j & 1] (bufs[0] holds Y_0 on entry).  With ref
-// the corrected form runs instead and the result replaces bufs[0] for every column.
-chfsi_status tc_filter_run(TcFilter* f, cudaStream_t s, int n, const cplx* H, cplx* bufs[2], const int* cnt,
-                           int mmax, const double* fa, const double* fb, const double* fg,
-                           const TcRefine* ref = nullptr);
+// first cnt[j] columns (cnt non-increasing: column i takes deg_i steps, the number of j with
+// i < cnt[j]); Y (n x cnt[1], ld n) holds Y_0 on entry and each column's last Y_j on return.
+// With ref the corrected form runs instead, with the same result.
+// Device time (ms) of the recurrence step launches since the last call, and the column-steps
+// they processed (sum over launches of their complex columns); resets both.
+double tc_filter_take_ms(TcFilter* f, long long* col_steps = nullptr);
+
+chfsi_status tc_filter_run(TcFilter* f, cudaStream_t s, int n, const cplx* H, cplx* Y, const int* cnt, int mmax,
+                           const double* fa, const double* fb, const double* fg, const TcRefine* ref = nullptr);

@@ -31,6 +31,7 @@ struct JacobiArgs {
   GridBarrier bar;
   int* err;
   int* sweeps;
+  int* rounds;        // rounds executed (every round of a sweep updates the whole matrix)
   int max_sweeps;
 };
 
@@ -125,6 +126,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(JacobiArgs g) {
   }
   if (tid == 0) {
     *g.sweeps = sweep;
+    *g.rounds = sweep * (kk - 1);
     if (!converged) atomicExch(g.err, DEV_ERR_NO_CONV);
   }
 }
@@ -156,6 +158,7 @@ struct JacobiFastArgs {
   GridBarrier bar;
   int* err;
   int* sweeps;
+  int* rounds;       // rounds in which a pair rotated (each updates A and V)
   int* final_buf;
   int* offcount;     // per sweep: off-diagonal entries above the threshold after it (zeroed)
   int max_sweeps;
@@ -212,7 +215,7 @@ __global__ void __launch_bounds__(256) jacobi_fast_kernel(JacobiFastArgs g) {
   const long long thr_bits = abs_bits(0.7071067811865476 * thresh);
   for (long e = tid; e < (long)k * k; e += nth) g.V[e] = cmk((e % k) == (e / k) ? 1.0 : 0.0, 0.0);
   const long ntri = (long)np * (np + 1) / 2;   // blocks (a, b), a <= b
-  int cur = 0, sweep = 0;
+  int cur = 0, sweep = 0, rounds = 0;
   bool converged = false;
   for (; sweep < g.max_sweeps && !converged; ++sweep) {
     int on_sweep = 0;
@@ -232,6 +235,7 @@ __global__ void __launch_bounds__(256) jacobi_fast_kernel(JacobiFastArgs g) {
       // no pair rotates this round: nothing changes, so every CTA (all computed the same
       // rotations from the same data) skips the copy, the buffer swap and the grid barrier
       if (on_round == 0) continue;
+      ++rounds;
       for (long e = tid; e < ntri + (long)k * np; e += nth) {
         if (e < ntri) {
           // triangular index -> (a, b), a <= b: b (b + 1) / 2 <= e < (b + 1) (b + 2) / 2
@@ -321,6 +325,7 @@ __global__ void __launch_bounds__(256) jacobi_fast_kernel(JacobiFastArgs g) {
   }
   if (tid == 0) {
     *g.sweeps = sweep;   // sweeps that rotated
+    *g.rounds = rounds;
     *g.final_buf = cur;
     if (!converged) atomicExch(g.err, DEV_ERR_NO_CONV);
   }
@@ -403,7 +408,8 @@ int fast_coop_blocks() {
   return cap;
 }
 
-cudaError_t jacobi_eig(cudaStream_t s, int k, cplx* G, double* lam, cplx* W, void* work, int* err, int* sweeps) {
+cudaError_t jacobi_eig(cudaStream_t s, int k, cplx* G, double* lam, cplx* W, void* work, int* err, int* sweeps,
+                       int* rounds) {
   if (k <= 0) return cudaSuccess;
   if (k <= 2 * JF_MAXPAIRS) {
     // one barrier per round; the second A buffer follows V in the workspace
@@ -425,6 +431,7 @@ cudaError_t jacobi_eig(cudaStream_t s, int k, cplx* G, double* lam, cplx* W, voi
     g.bar.count = bar;
     g.err = err;
     g.sweeps = sweeps;
+    g.rounds = rounds;
     g.max_sweeps = max_sweeps;
     cudaError_t e = cudaMemsetAsync(zero_begin, 0, (size_t)(w - zero_begin), s);
     if (e != cudaSuccess) return e;
@@ -455,6 +462,7 @@ cudaError_t jacobi_eig(cudaStream_t s, int k, cplx* G, double* lam, cplx* W, voi
   g.bar.count = bar;
   g.err = err;
   g.sweeps = sweeps;
+  g.rounds = rounds;
   g.max_sweeps = max_sweeps;
   cudaError_t e = cudaMemsetAsync(g.rot_count, 0, sizeof(int) * max_sweeps + sizeof(double) * 2 + sizeof(unsigned) * 4, s);
   if (e != cudaSuccess) return e;
@@ -528,6 +536,7 @@ extern "C" chfsi_status chfsi_reduced_eig_noalloc(void* cuda_stream, int k, cons
   unsigned* bar = (unsigned*)w;   w += sizeof(unsigned) * 4;
   g.err = (int*)w;                w += sizeof(int);
   g.sweeps = (int*)w;             w += sizeof(int);
+  g.rounds = (int*)w;             w += sizeof(int);
   g.bar.count = bar;
   g.max_sweeps = NOALLOC_SWEEPS;
   // the array keeps the previous call's contents: copy G in and clear what must start at zero
@@ -539,7 +548,8 @@ extern "C" chfsi_status chfsi_reduced_eig_noalloc(void* cuda_stream, int k, cons
   const long work_items = (long)(kk / 2) * (kk / 2) + (long)k * (kk / 2);
   int blocks = coop_blocks((int)((work_items + 255) / 256));
   void* args[] = {&g};
-  e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(blocks), dim3(256), args, 0, s);
+  // serialised with the library's other grid-barrier kernels on this device (see coop_launch)
+  e = coop_launch((const void*)jacobi_kernel, dim3(blocks), dim3(256), args, s);
   count_launch();
   if (e != cudaSuccess) return chfsi_cuda_error(e, "jacobi launch");
   jacobi_sort_kernel<<<k < 1024 ? k : 1024, 128, 0, s>>>(k, g.A, (const cplx*)g.V, lam, (cplx*)W);

@@ -56,3 +56,33 @@ def test_workspace_estimate_without_gpu():
         passes = -(-2 * n // 3584)
         need = 16 * 4 * n * n + 2 * 12 * (n * 2 * n + 2 * n * 2 * n) + 16 * passes * n * n
         assert ws(n, nev, nex, mixed) >= need
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the header's sizes and field offsets (a C probe
+    compiled against include/chfsi.h prints them)."""
+    import ctypes
+    import shutil
+    import subprocess
+    import pytest
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = {"chfsi_params": [f for f, _ in chfsi.Params._fields_],
+              "chfsi_info": [f for f, _ in chfsi.Info._fields_]}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "chfsi.h"', "int main(void) {"]
+    for st, fs in fields.items():
+        lines.append(f'printf("{st} size %zu\\n", sizeof({st}));')
+        for f in fs:
+            lines.append(f'printf("{st} {f} %zu\\n", offsetof({st}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for st, cls in (("chfsi_params", chfsi.Params), ("chfsi_info", chfsi.Info)):
+        assert got[(st, "size")] == ctypes.sizeof(cls), st
+        for f, _ in cls._fields_:
+            assert got[(st, f)] == getattr(cls, f).offset, (st, f)

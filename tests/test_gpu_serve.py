@@ -9,7 +9,7 @@ from oracle import direct as O1
 from paper_1305_5120_gb300 import chfsi as lib
 from paper_1305_5120_gb300 import serve, synth
 
-from gpu_util import torch_cuda
+from gpu_util import floored_residuals, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -95,3 +95,39 @@ def test_admission_respects_memory_budget():
         assert live <= srv.hbm_budget
     # and the budget bound concurrency below the four slots at least once
     assert sum(sorted(need_of.values())[:4]) > srv.hbm_budget or len(reqs) < 4
+
+
+def test_kpoint_sizes_over_four_slots_exact_and_complete():
+    """Problems of k-point size (n ~ U[1500, 4000], nev 5-15 % of n, cold starts) over four
+    concurrent slots, so that slot contexts move between sizes while other slots compute:
+    every eigenvalue equals the prescribed spectrum to 1e-10, every generalized residual is
+    at most 1e-10 (relative to ||H x||, or for |lam| < 1e-4 ||H'|| to 1e-4 ||H'|| ||S x||: the
+    solver's lock test, see floored_residuals), and the inertia count at the gap confirms
+    that the lowest nev were found."""
+    torch = torch_cuda()
+    rng = np.random.default_rng(5)
+    probs = []
+    for i in range(10):
+        n = int(rng.integers(1500, 4001))
+        nev = max(4, int(round(n * rng.uniform(0.05, 0.15))))
+        nex = max(2, int(round(0.2 * nev)))
+        H, S, lam = synth.prescribed_pencil_device(n, nev, 50.0, seed=100 + i)
+        probs.append((n, nev, nex, H, S, lam))
+    torch.cuda.synchronize()
+    reqs = [serve.SequenceRequest(seq_id=i, arrival=0.0, n=n, nev=nev, nex=nex, steps=1,
+                                  make_step=lambda l, H=H, S=S: (H, S), degree=20)
+            for i, (n, nev, nex, H, S, lam) in enumerate(probs)]
+    srv = serve.Server(device=0, slots=4, keep_vectors=True, precision=lib.CHFSI_PREC_MIXED, check_inertia=1)
+    recs = srv.run(reqs, realtime=False)
+    assert len(recs) == len(probs)
+    for r in recs:
+        n, nev, nex, H, S, lam = probs[r.seq_id]
+        assert r.status == 0, (r.seq_id, n, nev, lib.STATUS.get(r.status, r.status))
+        assert r.info["completeness"] == 2, (r.seq_id, r.info["completeness"])
+        ref = lam[:nev].cpu().numpy()
+        assert np.abs(r.evals - ref).max() <= 1e-10 * max(1.0, np.abs(ref).max()), r.seq_id
+        X = torch.from_numpy(r.X).to("cuda")
+        a, b, a0 = r.info["bounds"]
+        res, floored = floored_residuals(H, S, r.evals, X, max(abs(a0), abs(b)))
+        assert res.max() <= 1e-10, (r.seq_id, res.max())
+        assert floored.sum() == r.info["n_floor"], (r.seq_id, floored.sum(), r.info["n_floor"])

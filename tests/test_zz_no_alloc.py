@@ -20,7 +20,7 @@ def herm(k, seed):
     return synth.hermitian_part(synth.complex_gaussian(synth.rng_for(seed, 700 + k), (k, k)))
 
 
-@pytest.mark.parametrize("k", [48, 240])
+@pytest.mark.parametrize("k", [47, 48, 240, 256])
 def test_noalloc_matches_context_eigensolver_twice(k):
     torch = torch_cuda()
     ctx = lib.Context(device=0)
