@@ -105,6 +105,10 @@ typedef struct {
                               kernels of ms_filter_lowp, without operand slicing) */
   long long filter_step_cols; /* column-steps those kernels processed (each: one complex column
                               times the n x n H', 48 n^2 executed / 8 n^2 algorithmic flops) */
+  int eig_refined;         /* reduced eigensolves done by FP32 one-sided Jacobi + FP64 refinement */
+  int eig_refine_iters;    /* their FP64 refinement iterations */
+  int eig_f32_sweeps;      /* their FP32 sweeps */
+  int eig_fallbacks;       /* reduced eigensolves that fell back to the FP64 Jacobi */
   double ms_chol;          /* device time of the Cholesky factorisation of S and its inverse */
   double chol_flop;        /* its algorithmic work: (8/3) n^3 real flops (factor and inverse) */
 } chfsi_info;
@@ -142,6 +146,24 @@ chfsi_status chfsi_solve(chfsi_ctx *c, const void *H, const void *S, int n, int 
  */
 chfsi_status chfsi_next_in_sequence(chfsi_ctx *c, const void *H_next, const void *S_next,
                                     double *evals, void *X, chfsi_info *info);
+
+/*
+ * Many independent problems solved together (the k-point problems of one SCF cycle, Section
+ * 2: for every k-point its own H x = lambda S x).  Problem p: H[p], S[p] (n[p] x n[p]),
+ * nev[p], nex[p]; random start blocks; every problem to the same tol and degree.  Each
+ * problem runs Algorithm 1 as chfsi_solve would (same results); the iterations of all
+ * problems advance together, and the filter of one iteration of every problem is one grouped
+ * tensor-core launch per recurrence step (a tile scheduler over all problems' tiles, tile
+ * width picked by a timing autotuner, the step launches captured into a CUDA graph).
+ * Host arrays of device pointers: H, S, evals (evals[p]: nev[p] doubles), X (X[p]: n[p] x
+ * nev[p]); host arrays status[count] (per problem) and info[count] (may be NULL).  Returns
+ * CHFSI_OK when every problem succeeded, else the first problem's failure status.  The
+ * context keeps one internal context per problem slot (device memory for each; released by
+ * chfsi_destroy); the problems are not sequences (chfsi_next_in_sequence does not apply).
+ */
+chfsi_status chfsi_solve_batch(chfsi_ctx *c, int count, const void *const *H, const void *const *S, const int *n,
+                               const int *nev, const int *nex, double tol, int degree, double *const *evals,
+                               void *const *X, chfsi_status *status, chfsi_info *info);
 
 /* Upper estimate of the device memory (bytes) a context allocates to solve problems of size
  * (n, nev, nex) in the given precision; callers that admit work by memory budget (the

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libchfsi.so")
-SOURCES = ["chfsi_api.cu", "zgemm.cu", "dense.cu", "lanczos.cu", "jacobi.cu", "filter_tc.cu", "ozaki.cu"]
+SOURCES = ["chfsi_api.cu", "zgemm.cu", "dense.cu", "lanczos.cu", "jacobi.cu", "eigen.cu", "filter_tc.cu", "ozaki.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -46,7 +46,9 @@ class Info(ctypes.Structure):
                 ("gemm_tc_flop", ctypes.c_double), ("ms_eig", ctypes.c_double), ("eig_sweeps", ctypes.c_int),
                 ("eig_rounds", ctypes.c_longlong), ("eig_flop", ctypes.c_double), ("n_floor", ctypes.c_int),
                 ("completeness", ctypes.c_int), ("ms_filter_steps", ctypes.c_double),
-                ("filter_step_cols", ctypes.c_longlong), ("ms_chol", ctypes.c_double),
+                ("filter_step_cols", ctypes.c_longlong), ("eig_refined", ctypes.c_int),
+                ("eig_refine_iters", ctypes.c_int), ("eig_f32_sweeps", ctypes.c_int), ("eig_fallbacks", ctypes.c_int),
+                ("ms_chol", ctypes.c_double),
                 ("chol_flop", ctypes.c_double)]
 
     def as_dict(self):
@@ -57,7 +59,9 @@ class Info(ctypes.Structure):
                 "gemm_tc_flop": self.gemm_tc_flop, "ms_eig": self.ms_eig, "eig_sweeps": self.eig_sweeps,
                 "eig_rounds": self.eig_rounds, "eig_flop": self.eig_flop, "n_floor": self.n_floor,
                 "completeness": self.completeness, "ms_filter_steps": self.ms_filter_steps,
-                "filter_step_cols": self.filter_step_cols,
+                "filter_step_cols": self.filter_step_cols, "eig_refined": self.eig_refined,
+                "eig_refine_iters": self.eig_refine_iters, "eig_f32_sweeps": self.eig_f32_sweeps,
+                "eig_fallbacks": self.eig_fallbacks,
                 "ms_chol": self.ms_chol, "chol_flop": self.chol_flop}
 
 
@@ -71,6 +75,9 @@ _SIGS = {
     "chfsi_create": [ctypes.POINTER(_P), _I, _P, ctypes.POINTER(Params)],
     "chfsi_solve": [_P, _P, _P, _I, _I, _I, _P, _D, _I, _P, _P, ctypes.POINTER(Info)],
     "chfsi_next_in_sequence": [_P, _P, _P, _P, _P, ctypes.POINTER(Info)],
+    "chfsi_solve_batch": [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                          ctypes.POINTER(_I), _D, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I),
+                          ctypes.POINTER(Info)],
     "chfsi_destroy": [_P],
     "chfsi_status_string": [_I],
     "chfsi_kernel_launches": [],
@@ -225,6 +232,23 @@ class Context:
         st = self.lib.chfsi_next_in_sequence(self.h, _ptr(H_next), _ptr(S_next), _ptr(evals), _ptr(X),
                                              ctypes.byref(info))
         return st, evals, X, info
+
+    def solve_batch(self, Hs, Ss, ns, nevs, nexs, tol=1e-10, degree=0, evals=None, Xs=None):
+        """Independent problems solved together (chfsi_solve_batch).  Hs, Ss: lists of device
+        buffers (colmajor); returns (status of the call, per-problem statuses, evals, Xs, infos)."""
+        import torch
+        cnt = len(Hs)
+        evals = evals if evals is not None else [torch.empty(nv, dtype=torch.float64, device=Hs[p].device)
+                                                 for p, nv in enumerate(nevs)]
+        Xs = Xs if Xs is not None else [torch.empty((nv, n), dtype=torch.complex128, device=Hs[p].device)
+                                        for p, (n, nv) in enumerate(zip(ns, nevs))]
+        arrP = lambda ts: (_P * cnt)(*[_ptr(t) for t in ts])
+        arrI = lambda xs: (_I * cnt)(*[int(x) for x in xs])
+        status = (_I * cnt)()
+        infos = (Info * cnt)()
+        st = self.lib.chfsi_solve_batch(self.h, cnt, arrP(Hs), arrP(Ss), arrI(ns), arrI(nevs), arrI(nexs), tol, degree,
+                                        arrP(evals), arrP(Xs), status, infos)
+        return st, list(status), evals, Xs, list(infos)
 
     # --- stages -------------------------------------------------------------------------------
     def gemm(self, opA, opB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, precision=CHFSI_PREC_FP64):

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "dense.cuh"
+#include "eigen.cuh"
 #include "filter_tc.cuh"
 #include "jacobi.cuh"
 #include "lanczos.cuh"
@@ -64,15 +65,20 @@ struct Buf {
   size_t bytes = 0;
 };
 
+// Named workspaces of one context, grown on demand.  cudaFree is not guaranteed to wait for
+// kernels still queued on the context's stream, and the memory it releases can be handed to
+// another thread's cudaMalloc at once: a buffer is only freed after the stream has drained.
 struct Arena {
   std::vector<std::pair<const char*, Buf>> bufs;
-  cudaError_t get(const char* name, size_t bytes, void** out) {
+  cudaError_t get(const char* name, size_t bytes, void** out, cudaStream_t s) {
     for (auto& b : bufs) {
       if (strcmp(b.first, name) == 0) {
         if (b.second.bytes >= bytes) {
           *out = b.second.p;
           return cudaSuccess;
         }
+        cudaError_t es = cudaStreamSynchronize(s);
+        if (es != cudaSuccess) return es;
         cudaFree(b.second.p);
         b.second = Buf{};
         cudaError_t e = cudaMalloc(&b.second.p, bytes);
@@ -144,6 +150,15 @@ struct chfsi_ctx {
   int* sweeps_host = nullptr;     // pinned ring of (sweeps, rounds) copied after each eigensolve
   int n_sweeps_pending = 0;
   int pending_k[64] = {};         // matrix order of each pending eigensolve
+  bool spans_off = false;         // inside a span of another kind: the products record none
+  // reduced eigensolver by FP32 start + FP64 refinement: calls, refinement iterations, FP32
+  // sweeps, and calls that fell back to the FP64 Jacobi
+  int acc_eig_refined = 0, acc_eig_iters = 0, acc_eig_f32_sweeps = 0, acc_eig_fallbacks = 0;
+  int eig_path = -1;              // -1 automatic; 0 always the FP64 Jacobi (stage entry point option)
+  // batched solves: one internal context per problem slot (sharing this context's stream and
+  // parameters) and the grouped-filter state
+  std::vector<chfsi_ctx*> kids;
+  TcBatch* tcb = nullptr;
 };
 
 namespace {
@@ -161,7 +176,7 @@ inline chfsi_status cu(cudaError_t e, const char* what) {
 template <typename T>
 chfsi_status buf(chfsi_ctx* c, const char* name, size_t count, T** out) {
   void* p = nullptr;
-  cudaError_t e = c->arena.get(name, count * sizeof(T), &p);
+  cudaError_t e = c->arena.get(name, count * sizeof(T), &p, c->stream);
   if (e != cudaSuccess) return chfsi_cuda_error(e, name);
   *out = (T*)p;
   return CHFSI_OK;
@@ -169,6 +184,7 @@ chfsi_status buf(chfsi_ctx* c, const char* name, size_t count, T** out) {
 
 chfsi_status ensure_host(chfsi_ctx* c, int k) {
   if (k <= c->kcap) return CHFSI_OK;
+  CU(cudaStreamSynchronize(c->stream));   // no copy into the old mirrors may be pending
   if (c->h_d) cudaFreeHost(c->h_d);
   if (c->h_i) cudaFreeHost(c->h_i);
   c->h_d = nullptr;
@@ -253,11 +269,14 @@ cudaEvent_t pool_event(chfsi_ctx* c) {
   return e;
 }
 void span_begin(chfsi_ctx* c, int kind, double flop) {
+  if (c->spans_off) return;
   chfsi_ctx::Span sp{pool_event(c), pool_event(c), kind, flop};
   cudaEventRecord(sp.a, c->stream);
   c->spans.push_back(sp);
 }
-void span_end(chfsi_ctx* c) { cudaEventRecord(c->spans.back().b, c->stream); }
+void span_end(chfsi_ctx* c) {
+  if (!c->spans_off) cudaEventRecord(c->spans.back().b, c->stream);
+}
 // call after a stream synchronisation: adds the finished spans to the accumulators
 void spans_flush(chfsi_ctx* c) {
   for (auto& sp : c->spans) {
@@ -437,47 +456,78 @@ struct RitzData {
   const double* lam_host; // the same values (host)
 };
 
-chfsi_status run_filter(chfsi_ctx* c, int n, int k, const cplx* Hs, cplx* Y, const int* deg, double a, double b,
-                        double a0, int precision, long long* col_steps, const RitzData* ritz = nullptr) {
-  if (k <= 0) return CHFSI_OK;
-  const int mmax = deg[0];
-  if (mmax <= 0) return CHFSI_OK;
+// The host side of one filter call: per-step column counts (columns sorted by non-increasing
+// degree), the recurrence coefficients and, for the corrected form, p_j(lam_i).
+struct FilterPlan {
+  int n = 0, k = 0, mmax = 0;
+  const cplx* Hs = nullptr;
+  cplx* Y = nullptr;
+  std::vector<int> cnt, deg;
+  std::vector<double> fa, fb, fg, ptab;
+  bool ritz = false;
+  TcRefine ref{};
+  long long steps = 0;
+};
+
+chfsi_status filter_plan(int n, int k, const cplx* Hs, cplx* Y, const int* deg, double a, double b, double a0,
+                         const RitzData* ritz, FilterPlan* fp) {
+  fp->n = n;
+  fp->k = k;
+  fp->Hs = Hs;
+  fp->Y = Y;
+  fp->mmax = k > 0 ? deg[0] : 0;
+  fp->steps = 0;
+  fp->ritz = false;
+  if (k <= 0 || fp->mmax <= 0) return CHFSI_OK;
+  const int mmax = fp->mmax;
   for (int i = 1; i < k; ++i)
     if (deg[i] > deg[i - 1] || deg[i] < 0) return CHFSI_ERR_ARG;
   if (!(b > a) || !(a0 < a)) return CHFSI_ERR_ARG;
-  std::vector<double> fa, fb, fg;
-  filter_coefs(mmax, a, b, a0, fa, fb, fg);
-  std::vector<int> cnt(mmax + 1, 0);
+  filter_coefs(mmax, a, b, a0, fp->fa, fp->fb, fp->fg);
+  fp->deg.assign(deg, deg + k);
+  fp->cnt.assign(mmax + 1, 0);
   for (int j = 1; j <= mmax; ++j) {
     int q = 0;
     while (q < k && deg[q] >= j) ++q;
-    cnt[j] = q;
+    fp->cnt[j] = q;
+    fp->steps += q;
   }
-  long long steps = 0;
-  for (int j = 1; j <= mmax; ++j) steps += cnt[j];
-  if (col_steps) *col_steps += steps;
+  if (ritz) {
+    // p_j(lam_i), j = 0..mmax, by the scalar form of the same recurrence
+    fp->ptab.assign((size_t)(mmax + 1) * k, 0.0);
+    for (int i = 0; i < k; ++i) {
+      const double l = ritz->lam_host[i];
+      double pm2 = 0.0, pm1 = 1.0;
+      fp->ptab[i] = 1.0;
+      for (int j = 1; j <= mmax; ++j) {
+        const double p = fp->fa[j] * l * pm1 + fp->fb[j] * pm1 + (j >= 2 ? fp->fg[j] * pm2 : 0.0);
+        fp->ptab[(size_t)j * k + i] = p;
+        pm2 = pm1;
+        pm1 = p;
+      }
+    }
+    fp->ritz = true;
+    fp->ref = TcRefine{ritz->Z, ritz->lam_dev, fp->ptab.data(), fp->deg.data()};
+  }
+  return CHFSI_OK;
+}
+
+chfsi_status run_filter(chfsi_ctx* c, int n, int k, const cplx* Hs, cplx* Y, const int* deg, double a, double b,
+                        double a0, int precision, long long* col_steps, const RitzData* ritz = nullptr) {
+  FilterPlan fp;
+  TRY(filter_plan(n, k, Hs, Y, deg, a, b, a0, precision == CHFSI_PREC_MIXED ? ritz : nullptr, &fp));
+  if (fp.mmax <= 0) return CHFSI_OK;
+  const int mmax = fp.mmax;
+  const std::vector<int>& cnt = fp.cnt;
+  const std::vector<double>& fa = fp.fa;
+  const std::vector<double>& fb = fp.fb;
+  const std::vector<double>& fg = fp.fg;
+  if (col_steps) *col_steps += fp.steps;
   if (precision == CHFSI_PREC_MIXED) {
     if (!c->tc) c->tc = tc_filter_new();
-    if (ritz) {
-      // p_j(lam_i), j = 0..mmax, by the scalar form of the same recurrence
-      std::vector<double> ptab((size_t)(mmax + 1) * k);
-      for (int i = 0; i < k; ++i) {
-        const double l = ritz->lam_host[i];
-        double pm2 = 0.0, pm1 = 1.0;
-        ptab[i] = 1.0;
-        for (int j = 1; j <= mmax; ++j) {
-          const double p = fa[j] * l * pm1 + fb[j] * pm1 + (j >= 2 ? fg[j] * pm2 : 0.0);
-          ptab[(size_t)j * k + i] = p;
-          pm2 = pm1;
-          pm1 = p;
-        }
-      }
-      TcRefine ref{ritz->Z, ritz->lam_dev, ptab.data(), deg};
-      TRY(tc_filter_run(c->tc, c->stream, n, Hs, Y, cnt.data(), mmax, fa.data(), fb.data(), fg.data(), &ref));
-      return CHFSI_OK;
-    }
     // every column's result lands in Y at its last step
-    TRY(tc_filter_run(c->tc, c->stream, n, Hs, Y, cnt.data(), mmax, fa.data(), fb.data(), fg.data()));
+    TRY(tc_filter_run(c->tc, c->stream, n, Hs, Y, cnt.data(), mmax, fa.data(), fb.data(), fg.data(),
+                      fp.ritz ? &fp.ref : nullptr));
     return CHFSI_OK;
   }
   cplx* Y2;
@@ -731,13 +781,201 @@ chfsi_status orthonormalize(chfsi_ctx* c, int n, int nl, const cplx* Yl, int k, 
 }
 
 // a7 ---------------------------------------------------------------------------------------
+// FP32 one-sided Jacobi in one cluster, then FP64 refinement (eigen.cu); *done = false when
+// it did not converge within its budget (the caller then runs the FP64 Jacobi on G, which
+// this path leaves untouched).
+__global__ void fro_norm_kernel(int k, const cplx* A, double* out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (long e = threadIdx.x; e < (long)k * k; e += blockDim.x) s += cabs2(A[e]);
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) *out = sqrt(s);
+}
+
+struct Groups {   // connected components of the strongly coupled pairs (host side)
+  std::vector<int> gid, gpos, off, idx, voff;
+  int nv = 0, largest = 0;
+};
+void make_groups(int k, const std::vector<int2>& pairs, Groups* g) {
+  std::vector<int> parent(k);
+  std::iota(parent.begin(), parent.end(), 0);
+  auto find = [&](int a) {
+    while (parent[a] != a) a = parent[a] = parent[parent[a]];
+    return a;
+  };
+  for (const int2& p : pairs) {
+    const int a = find(p.x), b = find(p.y);
+    if (a != b) parent[std::max(a, b)] = std::min(a, b);
+  }
+  std::vector<std::vector<int>> members(k);
+  for (int i = 0; i < k; ++i) members[find(i)].push_back(i);
+  g->gid.assign(k, -1);
+  g->gpos.assign(k, 0);
+  g->off.assign(1, 0);
+  g->idx.clear();
+  g->voff.clear();
+  g->nv = 0;
+  g->largest = 0;
+  for (int r = 0; r < k; ++r) {
+    const auto& m = members[r];
+    if (m.size() < 2) continue;
+    const int id = (int)g->voff.size();
+    g->voff.push_back(g->nv);
+    g->nv += (int)(m.size() * m.size());
+    for (size_t q = 0; q < m.size(); ++q) {
+      g->gid[m[q]] = id;
+      g->gpos[m[q]] = (int)q;
+      g->idx.push_back(m[q]);
+    }
+    g->off.push_back((int)g->idx.size());
+    g->largest = std::max(g->largest, (int)m.size());
+  }
+}
+
+chfsi_status reduced_eig_refined(chfsi_ctx* c, int k, const cplx* G, double* lam, cplx* W, bool* done) {
+  *done = false;
+  const int max_sweeps = 40, max_iter = 12, cap = 4096;
+  const double tau = 0.05;
+  float2* B;
+  int* cnt;
+  cplx *P, *T, *R, *S, *R2, *S2, *F, *XU, *tmp, *V;
+  double *d, *fro;
+  unsigned long long* maxb;
+  int *np, *gint;
+  int2* pairs;
+  TRY(buf(c, "eo_B", (size_t)k * k, &B));
+  TRY(buf(c, "eo_cnt", max_sweeps, &cnt));
+  TRY(buf(c, "eo_P", (size_t)2 * k * k, &P));
+  TRY(buf(c, "eo_T", (size_t)2 * k * k, &T));
+  TRY(buf(c, "eo_R", (size_t)k * k, &R));
+  TRY(buf(c, "eo_S", (size_t)k * k, &S));
+  TRY(buf(c, "eo_R2", (size_t)k * k, &R2));
+  TRY(buf(c, "eo_S2", (size_t)k * k, &S2));
+  TRY(buf(c, "eo_F", (size_t)k * k, &F));
+  TRY(buf(c, "eo_XU", (size_t)k * k, &XU));
+  TRY(buf(c, "eo_tmp", (size_t)k * k, &tmp));
+  TRY(buf(c, "eo_V", (size_t)k * OA_GROUP_MAX, &V));
+  TRY(buf(c, "eo_d", k, &d));
+  TRY(buf(c, "eo_fro", 1, &fro));
+  TRY(buf(c, "eo_maxb", 2, &maxb));
+  TRY(buf(c, "eo_np", 1, &np));
+  TRY(buf(c, "eo_pairs", cap, &pairs));
+  TRY(buf(c, "eo_gint", (size_t)4 * k + 2, &gint));
+  cplx* X = P;                       // X and G X side by side: T = X^H [X | G X] is one product
+  cplx* GX = P + (size_t)k * k;
+  fro_norm_kernel<<<1, 1024, 0, c->stream>>>(k, G, fro);
+  count_launch();
+  double hfro = 0.0;
+  CU(cudaMemcpyAsync(&hfro, fro, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (!(hfro > 0.0) || !std::isfinite(hfro)) return CHFSI_OK;
+  CU(cudaMemsetAsync(c->d_err_qr, 0, sizeof(int), c->stream));
+  int used = 0;
+  CU(os_jacobi_f32(c->stream, k, G, 2.0 * hfro, B, cnt, max_sweeps, 9.5367431640625e-7f /* 2^-20 */, c->d_err_qr,
+                   c->d_sweeps, &used));
+  CU(os_columns(c->stream, k, B, X));
+  int hsweeps = 0;
+  CU(cudaMemcpyAsync(&hsweeps, c->d_sweeps, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  const double eps = 2.220446049250313e-16;
+  std::vector<int2> hp;
+  Groups gr;
+  c->spans_off = true;   // the products below belong to the eigensolver's span
+  chfsi_status st = CHFSI_OK;
+  bool conv = false;
+  int it = 0;
+  for (; it < max_iter; ++it) {
+    st = gemm64(c, gemm_args(k, k, k, OP_N, G, k, OP_N, X, k, GX, k, ONE, ZERO));
+    if (st != CHFSI_OK) break;
+    st = gemm64(c, gemm_args(k, 2 * k, k, OP_C, X, k, OP_N, P, k, T, k, ONE, ZERO));
+    if (st != CHFSI_OK) break;
+    CU(oa_analyze(c->stream, k, T, tau, d, R, S, maxb, np, cap, pairs));
+    unsigned long long hb[2];
+    int hn = 0, herr = 0;
+    CU(cudaMemcpyAsync(hb, maxb, sizeof(hb), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(&hn, np, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(&herr, c->d_err_qr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    double offmax, rmax;
+    memcpy(&offmax, &hb[0], sizeof(double));   // squared maxima
+    memcpy(&rmax, &hb[1], sizeof(double));
+    offmax = sqrt(offmax);
+    rmax = sqrt(rmax);
+    if (herr != DEV_OK || !std::isfinite(offmax) || !std::isfinite(rmax) || offmax > 1e-2 * hfro) break;
+    if (offmax <= 8.0 * eps * hfro && rmax <= 8.0 * eps) {
+      conv = true;
+      break;
+    }
+    if (hn > cap) break;
+    hp.resize(hn);
+    if (hn > 0) {
+      CU(cudaMemcpyAsync(hp.data(), pairs, sizeof(int2) * hn, cudaMemcpyDeviceToHost, c->stream));
+      CU(cudaStreamSynchronize(c->stream));
+    }
+    make_groups(k, hp, &gr);
+    if (gr.largest > OA_GROUP_MAX) break;
+    const int ngroups = (int)gr.voff.size();
+    cplx* XUp = XU;
+    if (ngroups > 0) {
+      // device copies of the group tables: gid[k], gpos[k], off[ngroups + 1], idx[members], voff[ngroups]
+      std::vector<int> h;
+      h.insert(h.end(), gr.gid.begin(), gr.gid.end());
+      h.insert(h.end(), gr.gpos.begin(), gr.gpos.end());
+      h.insert(h.end(), gr.off.begin(), gr.off.end());
+      h.insert(h.end(), gr.idx.begin(), gr.idx.end());
+      h.insert(h.end(), gr.voff.begin(), gr.voff.end());
+      int* dtab;
+      TRY(buf(c, "eo_gtab", h.size(), &dtab));
+      CU(cudaMemcpyAsync(dtab, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice, c->stream));
+      const int* dgid = dtab;
+      const int* dgpos = dtab + k;
+      const int* doff = dtab + 2 * k;
+      const int* didx = doff + ngroups + 1;
+      const int* dvoff = didx + gr.idx.size();
+      CU(oa_groups(c->stream, k, ngroups, S, doff, didx, dvoff, V, c->d_err_qr));
+      CU(oa_mix(c->stream, k, k, S, S2, true, tmp, dgid, dgpos, doff, didx, dvoff, V));
+      CU(oa_mix(c->stream, k, k, R, R2, true, tmp, dgid, dgpos, doff, didx, dvoff, V));
+      CU(oa_mix(c->stream, k, k, X, XU, false, tmp, dgid, dgpos, doff, didx, dvoff, V));
+      CU(oa_update(c->stream, k, S2, R2, dgid, F));
+    } else {
+      CU(cudaMemsetAsync(gint, 0xFF, sizeof(int) * k, c->stream));   // gid = -1 everywhere
+      CU(oa_update(c->stream, k, S, R, gint, F));
+      CU(cudaMemcpyAsync(XU, X, sizeof(cplx) * (size_t)k * k, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    // X <- X U (I + F) = XU + XU F
+    CU(cudaMemcpyAsync(X, XUp, sizeof(cplx) * (size_t)k * k, cudaMemcpyDeviceToDevice, c->stream));
+    st = gemm64(c, gemm_args(k, k, k, OP_N, XUp, k, OP_N, F, k, X, k, ONE, ONE));
+    if (st != CHFSI_OK) break;
+  }
+  c->spans_off = false;
+  c->acc_eig_f32_sweeps += hsweeps;
+  c->acc_eig_iters += it + (conv ? 1 : 0);
+  if (st != CHFSI_OK) return st;
+  if (!conv) {
+    ++c->acc_eig_fallbacks;
+    return CHFSI_OK;
+  }
+  ++c->acc_eig_refined;
+  CU(oa_sort(c->stream, k, d, X, lam, W));
+  *done = true;
+  return CHFSI_OK;
+}
+
 // The device error word is not reset here: inside a solve it is zero at this point unless an
 // earlier kernel (a bounded wait in a GEMM) failed, and that failure must reach the solve's
 // check rather than be erased; the stage entry points reset it on entry.
 chfsi_status reduced_eig(chfsi_ctx* c, int k, cplx* G, double* lam, cplx* W) {
+  const bool refine = c->prm.precision == CHFSI_PREC_MIXED && k >= 32 && c->eig_path != 0;
+  span_begin(c, 1, 0.0);
+  if (refine) {
+    bool done = false;
+    TRY(reduced_eig_refined(c, k, G, lam, W, &done));
+    if (done) {
+      span_end(c);
+      return CHFSI_OK;
+    }
+  }
   char* work;
   TRY(buf(c, "jac_work", jacobi_work_bytes(k), &work));
-  span_begin(c, 1, 0.0);
   CU(jacobi_eig(c->stream, k, G, lam, W, work, c->d_err, c->d_sweeps, c->d_rounds));
   span_end(c);
   if (c->n_sweeps_pending < 64) {
@@ -815,209 +1053,260 @@ chfsi_status inertia_check(chfsi_ctx* c, int n, const cplx* Hs, const cplx* Yl, 
   return CHFSI_OK;
 }
 
-struct Timer {
-  chfsi_ctx* c;
-  double* acc;
-  int idx = 0;
-  int stage[16];
-  void start() { idx = 0; }
-  void mark(int s) {
-    if (idx < 10) {   // events 0..9; 11..15 are used by solve_common
-      cudaEventRecord(c->ev[idx], c->stream);
-      stage[idx] = s;
-      ++idx;
-    }
-  }
-  // after a sync: add elapsed time between consecutive marks to the stage of the later mark
-  void flush() {
-    for (int i = 1; i < idx; ++i) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, c->ev[i - 1], c->ev[i]) == cudaSuccess) acc[stage[i]] += ms;
-    }
-    idx = 0;
-  }
-};
 
-// The iteration of Algorithm 1 on the stored standard-form problem.  Y (n x k) holds the
-// start block; on return Y holds the whole block sorted by Ritz value.
-chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, double a0, double* evals, cplx* Xout,
-                     const cplx* Linv, chfsi_info* info, bool seeded) {
-  const int n = c->n, nev = c->nev, k = nev + c->nex;
-  const double tol_lock = c->tol / c->kappa_L;
-  cplx *Z, *Y2;
-  double *lam, *res, *resabs;
-  int* perm;
-  double* lam_tmp;
-  TRY(buf(c, "it_Z", (size_t)n * k, &Z));
-  TRY(buf(c, "it_Y2", (size_t)n * k, &Y2));
-  TRY(buf(c, "it_lam", k, &lam));
-  TRY(buf(c, "it_lam_tmp", k, &lam_tmp));
-  TRY(buf(c, "it_res", k, &res));
-  TRY(buf(c, "it_resabs", k, &resabs));
-  TRY(buf(c, "it_perm", k, &perm));
-  TRY(ensure_host(c, k));
-  double* h_lam = c->h_d;
-  double* h_res = c->h_d + k;
-  double* h_lam2 = c->h_d + 2 * k;
-  int* h_perm = c->h_i;
-  int* h_deg = c->h_i + k;
-
-  std::vector<double> lam_locked;
-  std::vector<int> deg(k, c->degree);
-  int nl = 0, ka = k, it = 0;
+// The iteration of Algorithm 1 on the stored standard-form problem, as a resumable state so
+// that a batch of problems can be advanced stage by stage (the filters of all problems as one
+// grouped launch per recurrence step).  Y (n x k) holds the start block; on return Y holds
+// the whole block sorted by Ritz value.
+struct IterState {
+  // inputs
+  const cplx* Hs = nullptr;
+  cplx* Y = nullptr;
+  double a = 0, b = 0, a0 = 0;
+  double* evals = nullptr;
+  cplx* Xout = nullptr;
+  const cplx* Linv = nullptr;
+  chfsi_info* info = nullptr;
+  bool seeded = false;
+  // workspaces
+  cplx *Z = nullptr, *Y2 = nullptr;
+  double *lam = nullptr, *res = nullptr, *resabs = nullptr, *lam_tmp = nullptr;
+  int* perm = nullptr;
+  // loop state
+  int n = 0, nev = 0, k = 0, nl = 0, ka = 0, it = 0;
+  double tol_lock = 0, hnorm = 0;
+  std::vector<double> lam_locked, lam_active;
+  std::vector<int> deg;
   double ms[9] = {0};   // index 8: low-precision filter passes
-  Timer tm{c, ms};
+  int tm_idx = 0, tm_stage[16] = {};
   chfsi_status status = CHFSI_OK;
   long long colsteps = 0, colsteps_lowp = 0;
-  double min_res = INFINITY, max_res_locked = 0.0;
-  double min_res_abs = INFINITY, prev_min_res_abs = INFINITY;
+  double min_res = INFINITY, max_res_locked = 0.0, min_res_abs = INFINITY, prev_min_res_abs = INFINITY;
   bool last_lowp = false;
-  const double hnorm = std::max(fabs(a0), fabs(b));
-  double* h_resabs = c->h_d + 3 * k;
-  std::vector<double> lam_active;
   bool have_ritz = false;   // Z, lam (columns nl..k) hold H' Ya and the Ritz values of Ya
-  if (seeded && c->prm.precision == CHFSI_PREC_MIXED) {
+  // this iteration's filter
+  int prec = CHFSI_PREC_FP64;
+  FilterPlan plan;
+  RitzData rd{};
+  bool done = false;
+};
+
+// stage timer on the context's events 0..9: the time between consecutive marks goes to the
+// stage of the later mark
+void tm_start(chfsi_ctx* c, IterState& s) { s.tm_idx = 0; }
+void tm_mark(chfsi_ctx* c, IterState& s, int stage) {
+  if (s.tm_idx < 10) {
+    cudaEventRecord(c->ev[s.tm_idx], c->stream);
+    s.tm_stage[s.tm_idx] = stage;
+    ++s.tm_idx;
+  }
+}
+void tm_flush(chfsi_ctx* c, IterState& s) {   // after a synchronisation
+  for (int i = 1; i < s.tm_idx; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[i - 1], c->ev[i]) == cudaSuccess) s.ms[s.tm_stage[i]] += ms;
+  }
+  s.tm_idx = 0;
+}
+
+chfsi_status iter_begin(chfsi_ctx* c, IterState& s) {
+  const int n = c->n, nev = c->nev, k = nev + c->nex;
+  s.n = n;
+  s.nev = nev;
+  s.k = k;
+  s.nl = 0;
+  s.ka = k;
+  s.it = 0;
+  s.tol_lock = c->tol / c->kappa_L;
+  s.hnorm = std::max(fabs(s.a0), fabs(s.b));
+  s.deg.assign(k, c->degree);
+  TRY(buf(c, "it_Z", (size_t)n * k, &s.Z));
+  TRY(buf(c, "it_Y2", (size_t)n * k, &s.Y2));
+  TRY(buf(c, "it_lam", k, &s.lam));
+  TRY(buf(c, "it_lam_tmp", k, &s.lam_tmp));
+  TRY(buf(c, "it_res", k, &s.res));
+  TRY(buf(c, "it_resabs", k, &s.resabs));
+  TRY(buf(c, "it_perm", k, &s.perm));
+  TRY(ensure_host(c, k));
+  if (s.seeded && c->prm.precision == CHFSI_PREC_MIXED) {
     // the seed block (the previous problem's Ritz vectors) with its Rayleigh quotients for the
     // new H': Z = H' Y, lam_i = y_i^H z_i.  The corrected recurrence is exact for any diagonal
     // lam; with these the forcing R = Z - Y diag(lam) is as small as the change of H'.
-    TRY(gemm64(c, gemm_args(n, k, n, OP_N, Hs, n, OP_N, Y, n, Z, n, ONE, ZERO)));
-    CU(rayleigh_quotients(c->stream, n, k, Y, n, Z, n, lam));
-    CU(cudaMemcpyAsync(h_lam, lam, sizeof(double) * k, cudaMemcpyDeviceToHost, c->stream));
+    double* h_lam = c->h_d;
+    TRY(gemm64(c, gemm_args(n, k, n, OP_N, s.Hs, n, OP_N, s.Y, n, s.Z, n, ONE, ZERO)));
+    CU(rayleigh_quotients(c->stream, n, k, s.Y, n, s.Z, n, s.lam));
+    CU(cudaMemcpyAsync(h_lam, s.lam, sizeof(double) * k, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
-    lam_active.assign(h_lam, h_lam + k);
-    have_ritz = true;
+    s.lam_active.assign(h_lam, h_lam + k);
+    s.have_ritz = true;
   }
-  for (;;) {
-    ++it;
-    cplx* Ya = Y + (size_t)nl * n;
-    cplx* Za = Z + (size_t)nl * n;
-    double* lama = lam + nl;
-    tm.start();
-    tm.mark(0);
-    // line 3: filter (mixed precision while every active residual is above the switch)
-    // precision ladder: the tensor-core filter while the smallest active absolute residual is
-    // above mixed_switch * ||H'|| and the previous low-precision pass still made progress
-    // (an FP32-equivalent filter stalls near 2^-24 ||H'||)
-    int prec = CHFSI_PREC_FP64;
-    if (c->prm.precision == CHFSI_PREC_MIXED) {
-      const bool stalled = last_lowp && min_res_abs > 0.1 * prev_min_res_abs;
-      if (have_ritz) prec = stalled ? CHFSI_PREC_FP64 : CHFSI_PREC_MIXED;   // corrected recurrence: no floor
-      else if (min_res_abs > c->prm.mixed_switch * hnorm && !stalled) prec = CHFSI_PREC_MIXED;
-    }
-    last_lowp = prec == CHFSI_PREC_MIXED;
-    prev_min_res_abs = min_res_abs;
-    long long cs = 0;
-    {
-      RitzData rd{Za, lama, lam_active.data()};
-      const bool use_ritz = prec == CHFSI_PREC_MIXED && have_ritz && (int)lam_active.size() == ka;
-      TRY(run_filter(c, n, ka, Hs, Ya, deg.data(), a, b, a0, prec, &cs, use_ritz ? &rd : nullptr));
-    }
-    colsteps += cs;
-    if (prec == CHFSI_PREC_MIXED) colsteps_lowp += cs;
-    tm.mark(prec == CHFSI_PREC_MIXED ? 8 : 2);
-    // line 4: QR against the locked vectors
-    TRY(orthonormalize(c, n, nl, Y, ka, Ya, false));
-    tm.mark(3);
-    // lines 5-7: Rayleigh-Ritz
-    TRY(rayleigh_ritz(c, n, ka, Hs, Ya, lama, Za));
-    have_ritz = true;
-    tm.mark(4);
-    // residuals
-    // Res(y, lam) = ||H'y - lam y|| / max(||H'y||, 1e-4 ||H'||): for eigenvalues closer to 0
-    // than 1e-4 ||H'|| a relative residual of 1e-10 lies below FP64's reach, so the test
-    // becomes absolute there
-    CU(residual_norms(c->stream, n, ka, Za, n, Ya, n, lama, res, resabs, 1e-4 * hnorm));
-    CU(cudaMemcpyAsync(h_lam, lama, sizeof(double) * ka, cudaMemcpyDeviceToHost, c->stream));
-    CU(cudaMemcpyAsync(h_res, res, sizeof(double) * ka, cudaMemcpyDeviceToHost, c->stream));
-    CU(cudaMemcpyAsync(h_resabs, resabs, sizeof(double) * ka, cudaMemcpyDeviceToHost, c->stream));
-    int h_err = 0;
-    CU(cudaMemcpyAsync(&h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    tm.mark(5);
+  return CHFSI_OK;
+}
+
+// line 3 of the next iteration, planned: the precision and the host side of the filter
+chfsi_status iter_plan_filter(chfsi_ctx* c, IterState& s) {
+  ++s.it;
+  tm_start(c, s);
+  tm_mark(c, s, 0);
+  // precision ladder: the tensor-core filter while the smallest active absolute residual is
+  // above mixed_switch * ||H'|| and the previous low-precision pass still made progress
+  // (an FP32-equivalent filter stalls near 2^-24 ||H'||); with Ritz data the corrected
+  // recurrence has no such floor
+  int prec = CHFSI_PREC_FP64;
+  if (c->prm.precision == CHFSI_PREC_MIXED) {
+    const bool stalled = s.last_lowp && s.min_res_abs > 0.1 * s.prev_min_res_abs;
+    if (s.have_ritz) prec = stalled ? CHFSI_PREC_FP64 : CHFSI_PREC_MIXED;
+    else if (s.min_res_abs > c->prm.mixed_switch * s.hnorm && !stalled) prec = CHFSI_PREC_MIXED;
+  }
+  s.prec = prec;
+  s.last_lowp = prec == CHFSI_PREC_MIXED;
+  s.prev_min_res_abs = s.min_res_abs;
+  cplx* Ya = s.Y + (size_t)s.nl * s.n;
+  s.rd = RitzData{s.Z + (size_t)s.nl * s.n, s.lam + s.nl, s.lam_active.data()};
+  const bool use_ritz = prec == CHFSI_PREC_MIXED && s.have_ritz && (int)s.lam_active.size() == s.ka;
+  TRY(filter_plan(s.n, s.ka, s.Hs, Ya, s.deg.data(), s.a, s.b, s.a0, use_ritz ? &s.rd : nullptr, &s.plan));
+  return CHFSI_OK;
+}
+
+// the planned filter of one problem on its own
+chfsi_status iter_run_filter(chfsi_ctx* c, IterState& s) {
+  long long cs = 0;
+  const bool use_ritz = s.plan.ritz;
+  TRY(run_filter(c, s.n, s.ka, s.Hs, s.Y + (size_t)s.nl * s.n, s.deg.data(), s.a, s.b, s.a0, s.prec, &cs,
+                 use_ritz ? &s.rd : nullptr));
+  return CHFSI_OK;
+}
+
+// lines 4-13 after the filter: QR, Rayleigh-Ritz, residuals, deflation and locking
+chfsi_status iter_after_filter(chfsi_ctx* c, IterState& s) {
+  const int n = s.n, nev = s.nev;
+  int nl = s.nl, ka = s.ka;
+  double* h_lam = c->h_d;
+  double* h_res = c->h_d + s.k;
+  double* h_resabs = c->h_d + 3 * s.k;
+  int* h_perm = c->h_i;
+  int* h_deg = c->h_i + s.k;
+  cplx* Ya = s.Y + (size_t)nl * n;
+  cplx* Za = s.Z + (size_t)nl * n;
+  double* lama = s.lam + nl;
+  s.colsteps += s.plan.steps;
+  if (s.prec == CHFSI_PREC_MIXED) s.colsteps_lowp += s.plan.steps;
+  tm_mark(c, s, s.prec == CHFSI_PREC_MIXED ? 8 : 2);
+  // line 4: QR against the locked vectors
+  TRY(orthonormalize(c, n, nl, s.Y, ka, Ya, false));
+  tm_mark(c, s, 3);
+  // lines 5-7: Rayleigh-Ritz
+  TRY(rayleigh_ritz(c, n, ka, s.Hs, Ya, lama, Za));
+  s.have_ritz = true;
+  tm_mark(c, s, 4);
+  // residuals
+  // Res(y, lam) = ||H'y - lam y|| / max(||H'y||, 1e-4 ||H'||): for eigenvalues closer to 0
+  // than 1e-4 ||H'|| a relative residual of 1e-10 lies below FP64's reach, so the test
+  // becomes absolute there
+  CU(residual_norms(c->stream, n, ka, Za, n, Ya, n, lama, s.res, s.resabs, 1e-4 * s.hnorm));
+  CU(cudaMemcpyAsync(h_lam, lama, sizeof(double) * ka, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(h_res, s.res, sizeof(double) * ka, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(h_resabs, s.resabs, sizeof(double) * ka, cudaMemcpyDeviceToHost, c->stream));
+  int h_err = 0;
+  CU(cudaMemcpyAsync(&h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  tm_mark(c, s, 5);
+  CU(cudaStreamSynchronize(c->stream));
+  tm_flush(c, s);
+  spans_flush(c);
+  sweeps_flush(c);
+  if (h_err != DEV_OK) return map_dev_err(h_err);
+  for (int i = 0; i < ka; ++i)
+    if (!std::isfinite(h_res[i]) || !std::isfinite(h_lam[i])) return CHFSI_ERR_NUMERIC;
+  // lines 8-12: deflation and locking, i = converged .. nev
+  std::vector<int> lockv, rest;
+  for (int i = 0; i < ka; ++i) {
+    if (i < nev - nl && h_res[i] < s.tol_lock) lockv.push_back(i);
+    else rest.push_back(i);
+  }
+  // bounds of the next filter: a = largest Ritz value of the block, a0 = smallest seen
+  s.a = h_lam[ka - 1];
+  s.a0 = std::min(s.a0, h_lam[0]);
+  s.min_res = INFINITY;
+  s.min_res_abs = INFINITY;
+  for (int i : rest) {
+    s.min_res = std::min(s.min_res, h_res[i]);
+    s.min_res_abs = std::min(s.min_res_abs, h_resabs[i]);
+  }
+  for (int i : lockv) s.max_res_locked = std::max(s.max_res_locked, h_res[i]);
+  if (c->prm.per_vector_degree && !rest.empty()) {
+    // a10: degrees for the next filter, from the updated bounds (device kernel)
+    CU(vector_degrees(c->stream, ka, s.lam, s.res, s.a, s.b, s.tol_lock, c->prm.degree_min, c->prm.degree_max,
+                      s.perm));
+    CU(cudaMemcpyAsync(h_deg, s.perm, sizeof(int) * ka, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
-    tm.flush();
-    spans_flush(c);
-    sweeps_flush(c);
-    if (h_err != DEV_OK) return map_dev_err(h_err);
-    for (int i = 0; i < ka; ++i)
-      if (!isfinite(h_res[i]) || !isfinite(h_lam[i])) return CHFSI_ERR_NUMERIC;
-    // lines 8-12: deflation and locking, i = converged .. nev
-    std::vector<int> lockv, rest;
-    for (int i = 0; i < ka; ++i) {
-      if (i < nev - nl && h_res[i] < tol_lock) lockv.push_back(i);
-      else rest.push_back(i);
-    }
-    // bounds of the next filter: a = largest Ritz value of the block, a0 = smallest seen
-    a = h_lam[ka - 1];
-    a0 = std::min(a0, h_lam[0]);
-    min_res = INFINITY;
-    min_res_abs = INFINITY;
-    for (int i : rest) {
-      min_res = std::min(min_res, h_res[i]);
-      min_res_abs = std::min(min_res_abs, h_resabs[i]);
-    }
-    for (int i : lockv) max_res_locked = std::max(max_res_locked, h_res[i]);
-    if (c->prm.per_vector_degree && !rest.empty()) {
-      // a10: degrees for the next filter, from the updated bounds (device kernel)
-      CU(vector_degrees(c->stream, ka, lam, res, a, b, tol_lock, c->prm.degree_min, c->prm.degree_max, perm));
-      CU(cudaMemcpyAsync(h_deg, perm, sizeof(int) * ka, cudaMemcpyDeviceToHost, c->stream));
-      CU(cudaStreamSynchronize(c->stream));
-    }
-    // new order of the active block: locked first, then the rest (by degree when per-vector)
-    std::vector<int> order;
-    order.insert(order.end(), lockv.begin(), lockv.end());
-    std::vector<int> rest_sorted = rest;
-    if (c->prm.per_vector_degree)
-      std::stable_sort(rest_sorted.begin(), rest_sorted.end(), [&](int x, int y) { return h_deg[x] > h_deg[y]; });
-    order.insert(order.end(), rest_sorted.begin(), rest_sorted.end());
-    for (int i : lockv) lam_locked.push_back(h_lam[i]);
-    lam_active.clear();
-    for (int i : rest_sorted) lam_active.push_back(h_lam[i]);
-    for (size_t q = 0; q < rest_sorted.size(); ++q)
-      deg[q] = c->prm.per_vector_degree ? h_deg[rest_sorted[q]] : c->degree;
-    bool identity = true;
-    for (int i = 0; i < ka; ++i) {
-      h_perm[i] = order[i];
-      identity = identity && order[i] == i;
-    }
-    if (!identity) {
-      CU(cudaMemcpyAsync(perm, h_perm, sizeof(int) * ka, cudaMemcpyHostToDevice, c->stream));
-      CU(gather_columns(c->stream, n, ka, perm, Ya, n, Y2, n));
-      CU(copy_block(c->stream, n, ka, Y2, n, Ya, n));
-      CU(gather_columns(c->stream, n, ka, perm, Za, n, Y2, n));
-      CU(copy_block(c->stream, n, ka, Y2, n, Za, n));
-      CU(gather_values(c->stream, ka, perm, lama, lam_tmp));
-      CU(cudaMemcpyAsync(lama, lam_tmp, sizeof(double) * ka, cudaMemcpyDeviceToDevice, c->stream));
-    }
-    nl += (int)lockv.size();
-    ka -= (int)lockv.size();
-    if (nl >= nev || it >= c->prm.max_iter || ka == 0) break;
   }
+  // new order of the active block: locked first, then the rest (by degree when per-vector)
+  std::vector<int> order;
+  order.insert(order.end(), lockv.begin(), lockv.end());
+  std::vector<int> rest_sorted = rest;
+  if (c->prm.per_vector_degree)
+    std::stable_sort(rest_sorted.begin(), rest_sorted.end(), [&](int x, int y) { return h_deg[x] > h_deg[y]; });
+  order.insert(order.end(), rest_sorted.begin(), rest_sorted.end());
+  for (int i : lockv) s.lam_locked.push_back(h_lam[i]);
+  s.lam_active.clear();
+  for (int i : rest_sorted) s.lam_active.push_back(h_lam[i]);
+  for (size_t q = 0; q < rest_sorted.size(); ++q)
+    s.deg[q] = c->prm.per_vector_degree ? h_deg[rest_sorted[q]] : c->degree;
+  bool identity = true;
+  for (int i = 0; i < ka; ++i) {
+    h_perm[i] = order[i];
+    identity = identity && order[i] == i;
+  }
+  if (!identity) {
+    CU(cudaMemcpyAsync(s.perm, h_perm, sizeof(int) * ka, cudaMemcpyHostToDevice, c->stream));
+    CU(gather_columns(c->stream, n, ka, s.perm, Ya, n, s.Y2, n));
+    CU(copy_block(c->stream, n, ka, s.Y2, n, Ya, n));
+    CU(gather_columns(c->stream, n, ka, s.perm, Za, n, s.Y2, n));
+    CU(copy_block(c->stream, n, ka, s.Y2, n, Za, n));
+    CU(gather_values(c->stream, ka, s.perm, lama, s.lam_tmp));
+    CU(cudaMemcpyAsync(lama, s.lam_tmp, sizeof(double) * ka, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  nl += (int)lockv.size();
+  ka -= (int)lockv.size();
+  s.nl = nl;
+  s.ka = ka;
+  s.done = nl >= nev || s.it >= c->prm.max_iter || ka == 0;
+  return CHFSI_OK;
+}
+
+// after the last iteration: completeness, outputs, the sequence state and info
+chfsi_status iter_finish(chfsi_ctx* c, IterState& s) {
+  const int n = s.n, nev = s.nev, k = s.k, nl = s.nl;
+  double* h_lam2 = c->h_d + 2 * k;
+  int* h_perm = c->h_i;
+  chfsi_status status = CHFSI_OK;
   if (nl < nev) status = CHFSI_ERR_NO_CONV;
   // pairs whose lock test was absolute (|lam| below the residual floor)
   int n_floor = 0;
-  for (double l : lam_locked)
-    if (fabs(l) < 1e-4 * hnorm) ++n_floor;
+  for (double l : s.lam_locked)
+    if (fabs(l) < 1e-4 * s.hnorm) ++n_floor;
   // completeness: no Ritz value of the block outside the returned set may lie below the
   // largest returned eigenvalue (a lower unreturned one means a wanted eigenvalue was passed
   // over); optionally the exact count below the gap (inertia)
   int completeness = 0;
   if (status == CHFSI_OK && nl > 0) {
-    const double lmax = *std::max_element(lam_locked.begin(), lam_locked.end());
-    const double lmin = *std::min_element(lam_locked.begin(), lam_locked.end());
-    double lnext = a;   // largest Ritz value of the last block (the filter's lower end)
-    for (double l : lam_active) lnext = std::min(lnext, l);
-    if (lmax > lnext + 1e-8 * hnorm) {
+    const double lmax = *std::max_element(s.lam_locked.begin(), s.lam_locked.end());
+    const double lmin = *std::min_element(s.lam_locked.begin(), s.lam_locked.end());
+    double lnext = s.a;   // largest Ritz value of the last block (the filter's lower end)
+    for (double l : s.lam_active) lnext = std::min(lnext, l);
+    if (lmax > lnext + 1e-8 * s.hnorm) {
       status = CHFSI_ERR_INCOMPLETE;
     } else {
       completeness = 1;
-      if (c->prm.check_inertia) TRY(inertia_check(c, n, Hs, Y, nl, lmin, lmax, lnext, hnorm, &completeness, &status));
+      if (c->prm.check_inertia)
+        TRY(inertia_check(c, n, s.Hs, s.Y, nl, lmin, lmax, lnext, s.hnorm, &completeness, &status));
     }
   }
-  tm.start();
-  tm.mark(0);
+  tm_start(c, s);
+  tm_mark(c, s, 0);
   // outputs: locked pairs by ascending eigenvalue (then the lowest active ones on NO_CONV)
-  std::vector<double> all_lam(lam_locked);
-  all_lam.insert(all_lam.end(), lam_active.begin(), lam_active.end());
+  std::vector<double> all_lam(s.lam_locked);
+  all_lam.insert(all_lam.end(), s.lam_active.begin(), s.lam_active.end());
   std::vector<int> idx(k);
   std::iota(idx.begin(), idx.begin() + nl, 0);
   std::stable_sort(idx.begin(), idx.begin() + nl, [&](int x, int y) { return all_lam[x] < all_lam[y]; });
@@ -1027,12 +1316,12 @@ chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, 
     h_perm[i] = idx[i];
     h_lam2[i] = all_lam[idx[i]];
   }
-  CU(cudaMemcpyAsync(perm, h_perm, sizeof(int) * nev, cudaMemcpyHostToDevice, c->stream));
-  CU(gather_columns(c->stream, n, nev, perm, Y, n, Y2, n));
-  CU(cudaMemcpyAsync(evals, h_lam2, sizeof(double) * nev, cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(s.perm, h_perm, sizeof(int) * nev, cudaMemcpyHostToDevice, c->stream));
+  CU(gather_columns(c->stream, n, nev, s.perm, s.Y, n, s.Y2, n));
+  CU(cudaMemcpyAsync(s.evals, h_lam2, sizeof(double) * nev, cudaMemcpyHostToDevice, c->stream));
   // a11: X = L^{-H} Y
-  TRY(gemm64(c, gemm_args(n, nev, n, OP_C, Linv, n, OP_N, Y2, n, (cplx*)Xout, n, ONE, ZERO, TRI_A_UPPER)));
-  tm.mark(6);
+  TRY(gemm64(c, gemm_args(n, nev, n, OP_C, s.Linv, n, OP_N, s.Y2, n, s.Xout, n, ONE, ZERO, TRI_A_UPPER)));
+  tm_mark(c, s, 6);
   // sequence state: the whole block sorted by Ritz value
   std::vector<int> all(k);
   std::iota(all.begin(), all.end(), 0);
@@ -1042,31 +1331,33 @@ chfsi_status iterate(chfsi_ctx* c, const cplx* Hs, cplx* Y, double a, double b, 
     h_perm[i] = all[i];
     c->block_lam[i] = all_lam[all[i]];
   }
-  CU(cudaMemcpyAsync(perm, h_perm, sizeof(int) * k, cudaMemcpyHostToDevice, c->stream));
-  CU(gather_columns(c->stream, n, k, perm, Y, n, Y2, n));
-  CU(copy_block(c->stream, n, k, Y2, n, Y, n));
+  CU(cudaMemcpyAsync(s.perm, h_perm, sizeof(int) * k, cudaMemcpyHostToDevice, c->stream));
+  CU(gather_columns(c->stream, n, k, s.perm, s.Y, n, s.Y2, n));
+  CU(copy_block(c->stream, n, k, s.Y2, n, s.Y, n));
   int e_end = 0;
   TRY(read_err(c, &e_end));   // failures of the products after the last iteration's check
-  tm.flush();
+  tm_flush(c, s);
   if (e_end != DEV_OK) status = map_dev_err(e_end);
-  if (info) {
-    info->iterations = it;
+  if (chfsi_info* info = s.info) {
+    info->iterations = s.it;
     info->locked = nl;
-    info->filter_col_steps = colsteps;
-    info->filter_col_steps_lowp = colsteps_lowp;
-    info->max_resid = max_res_locked;
+    info->filter_col_steps = s.colsteps;
+    info->filter_col_steps_lowp = s.colsteps_lowp;
+    info->max_resid = s.max_res_locked;
     info->kappa_L = c->kappa_L;
-    info->bounds[0] = a;
-    info->bounds[1] = b;
-    info->bounds[2] = a0;
-    for (int s = 0; s < 7; ++s) info->ms_stage[s] += ms[s];
-    info->ms_stage[2] += ms[8];
-    info->ms_filter_lowp += ms[8];
+    info->bounds[0] = s.a;
+    info->bounds[1] = s.b;
+    info->bounds[2] = s.a0;
+    for (int q = 0; q < 7; ++q) info->ms_stage[q] += s.ms[q];
+    info->ms_stage[2] += s.ms[8];
+    info->ms_filter_lowp += s.ms[8];
     info->n_floor = n_floor;
     info->completeness = completeness;
   }
+  s.status = status;
   return status;
 }
+
 
 bool valid_ptrs(std::initializer_list<const void*> ps) {
   for (auto p : ps)
@@ -1079,8 +1370,10 @@ chfsi_status setup_device(chfsi_ctx* c) {
   return CHFSI_OK;
 }
 
-chfsi_status solve_common(chfsi_ctx* c, const cplx* H, const cplx* S, const cplx* X0, bool seeded, double* evals,
-                          void* X, chfsi_info* info) {
+// Everything of a solve before the iteration (Section 3's reduction to standard form, the
+// start block and Algorithm 1 line 1), leaving the iteration state ready to begin.
+chfsi_status solve_prefix(chfsi_ctx* c, const cplx* H, const cplx* S, const cplx* X0, bool seeded, double* evals,
+                          void* X, chfsi_info* info, IterState* is) {
   const int n = c->n, k = c->nev + c->nex;
   cudaEvent_t t0 = c->ev[14], t1 = c->ev[15];
   CU(cudaEventRecord(t0, c->stream));
@@ -1104,6 +1397,8 @@ chfsi_status solve_common(chfsi_ctx* c, const cplx* H, const cplx* S, const cplx
   c->acc_sweeps = 0;
   c->acc_rounds = 0;
   c->acc_eig_flop = 0.0;
+  c->acc_eig_refined = c->acc_eig_iters = c->acc_eig_f32_sweeps = c->acc_eig_fallbacks = 0;
+  c->spans_off = false;
   c->gemm_calls = 0;
   const char* inject = getenv("CHFSI_INJECT_GEMM_TIMEOUT");
   c->fault_gemm = inject ? atoi(inject) : 0;
@@ -1154,7 +1449,27 @@ chfsi_status solve_common(chfsi_ctx* c, const cplx* H, const cplx* S, const cplx
   CU(cudaEventRecord(l1, c->stream));
   CU(cudaEventSynchronize(l1));
   cudaEventElapsedTime(&ms_lanczos, r1, l1);
-  chfsi_status st = iterate(c, Hs, Y, a, b, a0, evals, (cplx*)X, Linv, info, seeded);
+  if (info) {
+    info->ms_stage[0] += ms_reduce;
+    info->ms_stage[1] += ms_lanczos;
+  }
+  *is = IterState();
+  is->Hs = Hs;
+  is->Y = Y;
+  is->a = a;
+  is->b = b;
+  is->a0 = a0;
+  is->evals = evals;
+  is->Xout = (cplx*)X;
+  is->Linv = Linv;
+  is->info = info;
+  is->seeded = seeded;
+  return iter_begin(c, *is);
+}
+
+// Everything after the iteration: device-time accounting, the sequence state.
+chfsi_status solve_suffix(chfsi_ctx* c, chfsi_info* info, chfsi_status st) {
+  cudaEvent_t t0 = c->ev[14], t1 = c->ev[15];
   CU(cudaEventRecord(t1, c->stream));
   CU(cudaEventSynchronize(t1));
   spans_flush(c);
@@ -1162,8 +1477,6 @@ chfsi_status solve_common(chfsi_ctx* c, const cplx* H, const cplx* S, const cplx
   if (info) {
     float tot = 0.f;
     cudaEventElapsedTime(&tot, t0, t1);
-    info->ms_stage[0] += ms_reduce;
-    info->ms_stage[1] += ms_lanczos;
     info->ms_stage[7] = tot;
     info->ms_gemm_tc = c->acc_ms[0];
     info->gemm_tc_flop = c->acc_flop;
@@ -1171,6 +1484,10 @@ chfsi_status solve_common(chfsi_ctx* c, const cplx* H, const cplx* S, const cplx
     info->eig_sweeps = c->acc_sweeps;
     info->eig_rounds = c->acc_rounds;
     info->eig_flop = c->acc_eig_flop;
+    info->eig_refined = c->acc_eig_refined;
+    info->eig_refine_iters = c->acc_eig_iters;
+    info->eig_f32_sweeps = c->acc_eig_f32_sweeps;
+    info->eig_fallbacks = c->acc_eig_fallbacks;
     info->ms_chol = c->acc_ms[2];
     info->chol_flop = c->acc_chol_flop;
     long long cols = 0;
@@ -1179,6 +1496,21 @@ chfsi_status solve_common(chfsi_ctx* c, const cplx* H, const cplx* S, const cplx
   }
   if (st == CHFSI_OK || st == CHFSI_ERR_NO_CONV || st == CHFSI_ERR_INCOMPLETE) c->have_seq = true;
   return st;
+}
+
+chfsi_status solve_common(chfsi_ctx* c, const cplx* H, const cplx* S, const cplx* X0, bool seeded, double* evals,
+                          void* X, chfsi_info* info) {
+  IterState s;
+  TRY(solve_prefix(c, H, S, X0, seeded, evals, X, info, &s));
+  chfsi_status st = CHFSI_OK;
+  for (;;) {
+    st = iter_plan_filter(c, s);
+    if (st == CHFSI_OK) st = iter_run_filter(c, s);
+    if (st == CHFSI_OK) st = iter_after_filter(c, s);
+    if (st != CHFSI_OK || s.done) break;
+  }
+  if (st == CHFSI_OK) st = iter_finish(c, s);
+  return solve_suffix(c, info, st);
 }
 
 }  // namespace
@@ -1336,6 +1668,9 @@ void chfsi_destroy(chfsi_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
+  for (chfsi_ctx* kid : c->kids) chfsi_destroy(kid);
+  c->kids.clear();
+  if (c->tcb) tc_batch_free(c->tcb);
   c->arena.release();
   if (c->tc) tc_filter_free(c->tc);
   if (c->oz) ozaki_free(c->oz);
@@ -1374,6 +1709,100 @@ chfsi_status chfsi_next_in_sequence(chfsi_ctx* c, const void* H_next, const void
   if (!c->have_seq) return CHFSI_ERR_STATE;
   TRY(setup_device(c));
   return solve_common(c, (const cplx*)H_next, (const cplx*)S_next, nullptr, true, evals, X, info);
+}
+
+chfsi_status chfsi_solve_batch(chfsi_ctx* c, int count, const void* const* H, const void* const* S, const int* n,
+                               const int* nev, const int* nex, double tol, int degree, double* const* evals,
+                               void* const* X, chfsi_status* status, chfsi_info* info) {
+  if (!c || count < 1 || !H || !S || !n || !nev || !nex || !evals || !X || !status || !(tol > 0.0))
+    return CHFSI_ERR_ARG;
+  for (int p = 0; p < count; ++p)
+    if (!H[p] || !S[p] || !evals[p] || !X[p] || n[p] < 2 || nev[p] < 1 || nex[p] < 0 || nev[p] + nex[p] > n[p])
+      return CHFSI_ERR_ARG;
+  TRY(setup_device(c));
+  while ((int)c->kids.size() < count) {
+    chfsi_ctx* kid = nullptr;
+    TRY(chfsi_create(&kid, c->device, c->stream, &c->prm));
+    c->kids.push_back(kid);
+  }
+  if (!c->tcb) c->tcb = tc_batch_new();
+  std::vector<IterState> st(count);
+  std::vector<char> active(count, 0);
+  // reduction to standard form, start block and Lanczos bounds, problem after problem
+  for (int p = 0; p < count; ++p) {
+    chfsi_ctx* kid = c->kids[p];
+    kid->n = n[p];
+    kid->nev = nev[p];
+    kid->nex = nex[p];
+    kid->tol = tol;
+    kid->degree = degree > 0 ? degree : c->prm.degree;
+    kid->have_seq = false;
+    kid->block_lam.clear();
+    chfsi_info* ip = info ? &info[p] : nullptr;
+    status[p] = solve_prefix(kid, (const cplx*)H[p], (const cplx*)S[p], nullptr, false, evals[p], X[p], ip, &st[p]);
+    if (status[p] == CHFSI_ERR_CUDA) return CHFSI_ERR_CUDA;
+    active[p] = status[p] == CHFSI_OK;
+  }
+  // Algorithm 1 for all problems in step: the filters of one iteration of every problem as
+  // one grouped launch per recurrence step, the other stages problem after problem
+  for (;;) {
+    std::vector<int> act;
+    for (int p = 0; p < count; ++p)
+      if (active[p]) act.push_back(p);
+    if (act.empty()) break;
+    std::vector<TcJob> jobs;
+    std::vector<int> job_of;
+    for (int p : act) {
+      chfsi_ctx* kid = c->kids[p];
+      chfsi_status e = iter_plan_filter(kid, st[p]);
+      if (e == CHFSI_OK && st[p].prec == CHFSI_PREC_MIXED && st[p].plan.mmax > 0) {
+        if (!kid->tc) kid->tc = tc_filter_new();
+        const FilterPlan& fp = st[p].plan;
+        jobs.push_back(TcJob{kid->tc, fp.n, fp.Hs, fp.Y, fp.cnt.data(), fp.mmax, fp.fa.data(), fp.fb.data(),
+                             fp.fg.data(), fp.ritz ? &fp.ref : nullptr});
+        job_of.push_back(p);
+      } else if (e == CHFSI_OK) {
+        e = iter_run_filter(kid, st[p]);
+      }
+      if (e != CHFSI_OK) {
+        status[p] = e;
+        active[p] = 0;
+        if (e == CHFSI_ERR_CUDA) return e;
+      }
+    }
+    if (!jobs.empty()) {
+      chfsi_status e = tc_filter_run_batch(c->tcb, c->stream, jobs.data(), (int)jobs.size(), nullptr, true);
+      if (e != CHFSI_OK) {
+        for (int p : job_of) {
+          status[p] = e;
+          active[p] = 0;
+        }
+        if (e == CHFSI_ERR_CUDA) return e;
+      }
+    }
+    for (int p : act) {
+      if (!active[p]) continue;
+      chfsi_ctx* kid = c->kids[p];
+      chfsi_status e = iter_after_filter(kid, st[p]);
+      if (e != CHFSI_OK) {
+        status[p] = e;
+        active[p] = 0;
+        if (e == CHFSI_ERR_CUDA) return e;
+        continue;
+      }
+      if (st[p].done) {
+        active[p] = 0;
+        status[p] = iter_finish(kid, st[p]);
+        if (status[p] == CHFSI_ERR_CUDA) return CHFSI_ERR_CUDA;
+      }
+    }
+  }
+  chfsi_status first = CHFSI_OK;
+  for (int p = 0; p < count; ++p) {
+    status[p] = solve_suffix(c->kids[p], info ? &info[p] : nullptr, status[p]);
+    if (first == CHFSI_OK && status[p] != CHFSI_OK) first = status[p];
+  }
+  return first;
 }
 
 // ---- stage entry points ----------------------------------------------------------------

@@ -24,29 +24,47 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <stdlib.h>
+#include <string.h>
+
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "filter_tc.cuh"
 
 void count_launch(unsigned long long n);
 
+#define TRY_CHFSI(x)                  \
+  do {                                \
+    chfsi_status _s = (x);            \
+    if (_s != CHFSI_OK) return _s;    \
+  } while (0)
+
 namespace {
 
 constexpr int BM = 128;          // tcgen05 M (cta_group::1)
-constexpr int BN = 64;           // real output columns per tile (32 complex)
 constexpr int BK = 64;           // bf16 per 128-byte swizzle row
-constexpr int STAGES = 3;
 constexpr int NSLICE = 3;
 constexpr int A_TILE = BM * BK * 2;            // bytes per A slice tile (16 KB)
-constexpr int B_TILE = BN * BK * 2;            // bytes per B slice tile (8 KB)
-constexpr int STAGE_BYTES = NSLICE * (A_TILE + B_TILE);
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
-constexpr int TMEM_COLS = 256;     // fp32 accumulators of levels s + t = 0, 1, 2 at columns [L BN, (L+1) BN)
 constexpr int NTHREADS = 192;
 constexpr long WAIT_LIMIT = 1L << 24;
 
-static_assert(STAGE_BYTES % 1024 == 0, "stage alignment");
+// Tile of BN real output columns (BN / 2 complex): the autotuner picks the width per shape.
+// TMEM holds the three level accumulators at columns [L BN, (L + 1) BN) (allocation: the next
+// power of two); the shared-memory ring has as many stages as fit.
+template <int BN>
+struct Tile {
+  static constexpr int B_TILE = BN * BK * 2;
+  static constexpr int STAGE_BYTES = NSLICE * (A_TILE + B_TILE);
+  static constexpr int STAGES = BN >= 128 ? 2 : 3;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int TMEM_COLS = BN <= 32 ? 128 : (BN <= 64 ? 256 : 512);
+  static_assert(STAGE_BYTES % 1024 == 0, "stage alignment");
+  static_assert(SMEM_BYTES <= 232448, "shared memory");
+  static_assert(3 * BN <= TMEM_COLS, "TMEM");
+};
 
 struct StepArgs {
   int n, mtiles;                 // rows, row tiles
@@ -198,9 +216,13 @@ __device__ __forceinline__ float2 join_slices(const uint32_t w[3]) {
   return make_float2(re, -nim);
 }
 
-__global__ void __launch_bounds__(NTHREADS, 1)
-    tc_filter_step_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                          StepArgs g) {
+template <int BN>
+__device__ __forceinline__ void step_body(const CUtensorMap* tmA, const CUtensorMap* tmB, const StepArgs& g, int mtile,
+                                          int ntile) {
+  constexpr int STAGES = Tile<BN>::STAGES;
+  constexpr int B_TILE = Tile<BN>::B_TILE;
+  constexpr int STAGE_BYTES = Tile<BN>::STAGE_BYTES;
+  constexpr int TMEM_COLS = Tile<BN>::TMEM_COLS;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -213,8 +235,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t accum = bars + 8u * (2 * STAGES);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * BM;
-  const int n0 = blockIdx.y * BN;   // real column offset
+  const int m0 = mtile * BM;
+  const int n0 = ntile * BN;   // real column offset
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -245,9 +267,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_expect_tx(full(s), STAGE_BYTES);
         const uint32_t st = base + s * STAGE_BYTES;
         for (int q = 0; q < NSLICE; ++q)
-          tma_load_2d(st + q * A_TILE, &tmA, full(s), kb * BK, q * g.mtiles * BM + m0);
+          tma_load_2d(st + q * A_TILE, tmA, full(s), kb * BK, q * g.mtiles * BM + m0);
         for (int q = 0; q < NSLICE; ++q)
-          tma_load_2d(st + NSLICE * A_TILE + q * B_TILE, &tmB, full(s), kb * BK, (int)(q * g.npad) + n0);
+          tma_load_2d(st + NSLICE * A_TILE + q * B_TILE, tmB, full(s), kb * BK, (int)(q * g.npad) + n0);
         issued = kb + 1;
       }
       // After a failure the consumer may have abandoned stages whose copies are still in
@@ -260,11 +282,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // MMA issuer.  The three B slice tiles of a stage lie one after another (slice t at rows
-      // 64 t of one K-major operand) and level L = s + t accumulates in TMEM columns [64 L,
-      // 64 L + 64), so the products of A slice s with B slices 0 .. 2 - s are one MMA of
-      // N = 64 (3 - s) into columns [64 s, 192): three instructions per 16-wide K step for
-      // the six slice products.  Each level has its own accumulator, so the per-instruction
-      // truncation of the FP32 accumulation acts on every level at that level's scale.
+      // BN t of one K-major operand) and level L = s + t accumulates in TMEM columns [BN L,
+      // BN L + BN), so the products of A slice s with B slices 0 .. 2 - s are one MMA of
+      // N = BN (3 - s) into columns [BN s, 3 BN) (split at N = 256): three to four instructions
+      // per 16-wide K step for the six slice products.  Each level has its own accumulator, so
+      // the per-instruction truncation of the FP32 accumulation acts on every level at that
+      // level's scale.
       for (int kb = 0; kb < g.kblocks; ++kb) {
         const int s = kb % STAGES;
         const uint32_t ph = (kb / STAGES) & 1;
@@ -279,9 +302,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
           for (int sa = 0; sa < NSLICE; ++sa) {
             const uint64_t da = da0 + (uint64_t)((sa * A_TILE + kk * 32) >> 4);
-            const uint64_t db = db0 + (uint64_t)((kk * 32) >> 4);
-            umma_bf16(tmem + (uint32_t)(sa * BN), da, db, idesc(BN * (NSLICE - sa)),
-                      (kk != 0 || sa != 0) ? 1u : later);
+            const uint32_t acc = (kk != 0 || sa != 0) ? 1u : later;
+            constexpr int NMAX = 256;
+#pragma unroll
+            for (int off = 0; off < BN * (NSLICE - sa); off += NMAX) {
+              const int nn = BN * (NSLICE - sa) - off < NMAX ? BN * (NSLICE - sa) - off : NMAX;
+              // B rows [off, off + nn) of the stage: 128 bytes per K-major row
+              const uint64_t db = db0 + (uint64_t)((off * 128 + kk * 32) >> 4);
+              umma_bf16(tmem + (uint32_t)(sa * BN + off), da, db, idesc(nn), acc);
+            }
           }
         }
         umma_commit(empty(s));   // frees the stage once these MMAs have read it
@@ -365,6 +394,38 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
   }
+}
+
+// One problem: the tensor maps travel in the parameter space.
+template <int BN>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    tc_filter_step_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                          StepArgs g) {
+  step_body<BN>(&tmA, &tmB, g, blockIdx.x, blockIdx.y);
+}
+
+// Many problems in one launch (one recurrence step of every problem of a batch): a device
+// table describes each problem (its tensor maps, step arguments and first tile); CTA t takes
+// tile t - tile_begin of the problem whose range holds t.
+struct alignas(128) GroupDesc {
+  CUtensorMap mapA;
+  CUtensorMap mapB;
+  StepArgs g;
+  int tile_begin, mtiles;
+};
+template <int BN>
+__global__ void __launch_bounds__(NTHREADS, 1) tc_filter_group_kernel(const GroupDesc* __restrict__ d, int ngroups) {
+  int gi = 0;
+  while (gi + 1 < ngroups && d[gi + 1].tile_begin <= (int)blockIdx.x) ++gi;
+  const int t = (int)blockIdx.x - d[gi].tile_begin;
+  const StepArgs g = d[gi].g;
+  if (threadIdx.x == 0) {
+    // the descriptors were written to global memory by a copy: order them for the TMA unit
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&d[gi].mapA) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&d[gi].mapB) : "memory");
+  }
+  __syncthreads();
+  step_body<BN>(&d[gi].mapA, &d[gi].mapB, g, t % d[gi].mtiles, t / d[gi].mtiles);
 }
 
 // Slices of H' (column-major, Hermitian) as the A operand: A_s[r][2c] = s_s(Re H'[r,c]),
@@ -485,12 +546,103 @@ struct TcFilter {
   int* deg = nullptr;
   int tab_cap = 0, k_cap = 0;
   int* err = nullptr;
-  CUtensorMap mapA, mapB[2];
-  bool attr = false;
+  CUtensorMap mapA, mapB[2][2];      // B maps per tile width (32, 64) and buffer
   cudaEvent_t ev[2] = {nullptr, nullptr};   // around the step launches
   double ms_steps = 0.0;
   long long col_steps = 0;
+  // tile-width trials awaiting their timing: (shape key, width index, events)
+  struct Trial {
+    long long key;
+    int v;
+    cudaEvent_t a, b;
+  };
+  std::vector<Trial> trials;
+  std::vector<cudaEvent_t> ev_pool;
 };
+
+namespace {
+// ---- autotuner of the tile width --------------------------------------------------------
+// The two widths compute every output element in the same order (the same K loop, one
+// element per accumulator column), so they give bit-identical results and the choice can
+// follow measured time alone.  Per launch shape (row tiles, columns) each width is timed on
+// its first use (CUDA events on the launching stream, read at the next synchronisation) and
+// the faster one is kept for the rest of the process.
+constexpr int NVAR = 2;
+constexpr int VAR_BN[NVAR] = {32, 64};
+struct Tune {
+  float ms[NVAR] = {-1.f, -1.f};
+  int choice = -1;
+};
+std::mutex g_tune_mu;
+std::map<long long, Tune> g_tune;
+
+// width index for the next launch of shape `key`; *trial = true when this launch is a timed trial
+int tune_pick(long long key, bool* trial) {
+  // tests pin a width (CHFSI_FILTER_WIDTH=32 or 64) to compare the two
+  if (const char* w = getenv("CHFSI_FILTER_WIDTH")) {
+    *trial = false;
+    return atoi(w) == 32 ? 0 : 1;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  Tune& t = g_tune[key];
+  if (t.choice >= 0) {
+    *trial = false;
+    return t.choice;
+  }
+  for (int v = NVAR - 1; v >= 0; --v)
+    if (t.ms[v] < 0.f) {
+      *trial = true;
+      return v;
+    }
+  *trial = false;
+  return 1;
+}
+void tune_record(long long key, int v, float ms) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  Tune& t = g_tune[key];
+  if (t.choice >= 0 || ms <= 0.f) return;
+  if (t.ms[v] < 0.f || ms < t.ms[v]) t.ms[v] = ms;
+  bool all = true;
+  for (int q = 0; q < NVAR; ++q) all = all && t.ms[q] > 0.f;
+  if (all) t.choice = t.ms[0] < t.ms[1] ? 0 : 1;
+}
+
+template <int BN>
+cudaError_t set_attr_once() {
+  static bool done = false;   // benign race: the attribute is idempotent
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(tc_filter_step_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Tile<BN>::SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_filter_group_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Tile<BN>::SMEM_BYTES);
+  done = e == cudaSuccess;
+  return e;
+}
+
+cudaEvent_t pool_ev(TcFilter* f) {
+  if (!f->ev_pool.empty()) {
+    cudaEvent_t e = f->ev_pool.back();
+    f->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+// after a synchronisation: the trials' times go to the tuner
+void flush_trials(TcFilter* f) {
+  for (auto& t : f->trials) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) tune_record(t.key, t.v, ms);
+    f->ev_pool.push_back(t.a);
+    f->ev_pool.push_back(t.b);
+  }
+  f->trials.clear();
+}
+}  // namespace
+
+TcFilter* tc_filter_new() { return new TcFilter(); }
 
 double tc_filter_take_ms(TcFilter* f, long long* col_steps) {
   const double ms = f->ms_steps;
@@ -499,8 +651,6 @@ double tc_filter_take_ms(TcFilter* f, long long* col_steps) {
   f->col_steps = 0;
   return ms;
 }
-
-TcFilter* tc_filter_new() { return new TcFilter(); }
 
 void tc_filter_free(TcFilter* f) {
   if (!f) return;
@@ -515,11 +665,19 @@ void tc_filter_free(TcFilter* f) {
   cudaFree(f->err);
   for (int i = 0; i < 2; ++i)
     if (f->ev[i]) cudaEventDestroy(f->ev[i]);
+  for (auto& t : f->trials) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  for (auto e : f->ev_pool) cudaEventDestroy(e);
   delete f;
 }
 
 static chfsi_status tc_ensure(TcFilter* f, int n, int k, cudaStream_t s) {
   if (n == f->n && k <= f->k && f->A) return CHFSI_OK;
+  // cudaFree is not guaranteed to wait for queued kernels that use these buffers, and the
+  // memory can go to another thread's allocation at once: drain the stream first
+  CHFSI_CUDA_TRY(cudaStreamSynchronize(s));
   cudaFree(f->A);
   cudaFree(f->B[0]);
   cudaFree(f->B[1]);
@@ -532,7 +690,7 @@ static chfsi_status tc_ensure(TcFilter* f, int n, int k, cudaStream_t s) {
   f->k = k;
   f->kpad = round_up(2L * n, BK);
   f->mpad = round_up(n, BM);
-  f->npad = round_up(2L * k, BN);
+  f->npad = round_up(2L * k, 64);   // a multiple of every tile width
   CHFSI_CUDA_TRY(cudaMalloc(&f->A, sizeof(__nv_bfloat16) * 3 * f->mpad * f->kpad));
   for (int i = 0; i < 2; ++i) {
     CHFSI_CUDA_TRY(cudaMalloc(&f->B[i], sizeof(__nv_bfloat16) * 3 * f->npad * f->kpad));
@@ -544,18 +702,18 @@ static chfsi_status tc_ensure(TcFilter* f, int n, int k, cudaStream_t s) {
   CHFSI_CUDA_TRY(cudaMalloc(&f->R, sizeof(float2) * (size_t)n * k));
   if (!f->err) CHFSI_CUDA_TRY(cudaMalloc(&f->err, sizeof(int)));
   if (!make_map(&f->mapA, f->A, 3 * f->mpad, f->kpad, BM)) return CHFSI_ERR_CUDA;
-  for (int i = 0; i < 2; ++i)
-    if (!make_map(&f->mapB[i], f->B[i], 3 * f->npad, f->kpad, BN)) return CHFSI_ERR_CUDA;
-  if (!f->attr) {
-    CHFSI_CUDA_TRY(cudaFuncSetAttribute(tc_filter_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    f->attr = true;
-  }
+  for (int v = 0; v < NVAR; ++v)
+    for (int i = 0; i < 2; ++i)
+      if (!make_map(&f->mapB[v][i], f->B[i], 3 * f->npad, f->kpad, VAR_BN[v])) return CHFSI_ERR_CUDA;
+  CHFSI_CUDA_TRY(set_attr_once<32>());
+  CHFSI_CUDA_TRY(set_attr_once<64>());
   return CHFSI_OK;
 }
 
-chfsi_status tc_filter_run(TcFilter* f, cudaStream_t s, int n, const cplx* H, cplx* Y, const int* cnt, int mmax,
-                           const double* fa, const double* fb, const double* fg, const TcRefine* ref) {
-  if (mmax < 1 || cnt[1] < 1) return CHFSI_OK;
+// Everything of a filter call before the recurrence steps: buffers, the slices of H' and of
+// the start block (or, corrected form, R and D_1).
+static chfsi_status tc_prologue(TcFilter* f, cudaStream_t s, int n, const cplx* H, cplx* Y, const int* cnt, int mmax,
+                                const double* fa, const TcRefine* ref) {
   const int k = cnt[1];
   chfsi_status st = tc_ensure(f, n, k, s);
   if (st != CHFSI_OK) return st;
@@ -566,10 +724,9 @@ chfsi_status tc_filter_run(TcFilter* f, cudaStream_t s, int n, const cplx* H, cp
     count_launch(1);
   }
   const unsigned cgrid = (unsigned)std::min<long>((n + 255) / 256, 16);
-  std::vector<float> htab;
-  std::vector<double> hpm;
   if (ref) {
     // device tables: rows j = 1..mmax of fa[j] p_{j-1}(lam_i) (FP32), and p_{m_i}(lam_i) (FP64)
+    if (f->tab_cap < (mmax + 1) * k || f->k_cap < k) CHFSI_CUDA_TRY(cudaStreamSynchronize(s));
     if (f->tab_cap < (mmax + 1) * k) {
       cudaFree(f->tabf);
       f->tabf = nullptr;
@@ -585,8 +742,8 @@ chfsi_status tc_filter_run(TcFilter* f, cudaStream_t s, int n, const cplx* H, cp
       CHFSI_CUDA_TRY(cudaMalloc(&f->deg, sizeof(int) * (size_t)k));
       f->k_cap = k;
     }
-    htab.assign((size_t)(mmax + 1) * k, 0.0f);
-    hpm.assign(k, 0.0);
+    std::vector<float> htab((size_t)(mmax + 1) * k, 0.0f);
+    std::vector<double> hpm(k, 0.0);
     for (int j = 1; j <= mmax; ++j)
       for (int i = 0; i < k; ++i) htab[(size_t)j * k + i] = (float)(fa[j] * ref->ptab[(size_t)(j - 1) * k + i]);
     for (int i = 0; i < k; ++i) hpm[i] = ref->ptab[(size_t)ref->deg[i] * k + i];
@@ -602,47 +759,298 @@ chfsi_status tc_filter_run(TcFilter* f, cudaStream_t s, int n, const cplx* H, cp
     slice_Y_kernel<<<gy, 256, 0, s>>>(n, k, f->kpad, f->npad, Y, f->B[0]);
     count_launch(1);
   }
+  return CHFSI_OK;
+}
+
+static StepArgs step_args(TcFilter* f, int n, cplx* Y, const int* cnt, int mmax, int j, const double* fa,
+                          const double* fb, const double* fg, const TcRefine* ref) {
+  const int k = cnt[1];
+  StepArgs g{};
+  g.n = n;
+  g.mtiles = (int)(f->mpad / BM);
+  g.ncols = cnt[j];
+  g.ncols_next = j < mmax ? cnt[j + 1] : 0;
+  g.kblocks = (int)(f->kpad / BK);
+  g.kpad = f->kpad;
+  g.npad = f->npad;
+  g.Bcur = f->B[(j - 1) & 1];
+  g.Bnext = f->B[j & 1];
+  g.Yfinal = ref ? f->Dout : Y;
+  g.fa = (float)fa[j];
+  g.fb = (float)fb[j];
+  g.fg = (float)((j >= (ref ? 3 : 2)) ? fg[j] : 0.0);   // Y_{-1} = 0; in the corrected form D_0 = 0
+  g.R = ref ? f->R : nullptr;
+  g.fcol = ref ? f->tabf + (size_t)j * k : nullptr;
+  g.err = f->err;
+  return g;
+}
+
+static chfsi_status tc_epilogue_launch(TcFilter* f, cudaStream_t s, int n, cplx* Y, int k, const TcRefine* ref) {
+  if (ref) {
+    const unsigned cgrid = (unsigned)std::min<long>((n + 255) / 256, 16);
+    dim3 g2(cgrid, (unsigned)k);
+    refine_combine_kernel<<<g2, 256, 0, s>>>(n, Y, f->Dout, f->pm, f->deg);
+    count_launch(1);
+  }
+  return CHFSI_OK;
+}
+
+chfsi_status tc_filter_run(TcFilter* f, cudaStream_t s, int n, const cplx* H, cplx* Y, const int* cnt, int mmax,
+                           const double* fa, const double* fb, const double* fg, const TcRefine* ref) {
+  if (mmax < 1 || cnt[1] < 1) return CHFSI_OK;
+  const int k = cnt[1];
+  chfsi_status st = tc_prologue(f, s, n, H, Y, cnt, mmax, fa, ref);
+  if (st != CHFSI_OK) return st;
   if (!f->ev[0]) {
     CHFSI_CUDA_TRY(cudaEventCreate(&f->ev[0]));
     CHFSI_CUDA_TRY(cudaEventCreate(&f->ev[1]));
   }
   CHFSI_CUDA_TRY(cudaEventRecord(f->ev[0], s));
   for (int j = ref ? 2 : 1; j <= mmax; ++j) {
-    StepArgs g{};
-    g.n = n;
-    g.mtiles = (int)(f->mpad / BM);
-    g.ncols = cnt[j];
-    g.ncols_next = j < mmax ? cnt[j + 1] : 0;
-    g.kblocks = (int)(f->kpad / BK);
-    g.kpad = f->kpad;
-    g.npad = f->npad;
-    g.Bcur = f->B[(j - 1) & 1];
-    g.Bnext = f->B[j & 1];
-    g.Yfinal = ref ? f->Dout : Y;
-    g.fa = (float)fa[j];
-    g.fb = (float)fb[j];
-    g.fg = (float)((j >= (ref ? 3 : 2)) ? fg[j] : 0.0);   // Y_{-1} = 0; in the corrected form D_0 = 0
-    g.R = ref ? f->R : nullptr;
-    g.fcol = ref ? f->tabf + (size_t)j * k : nullptr;
-    g.err = f->err;
+    const StepArgs g = step_args(f, n, Y, cnt, mmax, j, fa, fb, fg, ref);
     f->col_steps += cnt[j];
-    dim3 grid((unsigned)g.mtiles, (unsigned)((2L * cnt[j] + BN - 1) / BN));
-    tc_filter_step_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(f->mapA, f->mapB[(j - 1) & 1], g);
+    const long long key = ((long long)g.mtiles << 32) | (long long)(2 * cnt[j]);
+    bool trial = false;
+    const int v = tune_pick(key, &trial);
+    cudaEvent_t ta = nullptr, tb = nullptr;
+    if (trial) {
+      ta = pool_ev(f);
+      tb = pool_ev(f);
+      CHFSI_CUDA_TRY(cudaEventRecord(ta, s));
+    }
+    const int BNv = VAR_BN[v];
+    dim3 grid((unsigned)g.mtiles, (unsigned)((2L * cnt[j] + BNv - 1) / BNv));
+    if (v == 0)
+      tc_filter_step_kernel<32><<<grid, NTHREADS, Tile<32>::SMEM_BYTES, s>>>(f->mapA, f->mapB[0][(j - 1) & 1], g);
+    else
+      tc_filter_step_kernel<64><<<grid, NTHREADS, Tile<64>::SMEM_BYTES, s>>>(f->mapA, f->mapB[1][(j - 1) & 1], g);
     count_launch(1);
     CHFSI_CUDA_TRY(cudaGetLastError());
+    if (trial) {
+      CHFSI_CUDA_TRY(cudaEventRecord(tb, s));
+      f->trials.push_back({key, v, ta, tb});
+    }
   }
   CHFSI_CUDA_TRY(cudaEventRecord(f->ev[1], s));
-  if (ref) {
-    dim3 g2(cgrid, (unsigned)k);
-    refine_combine_kernel<<<g2, 256, 0, s>>>(n, Y, f->Dout, f->pm, f->deg);
-    count_launch(1);
-  }
+  TRY_CHFSI(tc_epilogue_launch(f, s, n, Y, k, ref));
   int h = 0;
   CHFSI_CUDA_TRY(cudaMemcpyAsync(&h, f->err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CHFSI_CUDA_TRY(cudaStreamSynchronize(s));
   float ms = 0.f;
   if (cudaEventElapsedTime(&ms, f->ev[0], f->ev[1]) == cudaSuccess) f->ms_steps += ms;
+  flush_trials(f);
   if (h == DEV_ERR_TIMEOUT) return CHFSI_ERR_TIMEOUT;
   if (h != DEV_OK) return CHFSI_ERR_NUMERIC;
+  return CHFSI_OK;
+}
+
+// ---- batch: one grouped launch per recurrence step for every problem ----------------------
+struct TcBatch {
+  GroupDesc* d = nullptr;          // device: descriptors of every step, step after step
+  size_t cap = 0;
+  std::vector<GroupDesc> h;
+  cudaGraphExec_t exec = nullptr;  // the captured step launches, updated in place when possible
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  std::vector<int> trial_v;
+  std::vector<long long> trial_key;
+  std::vector<cudaEvent_t> trial_ev;
+};
+
+TcBatch* tc_batch_new() { return new TcBatch(); }
+void tc_batch_free(TcBatch* b) {
+  if (!b) return;
+  cudaFree(b->d);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (int i = 0; i < 2; ++i)
+    if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+  for (auto e : b->trial_ev) cudaEventDestroy(e);
+  delete b;
+}
+
+chfsi_status tc_filter_run_batch(TcBatch* b, cudaStream_t s, const TcJob* jobs, int njobs, double* ms_steps,
+                                 bool use_graph) {
+  if (njobs <= 0) return CHFSI_OK;
+  int jmax = 0;
+  for (int p = 0; p < njobs; ++p) {
+    const TcJob& J = jobs[p];
+    if (J.mmax < 1 || J.cnt[1] < 1) continue;
+    TRY_CHFSI(tc_prologue(J.f, s, J.n, J.H, J.Y, J.cnt, J.mmax, J.fa, J.ref));
+    jmax = std::max(jmax, J.mmax);
+  }
+  // descriptors of all steps: for step j the problems with j in [start, mmax]
+  b->h.clear();
+  std::vector<int> step_begin, step_count, step_tiles;
+  std::vector<long long> step_key;
+  for (int j = 1; j <= jmax; ++j) {
+    step_begin.push_back((int)b->h.size());
+    int tiles = 0, cnt_groups = 0;
+    long long key = 1LL << 62;
+    for (int p = 0; p < njobs; ++p) {
+      const TcJob& J = jobs[p];
+      if (J.mmax < 1 || J.cnt[1] < 1 || j > J.mmax || j < (J.ref ? 2 : 1) || J.cnt[j] < 1) continue;
+      GroupDesc d;
+      memset(&d, 0, sizeof(d));
+      d.g = step_args(J.f, J.n, J.Y, J.cnt, J.mmax, j, J.fa, J.fb, J.fg, J.ref);
+      d.mapA = J.f->mapA;
+      d.tile_begin = tiles;
+      d.mtiles = d.g.mtiles;
+      tiles += d.g.mtiles * (int)((2L * J.cnt[j] + 63) / 64);   // counted at width 64 for the key
+      key += (long long)d.g.mtiles * 7919 + 2 * J.cnt[j];
+      J.f->col_steps += J.cnt[j];
+      b->h.push_back(d);
+      ++cnt_groups;
+    }
+    step_count.push_back(cnt_groups);
+    step_tiles.push_back(tiles);
+    step_key.push_back(key + ((long long)cnt_groups << 40));
+  }
+  // tile width per step (autotuned on the batch's shape), B maps and tile ranges for that width
+  std::vector<int> step_v(jmax), step_grid(jmax);
+  std::vector<bool> step_trial(jmax);
+  for (int j = 1; j <= jmax; ++j) {
+    bool trial = false;
+    const int v = step_count[j - 1] ? tune_pick(step_key[j - 1], &trial) : 1;
+    step_v[j - 1] = v;
+    step_trial[j - 1] = trial;
+    int tiles = 0;
+    for (int q = 0; q < step_count[j - 1]; ++q) {
+      GroupDesc& d = b->h[step_begin[j - 1] + q];
+      // the job this descriptor came from: its B buffer of step j
+      d.tile_begin = tiles;
+      tiles += d.mtiles * (int)((2L * d.g.ncols + VAR_BN[v] - 1) / VAR_BN[v]);
+    }
+    step_grid[j - 1] = tiles;
+  }
+  {
+    // B maps per descriptor (the job's filter, the buffer read at step j, the chosen width)
+    int idx = 0;
+    for (int j = 1; j <= jmax; ++j)
+      for (int p = 0; p < njobs; ++p) {
+        const TcJob& J = jobs[p];
+        if (J.mmax < 1 || J.cnt[1] < 1 || j > J.mmax || j < (J.ref ? 2 : 1) || J.cnt[j] < 1) continue;
+        b->h[idx++].mapB = J.f->mapB[step_v[j - 1]][(j - 1) & 1];
+      }
+  }
+  const size_t bytes = sizeof(GroupDesc) * std::max<size_t>(1, b->h.size());
+  if (b->cap < bytes) {
+    CHFSI_CUDA_TRY(cudaStreamSynchronize(s));   // no queued launch may still read the old table
+    cudaFree(b->d);
+    b->d = nullptr;
+    CHFSI_CUDA_TRY(cudaMalloc(&b->d, bytes));
+    b->cap = bytes;
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+  }
+  CHFSI_CUDA_TRY(cudaMemcpyAsync(b->d, b->h.data(), sizeof(GroupDesc) * b->h.size(), cudaMemcpyHostToDevice, s));
+  if (!b->ev[0]) {
+    CHFSI_CUDA_TRY(cudaEventCreate(&b->ev[0]));
+    CHFSI_CUDA_TRY(cudaEventCreate(&b->ev[1]));
+  }
+  // the step launches: captured into a graph (re-used through an in-place update when the
+  // launch shapes allow), unless a step is a timed autotuning trial
+  bool any_trial = false;
+  for (int j = 0; j < jmax; ++j) any_trial = any_trial || step_trial[j];
+  auto launch_steps = [&](bool timed) -> chfsi_status {
+    for (int j = 1; j <= jmax; ++j) {
+      if (!step_count[j - 1]) continue;
+      cudaEvent_t ta = nullptr, tb = nullptr;
+      if (timed && step_trial[j - 1]) {
+        ta = nullptr;
+        CHFSI_CUDA_TRY(cudaEventCreate(&ta));
+        CHFSI_CUDA_TRY(cudaEventCreate(&tb));
+        CHFSI_CUDA_TRY(cudaEventRecord(ta, s));
+      }
+      const GroupDesc* dj = b->d + step_begin[j - 1];
+      const int ng = step_count[j - 1];
+      if (step_v[j - 1] == 0)
+        tc_filter_group_kernel<32><<<step_grid[j - 1], NTHREADS, Tile<32>::SMEM_BYTES, s>>>(dj, ng);
+      else
+        tc_filter_group_kernel<64><<<step_grid[j - 1], NTHREADS, Tile<64>::SMEM_BYTES, s>>>(dj, ng);
+      count_launch(1);
+      CHFSI_CUDA_TRY(cudaGetLastError());
+      if (ta) {
+        CHFSI_CUDA_TRY(cudaEventRecord(tb, s));
+        b->trial_ev.push_back(ta);
+        b->trial_ev.push_back(tb);
+        b->trial_v.push_back(step_v[j - 1]);
+        b->trial_key.push_back(step_key[j - 1]);
+      }
+    }
+    return CHFSI_OK;
+  };
+  CHFSI_CUDA_TRY(cudaEventRecord(b->ev[0], s));
+  if (use_graph && !any_trial) {
+    cudaGraph_t graph = nullptr;
+    CHFSI_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    chfsi_status lst = launch_steps(false);
+    cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    if (lst != CHFSI_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return lst;
+    }
+    CHFSI_CUDA_TRY(ce);
+    bool updated = false;
+    if (b->exec) {
+      cudaGraphExecUpdateResultInfo info;
+      updated = cudaGraphExecUpdate(b->exec, graph, &info) == cudaSuccess;
+      if (!updated) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+      }
+    }
+    if (!updated) {
+      cudaError_t ie = cudaGraphInstantiate(&b->exec, graph, 0);
+      if (ie != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return chfsi_cuda_error(ie, "cudaGraphInstantiate");
+      }
+    }
+    cudaGraphDestroy(graph);
+    CHFSI_CUDA_TRY(cudaGraphLaunch(b->exec, s));
+  } else {
+    TRY_CHFSI(launch_steps(true));
+  }
+  CHFSI_CUDA_TRY(cudaEventRecord(b->ev[1], s));
+  for (int p = 0; p < njobs; ++p) {
+    const TcJob& J = jobs[p];
+    if (J.mmax < 1 || J.cnt[1] < 1) continue;
+    TRY_CHFSI(tc_epilogue_launch(J.f, s, J.n, J.Y, J.cnt[1], J.ref));
+  }
+  // status words of every problem, one synchronisation
+  std::vector<int> herr(njobs, 0);
+  for (int p = 0; p < njobs; ++p)
+    if (jobs[p].mmax >= 1 && jobs[p].cnt[1] >= 1)
+      CHFSI_CUDA_TRY(cudaMemcpyAsync(&herr[p], jobs[p].f->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CHFSI_CUDA_TRY(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]) == cudaSuccess) {
+    if (ms_steps) *ms_steps += ms;
+    // each problem's share of the grouped launches, by its executed work (columns x n^2)
+    double tot = 0.0;
+    std::vector<double> w(njobs, 0.0);
+    for (int p = 0; p < njobs; ++p) {
+      const TcJob& J = jobs[p];
+      for (int j = J.ref ? 2 : 1; j <= J.mmax && J.cnt[1] >= 1; ++j) w[p] += (double)J.cnt[j] * J.n * J.n;
+      tot += w[p];
+    }
+    for (int p = 0; p < njobs; ++p)
+      if (tot > 0.0) jobs[p].f->ms_steps += ms * (w[p] / tot);
+  }
+  for (size_t q = 0; q < b->trial_v.size(); ++q) {
+    float tms = 0.f;
+    if (cudaEventElapsedTime(&tms, b->trial_ev[2 * q], b->trial_ev[2 * q + 1]) == cudaSuccess)
+      tune_record(b->trial_key[q], b->trial_v[q], tms);
+  }
+  for (auto e : b->trial_ev) cudaEventDestroy(e);
+  b->trial_ev.clear();
+  b->trial_v.clear();
+  b->trial_key.clear();
+  for (int p = 0; p < njobs; ++p) {
+    if (herr[p] == DEV_ERR_TIMEOUT) return CHFSI_ERR_TIMEOUT;
+    if (herr[p] != DEV_OK) return CHFSI_ERR_NUMERIC;
+  }
   return CHFSI_OK;
 }

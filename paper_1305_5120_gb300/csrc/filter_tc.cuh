@@ -29,3 +29,25 @@ double tc_filter_take_ms(TcFilter* f, long long* col_steps = nullptr);
 
 chfsi_status tc_filter_run(TcFilter* f, cudaStream_t s, int n, const cplx* H, cplx* Y, const int* cnt, int mmax,
                            const double* fa, const double* fb, const double* fg, const TcRefine* ref = nullptr);
+
+// One filter call of a batch: the arguments of tc_filter_run for one problem (its own
+// TcFilter state; cnt, fa, fb, fg and ref stay valid until tc_filter_run_batch returns).
+struct TcJob {
+  TcFilter* f;
+  int n;
+  const cplx* H;
+  cplx* Y;
+  const int* cnt;
+  int mmax;
+  const double *fa, *fb, *fg;
+  const TcRefine* ref;
+};
+struct TcBatch;   // device descriptor table and the captured graph of a batch's step launches
+TcBatch* tc_batch_new();
+void tc_batch_free(TcBatch* b);
+// The filter of every job, recurrence step j of all of them as ONE grouped launch (a tile
+// scheduler over the problems' tiles; the tile width per step autotuned); the step launches
+// are captured into a CUDA graph when use_graph is set.  Same results as tc_filter_run on
+// each job.  *ms_steps += device time of the step launches.
+chfsi_status tc_filter_run_batch(TcBatch* b, cudaStream_t s, const TcJob* jobs, int njobs, double* ms_steps,
+                                 bool use_graph);

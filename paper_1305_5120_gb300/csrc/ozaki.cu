@@ -507,8 +507,13 @@ void ozaki_free(OzakiGemm* o) {
   delete o;
 }
 
-static cudaError_t grow(void** p, size_t* have, size_t need) {
+// Grows a workspace.  The previous product's kernels may still be queued on the stream and
+// use the old buffer, and cudaFree is not guaranteed to wait for them (the memory can go to
+// another thread's allocation at once): drain the stream first.
+static cudaError_t grow(void** p, size_t* have, size_t need, cudaStream_t s) {
   if (*have >= need) return cudaSuccess;
+  cudaError_t es = cudaStreamSynchronize(s);
+  if (es != cudaSuccess) return es;
   cudaFree(*p);
   *p = nullptr;
   *have = 0;
@@ -526,10 +531,10 @@ cudaError_t ozaki_gemm(OzakiGemm* o, const GemmArgs& g, cudaStream_t s, int* err
   const long M = g.M, N = g.N, K = g.K;
   const long mpad = round_up(M, BM), kpad = round_up(2 * K, BK), npad = round_up(2 * N, BN);
   cudaError_t e;
-  if ((e = grow((void**)&o->A, &o->a_bytes, sizeof(__nv_bfloat16) * SLICES * mpad * kpad)) != cudaSuccess) return e;
-  if ((e = grow((void**)&o->B, &o->b_bytes, sizeof(__nv_bfloat16) * SLICES * npad * kpad)) != cudaSuccess) return e;
+  if ((e = grow((void**)&o->A, &o->a_bytes, sizeof(__nv_bfloat16) * SLICES * mpad * kpad, s)) != cudaSuccess) return e;
+  if ((e = grow((void**)&o->B, &o->b_bytes, sizeof(__nv_bfloat16) * SLICES * npad * kpad, s)) != cudaSuccess) return e;
   size_t have = o->exps_n * sizeof(int);
-  if ((e = grow((void**)&o->exps, &have, sizeof(int) * (M + N))) != cudaSuccess) return e;
+  if ((e = grow((void**)&o->exps, &have, sizeof(int) * (M + N), s)) != cudaSuccess) return e;
   o->exps_n = have / sizeof(int);
   if (!o->attr) {
     if ((e = cudaFuncSetAttribute(ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)) != cudaSuccess)
@@ -598,7 +603,7 @@ cudaError_t ozaki_gemm(OzakiGemm* o, const GemmArgs& g, cudaStream_t s, int* err
   a.splits = splits;
   a.err = err;
   if (splits > 1) {
-    if ((e = grow((void**)&o->partial, &o->partial_bytes, sizeof(cplx) * splits * M * N)) != cudaSuccess) return e;
+    if ((e = grow((void**)&o->partial, &o->partial_bytes, sizeof(cplx) * splits * M * N, s)) != cudaSuccess) return e;
     a.partial = o->partial;
   }
   dim3 grid((unsigned)(mpad / BM), (unsigned)(npad / BN), (unsigned)splits);

@@ -116,6 +116,7 @@ def test_sequence_n2000_against_golden(prec):
     w = synth.SEQ_N2000
     ctx = lib.Context(device=0, precision=prec)
     k = w.nev + w.nex
+    refined = fallbacks = 0
     for l, p in synth.sequence(w.n, w.n_low, w.high, w.steps, w.seed):
         H, S = lib.colmajor(p.H), lib.colmajor(p.S)
         if l == 0:
@@ -124,9 +125,15 @@ def test_sequence_n2000_against_golden(prec):
         else:
             st, ev, X, info = ctx.next_in_sequence(H, None, nev=w.nev, n=w.n)
         assert st == 0, (l, lib.STATUS[st])
+        refined += info.eig_refined
+        fallbacks += info.eig_fallbacks
         if l in gold:
             check_pairs(p.H, p.S, ev.cpu().numpy(), lib.to_numpy(X), gold[l], w.nev)
     ctx.close()
+    if prec == lib.CHFSI_PREC_MIXED:
+        # the reduced eigenproblems ran through the FP32 start + FP64 refinement, not the
+        # fallback (FP64 Jacobi)
+        assert refined >= 40 and fallbacks <= refined // 10, (refined, fallbacks)
 
 
 def test_error_paths():
