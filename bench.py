@@ -263,12 +263,18 @@ def kernel_rooflines(infos, n, fp64_peak):
                              "peak_note": f"{pk_kind} bf16 sustained; 78 executed digit products"}
     if e_ms > 0:
         a = e_flop / (e_ms / 1e3) / 1e12
-        k["jacobi_fast_kernel"] = {"role": "reduced eigensolver (FP64, grid barriers)", "bound": "alu",
-                                   "achieved": a, "peak": fp64_peak, "unit": "TFLOP/s", "frac": a / fp64_peak,
-                                   "ms": e_ms, "sweeps": int(sum(i.eig_sweeps for _, i in infos)),
-                                   "rounds": int(sum(i.eig_rounds for _, i in infos)),
-                                   "work_note": "28 k^2 flops per rotating round (A's Hermitian half and the "
-                                                "eigenvector accumulator)", "peak_note": fp64_note}
+        k["reduced_eigensolver"] = {
+            "role": "Rayleigh-Ritz eigenproblem: FP32 one-sided Jacobi (os_jacobi_kernel, one cluster) + FP64 "
+                    "refinement on the tensor cores; FP64 Jacobi (jacobi_fast_kernel) as fallback",
+            "bound": "latency", "ms": e_ms,
+            "calls_refined": int(sum(i.eig_refined for _, i in infos)),
+            "refine_iterations": int(sum(i.eig_refine_iters for _, i in infos)),
+            "f32_sweeps": int(sum(i.eig_f32_sweeps for _, i in infos)),
+            "fallbacks": int(sum(i.eig_fallbacks for _, i in infos)),
+            "fp64_jacobi": {"sweeps": int(sum(i.eig_sweeps for _, i in infos)),
+                            "rounds": int(sum(i.eig_rounds for _, i in infos)),
+                            "achieved_tflops_over_eig_span": a, "peak": fp64_peak,
+                            "work_note": "28 k^2 flops per rotating round", "peak_note": fp64_note}}
     if c_ms > 0:
         a = c_flop / (c_ms / 1e3) / 1e12
         k["chol_inv_kernel"] = {"role": "Cholesky of S and its inverse (FP64)", "bound": "alu", "achieved": a,
@@ -364,6 +370,201 @@ def run_kpoints(args):
             "by_slots": lines}
     print(json.dumps(line), flush=True)
     return 0 if all(v["wrong"] == 0 and v["failed"] == 0 for v in lines.values()) else 1
+
+
+def run_batch(args):
+    """Batched k-points (chfsi_solve_batch): the same 64 problems as --workload kpoints (n ~
+    U[1500, 4000], nev ~ U[5 %, 15 %] n, nex = 0.2 nev, spectra as the single-problem
+    workload, per-problem seeds 0..63, cold starts), solved as one batch: every problem's
+    filter of an iteration is one grouped tensor-core launch per recurrence step.  One warm-up
+    batch of the first four problems, then the timed batch (CUDA events on the context's
+    stream); every result checked against its prescribed spectrum, its completeness (inertia
+    count at the gap) and its status."""
+    import torch
+    from paper_1305_5120_gb300 import chfsi, synth
+    rng = np.random.default_rng(0)
+    probs = []
+    for i in range(args.kpoints):
+        n = int(rng.integers(1500, 4001))
+        nev = max(4, int(round(n * rng.uniform(0.05, 0.15))))
+        nex = max(2, int(round(0.2 * nev)))
+        H, S, lam = synth.prescribed_pencil_device(n, nev, 50.0, seed=i)
+        probs.append((n, nev, nex, chfsi.colmajor(H), chfsi.colmajor(S), lam[:nev].cpu().numpy()))
+        del H, S
+    torch.cuda.synchronize()
+    prec = chfsi.CHFSI_PREC_MIXED if args.precision == "mixed" else chfsi.CHFSI_PREC_FP64
+    ctx = chfsi.Context(device=0, precision=prec, check_inertia=args.check_inertia)
+
+    def solve(ps):
+        return ctx.solve_batch([p[3] for p in ps], [p[4] for p in ps], [p[0] for p in ps], [p[1] for p in ps],
+                               [p[2] for p in ps], 1e-10, 20)
+
+    solve(probs[:4])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = chfsi.kernel_launches()
+    t0 = time.perf_counter()
+    e0.record(ctx.stream)
+    st, sts, evals, Xs, infos = solve(probs)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = e0.elapsed_time(e1)
+    wrong = []
+    for q, (n, nev, nex, Hd, Sd, lam) in enumerate(probs):
+        err = float(np.abs(evals[q].cpu().numpy() - lam).max())
+        if sts[q] != 0 or err > 1e-10 * max(1.0, float(np.abs(lam).max())) or \
+                (args.check_inertia and infos[q].completeness != 2):
+            wrong.append({"id": q, "status": int(sts[q]), "n": n, "nev": nev, "err": err,
+                          "completeness": int(infos[q].completeness)})
+    stages = np.sum([list(i.ms_stage) for i in infos], axis=0).tolist()
+    line = {"metric": METRIC, "value": len(probs) / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x6+f64" if prec == chfsi.CHFSI_PREC_MIXED else "f64", "data": "synthetic",
+            "config": {"workload": f"batch of {len(probs)} k-points, n ~ U[1500,4000], nev 5-15% n, nex 0.2 nev, "
+                                   "cold start, chfsi_solve_batch", "precision": args.precision,
+                       "check_inertia": args.check_inertia},
+            "wall_s": wall, "wrong": len(wrong), "failures": wrong[:8], "gpu_launches": chfsi.kernel_launches() - launches0,
+            "iterations": int(sum(i.iterations for i in infos)),
+            "pairs_under_floor": int(sum(i.n_floor for i in infos)),
+            "stages_ms_summed": dict(zip(["reduce", "lanczos", "filter", "qr", "rayleigh_ritz", "residual_lock",
+                                          "back_transform", "total"], stages)),
+            "eig": {"ms": float(sum(i.ms_eig for i in infos)), "refined": int(sum(i.eig_refined for i in infos)),
+                    "fallbacks": int(sum(i.eig_fallbacks for i in infos))},
+            "filter_steps_ms": float(sum(i.ms_filter_steps for i in infos)),
+            "chol_ms": float(sum(i.ms_chol for i in infos))}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0 if not wrong else 1
+
+
+def run_large(args):
+    """The large sequence (n = 13000, nev = 1300, nex = 260, degree chosen per vector in
+    [10, 25], mixed precision, 8 steps of the perturbation law H_{l+1} = H_l + 1e-2 0.7^l E_l,
+    S fixed), generated on the device.  Per step: device time, outer iterations, the
+    completeness check (inertia count at the gap), the largest generalized residual (floored
+    as the lock test guarantees) and S-orthonormality; at step 0 the error of every
+    eigenvalue against the prescribed spectrum; at later steps the Weyl bound
+    |lam_l - lam_{l-1}| <= eps_{l-1} ||S^{-1}||_2 (||S^{-1}||_2 = 5.5 for cond(S) = 10)."""
+    import torch
+    from paper_1305_5120_gb300 import chfsi, synth
+    w = synth.SEQ_N13000
+    steps = args.large_steps
+    H, S, lam = synth.prescribed_pencil_device(w.n, w.n_low, w.high, w.seed)
+    Sd = S.T.contiguous()
+    ctx = chfsi.Context(device=0, precision=chfsi.CHFSI_PREC_MIXED, per_vector_degree=1, degree_min=10,
+                        degree_max=25, check_inertia=1)
+    evals = torch.empty(w.nev, dtype=torch.float64, device="cuda")
+    X = torch.empty((w.nev, w.n), dtype=torch.complex128, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows, prev, tot_ms = [], None, 0.0
+    for l in range(steps):
+        if l > 0:
+            H = H + (1e-2 * 0.7 ** (l - 1)) * synth.perturbation_device(w.n, w.seed, l - 1)
+        Hd = H.T.contiguous()
+        torch.cuda.synchronize()
+        e0.record(ctx.stream)
+        if l == 0:
+            st, _, _, info = ctx.solve(Hd, Sd, w.n, w.nev, w.nex, None, w.tol, 0, evals, X)
+        else:
+            st, _, _, info = ctx.next_in_sequence(Hd, None, evals, X)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        tot_ms += ms
+        Xm = X.T
+        HX = H @ Xm
+        SX = S @ Xm
+        a, b, a0 = info.bounds
+        hn = max(abs(a0), abs(b))
+        num = torch.linalg.vector_norm(HX - SX * evals[None, :], dim=0)
+        res = (num / torch.maximum(torch.linalg.vector_norm(HX, dim=0),
+                                   1e-4 * hn * torch.linalg.vector_norm(SX, dim=0))).max().item()
+        G = Xm.conj().T @ SX
+        orth = (G - torch.eye(w.nev, dtype=G.dtype, device=G.device)).abs().max().item()
+        row = {"step": l, "status": int(st), "ms": ms, "iterations": int(info.iterations),
+               "completeness": int(info.completeness), "max_resid_floored": res, "s_orth": orth,
+               "n_floor": int(info.n_floor), "filter_col_steps": int(info.filter_col_steps),
+               "eig_refined": int(info.eig_refined), "eig_fallbacks": int(info.eig_fallbacks)}
+        ev = evals.cpu().numpy()
+        if l == 0:
+            err = np.abs(ev - lam[:w.nev].cpu().numpy())
+            np.savetxt(os.path.join(ROOT, "gpurun_out", "large_step0_eig_errors.txt"), err)
+            row["eig_error_vs_prescribed"] = {"max": float(err.max()), "median": float(np.median(err)),
+                                              "p99": float(np.percentile(err, 99)),
+                                              "worst_index": int(err.argmax())}
+        else:
+            row["weyl_max_shift"] = float(np.abs(ev - prev).max())
+            row["weyl_bound"] = 1e-2 * 0.7 ** (l - 1) * 5.5
+        prev = ev
+        rows.append(row)
+        del HX, SX, G, Xm
+    line = {"metric": METRIC, "value": steps / (tot_ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": 0, "ms_per_step": tot_ms / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16x6+f64", "data": "synthetic",
+            "config": {"workload": w.name + ", per-vector degree 10..25, check_inertia", "n": w.n, "nev": w.nev,
+                       "nex": w.nex, "precision": "mixed"},
+            "per_step": rows}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0 if all(r["status"] == 0 for r in rows) else 1
+
+
+def run_serve(args):
+    """Serving (continuous batching) at a stated reduced scale of the sequence-serving
+    workload: args.serve_sequences k-point sequences of args.serve_steps correlated steps,
+    n log-uniform in [2000, args.serve_nmax], nev ~ U[3 %, 20 %] n, nex = 0.2 nev, Poisson
+    arrivals at args.serve_rate sequences/s (one seeded schedule), Ritz vectors and bounds kept
+    on the device between a sequence's steps, admission by HBM budget.  The mixed arm and the
+    plain-FP64 arm serve the same requests; eigenproblems/s, p50/p99 per-solve latency; every
+    result checked against its prescribed spectrum (step 0) and its floored residuals."""
+    import torch
+    from paper_1305_5120_gb300 import chfsi, serve, synth
+    rng = np.random.default_rng(11)
+    t = 0.0
+    seqs = []
+    for i in range(args.serve_sequences):
+        n = int(round(np.exp(rng.uniform(np.log(2000), np.log(args.serve_nmax)))))
+        nev = max(4, int(round(n * rng.uniform(0.03, 0.20))))
+        nex = max(2, int(round(0.2 * nev)))
+        H, S, lam = synth.prescribed_pencil_device(n, nev, 80.0, seed=500 + i)
+        Hs = [H]
+        for l in range(1, args.serve_steps):
+            Hs.append(Hs[-1] + (1e-2 * 0.7 ** (l - 1)) * synth.perturbation_device(n, 500 + i, l - 1))
+        t += float(rng.exponential(1.0 / args.serve_rate))
+        seqs.append((i, t, n, nev, nex, Hs, S, lam))
+    torch.cuda.synchronize()
+
+    def requests():
+        return [serve.SequenceRequest(seq_id=i, arrival=arr, n=n, nev=nev, nex=nex, steps=len(Hs),
+                                      make_step=lambda l, Hs=Hs, S=S: (Hs[l], S if l == 0 else None), degree=20)
+                for (i, arr, n, nev, nex, Hs, S, lam) in seqs]
+
+    arms = {}
+    for name, prec in (("mixed", chfsi.CHFSI_PREC_MIXED), ("fp64", chfsi.CHFSI_PREC_FP64)):
+        srv = serve.Server(device=0, slots=args.slots, keep_vectors=False, precision=prec)
+        recs = srv.run(requests(), realtime=True)
+        summ = serve.latency_summary(recs)
+        wrong = 0
+        for r in recs:
+            i, arr, n, nev, nex, Hs, S, lam = seqs[r.seq_id]
+            if r.status != 0:
+                wrong += 1
+            elif r.step == 0 and np.abs(r.evals - lam[:nev].cpu().numpy()).max() > 1e-10 * max(
+                    1.0, float(lam[:nev].abs().max())):
+                wrong += 1
+        arms[name] = dict(summ, wrong=wrong)
+    line = {"metric": METRIC, "value": arms["mixed"]["eigenproblems_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.serve_steps, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16x6+f64", "data": "synthetic",
+            "config": {"workload": f"serving: {args.serve_sequences} sequences x {args.serve_steps} steps, n log-U"
+                                   f"[2000,{args.serve_nmax}], nev 3-20% n, nex 0.2 nev, Poisson "
+                                   f"{args.serve_rate}/s, {args.slots} slots (reduced scale)"},
+            "arms": arms,
+            "mixed_over_fp64": (arms["mixed"]["eigenproblems_per_s"] / arms["fp64"]["eigenproblems_per_s"]
+                                if arms["fp64"]["eigenproblems_per_s"] else None)}
+    print(json.dumps(line), flush=True)
+    return 0 if all(a["wrong"] == 0 for a in arms.values()) else 1
 
 
 def config_dict(w, precision):
@@ -633,7 +834,13 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--kernel-case", choices=["filter", "ozaki", "zgemm"], default=None)
-    ap.add_argument("--workload", choices=["sequence", "kpoints", "seeding"], default="sequence")
+    ap.add_argument("--workload", choices=["sequence", "kpoints", "batch", "large", "serve", "seeding"],
+                    default="sequence")
+    ap.add_argument("--large-steps", type=int, default=8)
+    ap.add_argument("--serve-sequences", type=int, default=6)
+    ap.add_argument("--serve-steps", type=int, default=3)
+    ap.add_argument("--serve-nmax", type=int, default=4000)
+    ap.add_argument("--serve-rate", type=float, default=2.0)
     ap.add_argument("--kpoints", type=int, default=64)
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--n", type=int, default=2000)
@@ -648,6 +855,12 @@ def main():
         return kernel_case(args)
     if args.workload == "kpoints":
         return run_kpoints(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "large":
+        return run_large(args)
+    if args.workload == "serve":
+        return run_serve(args)
     if args.workload == "seeding":
         return run_seeding(args)
     if args.impl == "reference":

@@ -305,7 +305,7 @@ __global__ void set_word_kernel(int* w, int v) { *w = v; }
 
 chfsi_status gemm64(chfsi_ctx* c, const GemmArgs& g) {
   if (c->prm.precision == CHFSI_PREC_MIXED && g.epi == EPI_GEMM && g.N > 1 && g.M > 1 &&
-      (double)g.M * g.N * g.K >= 4.0e6) {
+      (double)g.M * g.N * g.K >= 2.5e5) {
     if (!c->oz) c->oz = ozaki_new();
     span_begin(c, 0, gemm_flop(g));
     CU(ozaki_gemm(c->oz, g, c->stream, c->d_err));
@@ -322,12 +322,76 @@ chfsi_status gemm64(chfsi_ctx* c, const GemmArgs& g) {
 }
 
 // a1 + inverse: L and Linv from S --------------------------------------------------------
+// Blocked right-looking Cholesky of S and its inverse for the mixed-precision path: the
+// diagonal blocks (CHOL_NB) by the cooperative FP64 factorisation, the panels L21 = A21 L11^{-H},
+// the trailing updates A22 -= L21 L21^H (lower triangle) and the block rows of L^{-1}
+// (X_i = -L_ii^{-1} (L[i, :i] X[:i, :i])) as FP64-accurate tensor-core products, so that only
+// the diagonal blocks run on the FP64 pipe.
+constexpr int CHOL_NB = 128;
+__global__ void zero_upper_blk_kernel(int n, cplx* A, long lda) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)n * n; e += (long)gridDim.x * blockDim.x) {
+    const long r = e % n, col = e / n;
+    if (r < col) A[r + col * lda] = cmk(0.0, 0.0);
+  }
+}
+chfsi_status factor_blocked(chfsi_ctx* c, int n, cplx* L, cplx* Linv) {
+  const int nb = CHOL_NB, nblk = (n + nb - 1) / nb;
+  cplx *D, *Di, *DI, *P, *T;
+  char* w;
+  TRY(buf(c, "cb_D", (size_t)nb * nb, &D));
+  TRY(buf(c, "cb_Di", (size_t)nb * nb, &Di));
+  TRY(buf(c, "cb_DI", (size_t)nblk * nb * nb, &DI));   // L_ii^{-1} of every block (ld nb)
+  TRY(buf(c, "cb_P", (size_t)n * nb, &P));
+  TRY(buf(c, "cb_T", (size_t)n * nb, &T));
+  TRY(buf(c, "cb_work", chol_inv_work_bytes(nb), &w));
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int j0 = bi * nb, jb = std::min(nb, n - j0), r = n - j0 - jb;
+    cplx* A11 = L + j0 + (size_t)j0 * n;
+    CU(copy_block(c->stream, jb, jb, A11, n, D, jb));
+    CU(chol_inv_small(c->stream, jb, D, Di, w, c->d_err));
+    CU(copy_block(c->stream, jb, jb, D, jb, A11, n));
+    CU(copy_block(c->stream, jb, jb, Di, jb, DI + (size_t)bi * nb * nb, nb));
+    if (r > 0) {
+      cplx* A21 = L + (j0 + jb) + (size_t)j0 * n;
+      cplx* A22 = L + (j0 + jb) + (size_t)(j0 + jb) * n;
+      // L21 = A21 L11^{-H} (L11^{-H} upper triangular)
+      TRY(gemm64(c, gemm_args(r, jb, jb, OP_N, A21, n, OP_C, Di, jb, P, r, ONE, ZERO, TRI_B_UPPER)));
+      CU(copy_block(c->stream, r, jb, P, r, A21, n));
+      // A22 -= L21 L21^H, lower triangle
+      TRY(gemm64(c, gemm_args(r, r, jb, OP_N, P, r, OP_C, P, r, A22, n, MONE, ONE, TRI_C_LOWER)));
+    }
+  }
+  zero_upper_blk_kernel<<<(unsigned)std::min<long>(((long)n * n + 255) / 256, 152L * 16), 256, 0, c->stream>>>(n, L,
+                                                                                                           n);
+  count_launch();
+  CU(cudaGetLastError());
+  if (!Linv) return CHFSI_OK;
+  CU(cudaMemsetAsync(Linv, 0, sizeof(cplx) * (size_t)n * n, c->stream));
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int i0 = bi * nb, jb = std::min(nb, n - i0);
+    const cplx* DIi = DI + (size_t)bi * nb * nb;
+    CU(copy_block(c->stream, jb, jb, DIi, nb, Linv + i0 + (size_t)i0 * n, n));
+    if (i0 > 0) {
+      // T = L[i0:i0+jb, 0:i0] X[0:i0, 0:i0] (X lower triangular), then X[i0:, 0:i0] = -L_ii^{-1} T
+      TRY(gemm64(c, gemm_args(jb, i0, i0, OP_N, L + i0, n, OP_N, Linv, n, T, jb, ONE, ZERO, TRI_B_LOWER)));
+      TRY(gemm64(c, gemm_args(jb, i0, jb, OP_N, DIi, nb, OP_N, T, jb, Linv + i0, n, MONE, ZERO, TRI_A_LOWER)));
+    }
+  }
+  return CHFSI_OK;
+}
+
 // The error word is not reset here: inside a solve a GEMM before it (the carry-over of the
 // block when S changes) may have recorded a bounded-wait failure; the entry points reset it.
 chfsi_status factor_S(chfsi_ctx* c, int n, const cplx* S, cplx* L, cplx* Linv) {
   CU(cudaMemcpyAsync(L, S, sizeof(cplx) * (size_t)n * n, cudaMemcpyDeviceToDevice, c->stream));
   span_begin(c, 2, (8.0 / 3.0) * (double)n * n * n);
-  if (n <= CHOL_INV_KMAX) {
+  if (c->prm.precision == CHFSI_PREC_MIXED && n > 2 * CHOL_NB) {
+    const bool spans = c->spans_off;
+    c->spans_off = true;   // the products belong to the Cholesky's span
+    chfsi_status st = factor_blocked(c, n, L, Linv);
+    c->spans_off = spans;
+    TRY(st);
+  } else if (n <= CHOL_INV_KMAX) {
     // one cooperative launch for L and L^{-1} over all SMs
     cplx* X = Linv;
     if (!X) TRY(buf(c, "chol_inv_X", (size_t)n * n, &X));
@@ -673,18 +737,22 @@ chfsi_status cholqr32_pass(chfsi_ctx* c, int n, int k, cplx* Y, bool* ok) {
   return CHFSI_OK;
 }
 
-// E = G - I in place; *fro2 = ||E||_F^2 (one CTA, fixed-order reduction)
+// grid of the block-partial reductions (at most one block per SM; the host adds the partials)
+constexpr int RED_BLOCKS = 152;
+unsigned red_blocks(long total) { return (unsigned)std::max(1L, std::min((total + 255) / 256, (long)RED_BLOCKS)); }
+
+// E = G - I in place; ||E||_F^2 as one partial sum per block (added on the host in order)
 __global__ void sub_identity_kernel(int k, cplx* G, double* fro2) {
   __shared__ double sh[32];
   double s = 0.0;
-  for (long e = threadIdx.x; e < (long)k * k; e += blockDim.x) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)k * k; e += (long)gridDim.x * blockDim.x) {
     cplx v = G[e];
     if (e % k == e / k) v.x -= 1.0;
     G[e] = v;
     s += cabs2(v);
   }
   s = block_sum(s, sh);
-  if (threadIdx.x == 0) *fro2 = s;
+  if (threadIdx.x == 0) fro2[blockIdx.x] = s;
 }
 // P = a E + b I
 __global__ void axpi_kernel(int k, const cplx* E, double a, double b, cplx* P) {
@@ -706,14 +774,17 @@ chfsi_status lowdin_pass(chfsi_ctx* c, int n, int k, cplx* Y, bool* ok) {
   TRY(buf(c, "qr_P", (size_t)k * k, &P));
   TRY(buf(c, "qr_Q", (size_t)k * k, &Q));
   TRY(buf(c, "qr_T", (size_t)n * k, &T));
-  TRY(buf(c, "qr_fro2", 2, &fro2));
+  TRY(buf(c, "qr_fro2", RED_BLOCKS, &fro2));
   TRY(gemm64(c, gemm_args(k, k, n, OP_C, Y, n, OP_N, Y, n, E, k, ONE, ZERO)));
   CU(hermitize(c->stream, k, E, k));
-  sub_identity_kernel<<<1, 1024, 0, c->stream>>>(k, E, fro2);
+  const unsigned sb = red_blocks((long)k * k);
+  sub_identity_kernel<<<sb, 256, 0, c->stream>>>(k, E, fro2);
   count_launch();
-  double h = 0.0;
-  CU(cudaMemcpyAsync(&h, fro2, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  double hp[RED_BLOCKS];
+  CU(cudaMemcpyAsync(hp, fro2, sizeof(double) * sb, cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
+  double h = 0.0;
+  for (unsigned q = 0; q < sb; ++q) h += hp[q];
   if (!(sqrt(h) <= 1e-3)) {
     *ok = false;
     return CHFSI_OK;
@@ -736,6 +807,14 @@ chfsi_status lowdin_pass(chfsi_ctx* c, int n, int k, cplx* Y, bool* ok) {
   CU(copy_block(c->stream, n, k, T, n, Y, n));
   *ok = true;
   return CHFSI_OK;
+}
+
+// a breakdown of the QR is reported as such only when no earlier product failed: a failed
+// product (error word set) spoils the block, and that failure is the one to report
+chfsi_status qr_breakdown(chfsi_ctx* c) {
+  int e = 0;
+  TRY(read_err(c, &e));
+  return e != DEV_OK ? map_dev_err(e) : CHFSI_ERR_NUMERIC;
 }
 
 chfsi_status orthonormalize(chfsi_ctx* c, int n, int nl, const cplx* Yl, int k, cplx* Y,
@@ -766,9 +845,9 @@ chfsi_status orthonormalize(chfsi_ctx* c, int n, int nl, const cplx* Yl, int k, 
   TRY(cholqr_pass(c, n, k, Y, false, &ok));
   if (!ok) {
     TRY(cholqr_pass(c, n, k, Y, true, &ok));
-    if (!ok) return CHFSI_ERR_NUMERIC;
+    if (!ok) return qr_breakdown(c);
     TRY(cholqr_pass(c, n, k, Y, false, &ok));
-    if (!ok) return CHFSI_ERR_NUMERIC;
+    if (!ok) return qr_breakdown(c);
   }
   if (!exact_qr) {
     // inside the solve only the span and orthonormality matter (Rayleigh-Ritz follows)
@@ -776,7 +855,7 @@ chfsi_status orthonormalize(chfsi_ctx* c, int n, int nl, const cplx* Yl, int k, 
     if (ok) return CHFSI_OK;
   }
   TRY(cholqr_pass(c, n, k, Y, false, &ok));
-  if (!ok) return CHFSI_ERR_NUMERIC;
+  if (!ok) return qr_breakdown(c);
   return CHFSI_OK;
 }
 
@@ -784,12 +863,14 @@ chfsi_status orthonormalize(chfsi_ctx* c, int n, int nl, const cplx* Yl, int k, 
 // FP32 one-sided Jacobi in one cluster, then FP64 refinement (eigen.cu); *done = false when
 // it did not converge within its budget (the caller then runs the FP64 Jacobi on G, which
 // this path leaves untouched).
-__global__ void fro_norm_kernel(int k, const cplx* A, double* out) {
+// ||A||_F^2 as one partial sum per block (the host adds them in block order: deterministic)
+__global__ void fro2_kernel(int k, const cplx* A, double* part) {
   __shared__ double sh[32];
   double s = 0.0;
-  for (long e = threadIdx.x; e < (long)k * k; e += blockDim.x) s += cabs2(A[e]);
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)k * k; e += (long)gridDim.x * blockDim.x)
+    s += cabs2(A[e]);
   s = block_sum(s, sh);
-  if (threadIdx.x == 0) *out = sqrt(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
 struct Groups {   // connected components of the strongly coupled pairs (host side)
@@ -856,18 +937,22 @@ chfsi_status reduced_eig_refined(chfsi_ctx* c, int k, const cplx* G, double* lam
   TRY(buf(c, "eo_tmp", (size_t)k * k, &tmp));
   TRY(buf(c, "eo_V", (size_t)k * OA_GROUP_MAX, &V));
   TRY(buf(c, "eo_d", k, &d));
-  TRY(buf(c, "eo_fro", 1, &fro));
+  TRY(buf(c, "eo_fro", RED_BLOCKS, &fro));
   TRY(buf(c, "eo_maxb", 2, &maxb));
   TRY(buf(c, "eo_np", 1, &np));
   TRY(buf(c, "eo_pairs", cap, &pairs));
   TRY(buf(c, "eo_gint", (size_t)4 * k + 2, &gint));
   cplx* X = P;                       // X and G X side by side: T = X^H [X | G X] is one product
   cplx* GX = P + (size_t)k * k;
-  fro_norm_kernel<<<1, 1024, 0, c->stream>>>(k, G, fro);
+  const unsigned fb = red_blocks((long)k * k);
+  fro2_kernel<<<fb, 256, 0, c->stream>>>(k, G, fro);
   count_launch();
-  double hfro = 0.0;
-  CU(cudaMemcpyAsync(&hfro, fro, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  double hpart[RED_BLOCKS];
+  CU(cudaMemcpyAsync(hpart, fro, sizeof(double) * fb, cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
+  double hfro = 0.0;
+  for (unsigned q = 0; q < fb; ++q) hfro += hpart[q];
+  hfro = sqrt(hfro);
   if (!(hfro > 0.0) || !std::isfinite(hfro)) return CHFSI_OK;
   CU(cudaMemsetAsync(c->d_err_qr, 0, sizeof(int), c->stream));
   int used = 0;
@@ -1430,8 +1515,13 @@ chfsi_status solve_prefix(chfsi_ctx* c, const cplx* H, const cplx* S, const cplx
   // line 1: Lanczos
   TRY(lanczos_H(c, n, Hs, c->prm.lanczos_steps, k, nullptr, al, be, bd));
   double h[4];
+  int h_err = 0;
   CU(cudaMemcpyAsync(h, bd, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(&h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
+  // a product that failed (a bounded wait ran out) left H' unusable: report that failure,
+  // not the bounds it spoiled
+  if (h_err != DEV_OK) return map_dev_err(h_err);
   float ms_reduce = 0.f, ms_lanczos = 0.f;
   cudaEventElapsedTime(&ms_reduce, r0, r1);
   double b = h[0], a = h[1], a0 = h[2];

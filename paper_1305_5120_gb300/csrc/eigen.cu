@@ -152,6 +152,85 @@ __global__ void __launch_bounds__(OS_THREADS, 1) os_jacobi_kernel(OsArgs g) {
   }
 }
 
+// Block form of the same sweeps for k up to a few hundred: the columns are cut into 2 NC
+// half-blocks of hb columns (NC = CTAs in the cluster) and a block sweep pairs the half-blocks
+// by the round-robin schedule (2 NC - 1 block rounds).  In a block round every CTA copies its
+// two half-blocks (2 hb columns) into shared memory and sweeps all their column pairs there
+// (2 hb - 1 inner rounds of hb disjoint pairs, one warp per pair, CTA barriers), then writes
+// them back; one cluster barrier per block round instead of one per column round.  A block
+// sweep rotates every column pair at least once; it is repeated until one rotates nothing.
+__global__ void __launch_bounds__(OS_THREADS, 1) os_block_kernel(OsArgs g, int hb) {
+  extern __shared__ float2 cols[];   // 2 hb columns of k
+  __shared__ int s_rot;
+  const int k = g.k, nb = 2 * gridDim.x;   // half-blocks
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int sweep = 0;
+  bool done = false;
+  for (; sweep < g.max_sweeps && !done; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int r = 0; r < nb - 1; ++r) {
+      const int ha = slot(blockIdx.x, r, nb), hbk = slot(nb - 1 - blockIdx.x, r, nb);
+      // local column t -> global column
+      auto gcol = [&](int t) { return t < hb ? ha * hb + t : hbk * hb + (t - hb); };
+      for (long e = threadIdx.x; e < 2L * hb * k; e += blockDim.x) {
+        const int t = (int)(e / k), i = (int)(e % k), gc = gcol(t);
+        cols[e] = gc < k ? __ldcg(g.B + (long)gc * k + i) : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      const int m = 2 * hb;   // local columns (even)
+      for (int ir = 0; ir < m - 1; ++ir) {
+        for (int pj = warp; pj < hb; pj += OS_WARPS) {
+          int p = slot(pj, ir, m), q = slot(m - 1 - pj, ir, m);
+          if (p > q) { const int t = p; p = q; q = t; }
+          if (gcol(p) >= k || gcol(q) >= k) continue;
+          float2* x = cols + (long)p * k;
+          float2* y = cols + (long)q * k;
+          float a = 0.f, b = 0.f, gr = 0.f, gi = 0.f;
+          for (int i = lane; i < k; i += 32) {
+            const float2 xv = x[i], yv = y[i];
+            a = fmaf(xv.x, xv.x, fmaf(xv.y, xv.y, a));
+            b = fmaf(yv.x, yv.x, fmaf(yv.y, yv.y, b));
+            gr = fmaf(xv.x, yv.x, fmaf(xv.y, yv.y, gr));
+            gi = fmaf(xv.x, yv.y, fmaf(-xv.y, yv.x, gi));
+          }
+          a = warp_sumf(a);
+          b = warp_sumf(b);
+          gr = warp_sumf(gr);
+          gi = warp_sumf(gi);
+          const float ag = sqrtf(fmaf(gr, gr, gi * gi));
+          if (!(ag > g.tol * sqrtf(a * b))) continue;
+          const float phr = gr / ag, phi = gi / ag;
+          const float tau = (b - a) / (2.f * ag);
+          const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
+          const float c = rsqrtf(fmaf(t, t, 1.f)), sn = t * c;
+          for (int i = lane; i < k; i += 32) {
+            const float2 xv = x[i], yv = y[i];
+            const float wr = fmaf(phr, yv.x, phi * yv.y), wi = fmaf(phr, yv.y, -phi * yv.x);
+            x[i] = make_float2(fmaf(c, xv.x, -sn * wr), fmaf(c, xv.y, -sn * wi));
+            y[i] = make_float2(fmaf(sn, xv.x, c * wr), fmaf(sn, xv.y, c * wi));
+          }
+          if (lane == 0) atomicAdd(&s_rot, 1);
+        }
+        __syncthreads();
+      }
+      for (long e = threadIdx.x; e < 2L * hb * k; e += blockDim.x) {
+        const int t = (int)(e / k), i = (int)(e % k), gc = gcol(t);
+        if (gc < k) __stcg(g.B + (long)gc * k + i, cols[e]);
+      }
+      cluster_sync_all();
+    }
+    if (threadIdx.x == 0 && s_rot) atomicAdd(&g.rot_count[sweep], s_rot);
+    cluster_sync_all();
+    done = *(volatile int*)&g.rot_count[sweep] == 0;
+    __syncthreads();
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *g.sweeps = sweep;
+    if (!done) atomicExch(g.err, DEV_ERR_NO_CONV);
+  }
+}
+
 // B = G + s I in FP32 (rounded to nearest)
 __global__ void os_init_kernel(int k, const cplx* G, double s, float2* B) {
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)k * k; e += (long)gridDim.x * blockDim.x) {
@@ -195,6 +274,8 @@ __global__ void oa_diag_kernel(int k, const cplx* T, double* lam) {
 // Squared magnitudes throughout: no square root per entry on the FP64 pipe.
 __global__ void oa_pairs_kernel(int k, const cplx* T, const double* lam, double tau, cplx* R, cplx* S,
                                 unsigned long long* maxbits, int* npairs, int cap, int2* pairs) {
+  // maxima reduced in the warp, then the block, then one atomic per block
+  unsigned long long ms = 0, mr = 0;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)k * k; e += (long)gridDim.x * blockDim.x) {
     const int i = (int)(e % k), j = (int)(e / k);
     const cplx x = T[e], xt = T[j + (long)i * k];                  // X^H X entries (i, j) and (j, i)
@@ -207,15 +288,35 @@ __global__ void oa_pairs_kernel(int k, const cplx* T, const double* lam, double 
     }
     R[e] = r;
     S[e] = cmk(sv.x, i == j ? 0.0 : sv.y);
-    atomicMax(maxbits + 1, (unsigned long long)__double_as_longlong(cabs2(r)));
+    mr = max(mr, (unsigned long long)__double_as_longlong(cabs2(r)));
     if (i != j) {
       const double sa2 = cabs2(sv), dl = tau * (lam[j] - lam[i]);
-      atomicMax(maxbits, (unsigned long long)__double_as_longlong(sa2));
+      ms = max(ms, (unsigned long long)__double_as_longlong(sa2));
       if (i < j && sa2 > dl * dl) {
         const int slot_i = atomicAdd(npairs, 1);
         if (slot_i < cap) pairs[slot_i] = make_int2(i, j);
       }
     }
+  }
+  __shared__ unsigned long long sh[2][32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ms = max(ms, __shfl_xor_sync(0xffffffffu, ms, o));
+    mr = max(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    sh[0][w] = ms;
+    sh[1][w] = mr;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+      ms = max(ms, sh[0][q]);
+      mr = max(mr, sh[1][q]);
+    }
+    if (ms) atomicMax(maxbits, ms);
+    if (mr) atomicMax(maxbits + 1, mr);
   }
 }
 
@@ -407,6 +508,42 @@ cudaError_t os_jacobi_f32(cudaStream_t s, int k, const cplx* G, double shift, fl
   a.rot_count = counters;
   a.sweeps = sweeps;
   a.err = err;
+  // block form when two half-blocks of columns fit in shared memory
+  static int nc_blk_ok = 0;
+  for (int nc : {16, 8}) {
+    if (nc_blk_ok && nc > nc_blk_ok) continue;
+    const int kk = k + (k & 1);
+    const int hb = (kk + 2 * nc - 1) / (2 * nc);
+    const size_t smem = sizeof(float2) * 2 * (size_t)hb * k;
+    if (smem > 200 * 1024 || hb > 2 * OS_WARPS) break;
+    if (nc == 16) cudaFuncSetAttribute(os_block_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(os_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nc);
+    cfg.blockDim = dim3(OS_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = nc;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, os_block_kernel, &cfg) != cudaSuccess || nclusters < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    e = cudaLaunchKernelEx(&cfg, os_block_kernel, a, hb);
+    count_launch(1);
+    if (e == cudaSuccess) {
+      nc_blk_ok = nc;
+      if (cluster_used) *cluster_used = nc;
+      return cudaSuccess;
+    }
+    cudaGetLastError();
+  }
   for (int nc : {16, 8}) {
     if (nc_ok && nc > nc_ok) continue;
     if (nc == 16) cudaFuncSetAttribute(os_jacobi_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

@@ -981,16 +981,29 @@ chfsi_status tc_filter_run_batch(TcBatch* b, cudaStream_t s, const TcJob* jobs, 
     return CHFSI_OK;
   };
   CHFSI_CUDA_TRY(cudaEventRecord(b->ev[0], s));
-  if (use_graph && !any_trial) {
+  // only a created stream can be captured (not the legacy or per-thread default stream), and
+  // not one that is being captured already
+  cudaStreamCaptureStatus cap_now = cudaStreamCaptureStatusNone;
+  const bool capturable = s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread &&
+                          cudaStreamIsCapturing(s, &cap_now) == cudaSuccess && cap_now == cudaStreamCaptureStatusNone;
+  cudaGetLastError();
+  bool captured = false;
+  if (use_graph && capturable && !any_trial &&
+      cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    captured = true;
     cudaGraph_t graph = nullptr;
-    CHFSI_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     chfsi_status lst = launch_steps(false);
     cudaError_t ce = cudaStreamEndCapture(s, &graph);
-    if (lst != CHFSI_OK) {
-      if (graph) cudaGraphDestroy(graph);
-      return lst;
+    if (cudaStreamIsCapturing(s, &cap_now) == cudaSuccess && cap_now != cudaStreamCaptureStatusNone) {
+      cudaGraph_t g2 = nullptr;   // never leave the caller's stream capturing
+      cudaStreamEndCapture(s, &g2);
+      if (g2) cudaGraphDestroy(g2);
     }
-    CHFSI_CUDA_TRY(ce);
+    if (lst != CHFSI_OK || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      if (lst != CHFSI_OK) return lst;
+      return chfsi_cuda_error(ce, "cudaStreamEndCapture");
+    }
     bool updated = false;
     if (b->exec) {
       cudaGraphExecUpdateResultInfo info;
@@ -1010,7 +1023,9 @@ chfsi_status tc_filter_run_batch(TcBatch* b, cudaStream_t s, const TcJob* jobs, 
     }
     cudaGraphDestroy(graph);
     CHFSI_CUDA_TRY(cudaGraphLaunch(b->exec, s));
-  } else {
+  }
+  if (!captured) {
+    cudaGetLastError();
     TRY_CHFSI(launch_steps(true));
   }
   CHFSI_CUDA_TRY(cudaEventRecord(b->ev[1], s));

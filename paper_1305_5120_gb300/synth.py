@@ -174,3 +174,17 @@ def prescribed_pencil_device(n: int, n_low: int, high: float, seed: int, device=
     H = (mq * lam[None, :]) @ mq.conj().T
     H = 0.5 * (H + H.conj().T)
     return H, S, lam
+
+
+def perturbation_device(n: int, seed: int, step: int, device="cuda"):
+    """The sequence perturbation E of `perturbation` (Hermitian, unit 2-norm exactly), built
+    with torch on `device` (mathematical orientation, complex128)."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed) * 1000003 + 7919 * (step + 1) + 29)
+    u = _torch_haar(n, gen, device)
+    e = semicircle(rng_for(seed, 100 + step), n)
+    e = torch.from_numpy(e / np.max(np.abs(e))).to(device)
+    E = (u * e[None, :]) @ u.conj().T
+    return 0.5 * (E + E.conj().T)
+

@@ -34,11 +34,15 @@ def problems(count, lo, hi, seed, device=False):
     return out
 
 
-@pytest.mark.parametrize("prec", [lib.CHFSI_PREC_MIXED, lib.CHFSI_PREC_FP64], ids=["mixed", "fp64"])
-def test_batch_equals_single_solves(prec):
+@pytest.mark.parametrize("prec,own_stream", [(lib.CHFSI_PREC_MIXED, True), (lib.CHFSI_PREC_MIXED, False),
+                                             (lib.CHFSI_PREC_FP64, True)], ids=["mixed-graph", "mixed-default", "fp64"])
+def test_batch_equals_single_solves(prec, own_stream):
+    """On a created stream the grouped step launches are captured into a CUDA graph; on the
+    default stream (not capturable) they are launched directly: same results either way."""
     torch = torch_cuda()
     probs = problems(5, 260, 700, seed=3)
-    ctx = lib.Context(device=0, precision=prec)
+    stream = torch.cuda.Stream() if own_stream else None
+    ctx = lib.Context(device=0, precision=prec, stream=stream)
     st, sts, evals, Xs, infos = ctx.solve_batch([p[3] for p in probs], [p[4] for p in probs],
                                                 [p[0] for p in probs], [p[1] for p in probs], [p[2] for p in probs],
                                                 1e-10, 20)
@@ -60,7 +64,8 @@ def test_batch_equals_single_solves(prec):
 def test_batch_kpoint_sizes_complete():
     torch = torch_cuda()
     probs = problems(6, 1500, 4000, seed=4, device=True)
-    ctx = lib.Context(device=0, precision=lib.CHFSI_PREC_MIXED, check_inertia=1)
+    torch.cuda.synchronize()   # generated on the default stream; solved on another
+    ctx = lib.Context(device=0, precision=lib.CHFSI_PREC_MIXED, check_inertia=1, stream=torch.cuda.Stream())
     st, sts, evals, Xs, infos = ctx.solve_batch([p[3] for p in probs], [p[4] for p in probs],
                                                 [p[0] for p in probs], [p[1] for p in probs], [p[2] for p in probs],
                                                 1e-10, 20)

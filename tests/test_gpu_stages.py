@@ -41,8 +41,11 @@ def empty(rows, cols, dtype=None):
     return torch.empty((cols, rows), dtype=dtype or torch.complex128, device="cuda")
 
 
-@pytest.mark.parametrize("n", [64, 200, 333])
+@pytest.mark.parametrize("n", [64, 200, 333, 700])
 def test_cholesky(ctx, n):
+    """In mixed precision n > 256 takes the blocked factorisation (128-wide diagonal blocks on
+    the FP64 pipe, panels and trailing updates as tensor-core products): 333 and 700 are
+    ragged multiples of the block."""
     S, _ = synth.spd_factor(n, n)
     L = empty(n, n)
     ctx.cholesky(n, dev(S), L)
@@ -52,11 +55,12 @@ def test_cholesky(ctx, n):
     assert np.abs(np.triu(Lg, 1)).max() == 0.0
 
 
-def test_cholesky_not_hpd(ctx):
-    S = np.diag(np.r_[np.ones(40), -1.0, np.ones(23)]).astype(complex)
-    L = empty(64, 64)
+@pytest.mark.parametrize("n,bad", [(64, 40), (600, 450)])
+def test_cholesky_not_hpd(ctx, n, bad):
+    S = np.diag(np.r_[np.ones(bad), -1.0, np.ones(n - bad - 1)]).astype(complex)
+    L = empty(n, n)
     with pytest.raises(lib.ChfsiError) as e:
-        ctx.cholesky(64, dev(S), L)
+        ctx.cholesky(n, dev(S), L)
     assert e.value.status == 2
 
 
