@@ -71,9 +71,10 @@ typedef struct {
                               1: also count the eigenvalues of H' below the gap sigma between the
                               largest returned eigenvalue and the smallest other Ritz value
                               (Sylvester: H' - sigma I + tau Y Y^H, Y the returned vectors, must
-                              be positive definite -- an FP32 Cholesky, valid while the gap
-                              exceeds the factorisation's backward error; smaller gaps are
-                              reported as inconclusive, not as failures).  Every solve checks
+                              be positive definite -- an FP32 Cholesky for n <= 8192, the
+                              blocked FP64 one above; valid while the gap exceeds the
+                              factorisation's backward error; smaller gaps are reported as
+                              inconclusive, not as failures).  Every solve checks
                               that no unreturned Ritz value of the block lies below the largest
                               returned eigenvalue. */
 } chfsi_params;

@@ -123,6 +123,7 @@ struct chfsi_ctx {
   int* d_sweeps = nullptr;
   int* d_rounds = nullptr;
   int* d_err_qr = nullptr;
+  int* d_err_f32 = nullptr;   // the FP32 eigensolver stage's sweep-budget flag (not an error)
   // host-side fault injection for tests (environment CHFSI_INJECT_GEMM_TIMEOUT=N when a solve
   // starts): the N-th FP64-accurate product of that solve reports a bounded-wait timeout in
   // the error word, as the kernel itself would
@@ -334,7 +335,7 @@ __global__ void zero_upper_blk_kernel(int n, cplx* A, long lda) {
     if (r < col) A[r + col * lda] = cmk(0.0, 0.0);
   }
 }
-chfsi_status factor_blocked(chfsi_ctx* c, int n, cplx* L, cplx* Linv) {
+chfsi_status factor_blocked(chfsi_ctx* c, int n, cplx* L, cplx* Linv, int* err) {
   const int nb = CHOL_NB, nblk = (n + nb - 1) / nb;
   cplx *D, *Di, *DI, *P, *T;
   char* w;
@@ -348,7 +349,7 @@ chfsi_status factor_blocked(chfsi_ctx* c, int n, cplx* L, cplx* Linv) {
     const int j0 = bi * nb, jb = std::min(nb, n - j0), r = n - j0 - jb;
     cplx* A11 = L + j0 + (size_t)j0 * n;
     CU(copy_block(c->stream, jb, jb, A11, n, D, jb));
-    CU(chol_inv_small(c->stream, jb, D, Di, w, c->d_err));
+    CU(chol_inv_small(c->stream, jb, D, Di, w, err));
     CU(copy_block(c->stream, jb, jb, D, jb, A11, n));
     CU(copy_block(c->stream, jb, jb, Di, jb, DI + (size_t)bi * nb * nb, nb));
     if (r > 0) {
@@ -388,7 +389,7 @@ chfsi_status factor_S(chfsi_ctx* c, int n, const cplx* S, cplx* L, cplx* Linv) {
   if (c->prm.precision == CHFSI_PREC_MIXED && n > 2 * CHOL_NB) {
     const bool spans = c->spans_off;
     c->spans_off = true;   // the products belong to the Cholesky's span
-    chfsi_status st = factor_blocked(c, n, L, Linv);
+    chfsi_status st = factor_blocked(c, n, L, Linv, c->d_err);
     c->spans_off = spans;
     TRY(st);
   } else if (n <= CHOL_INV_KMAX) {
@@ -863,14 +864,31 @@ chfsi_status orthonormalize(chfsi_ctx* c, int n, int nl, const cplx* Yl, int k, 
 // FP32 one-sided Jacobi in one cluster, then FP64 refinement (eigen.cu); *done = false when
 // it did not converge within its budget (the caller then runs the FP64 Jacobi on G, which
 // this path leaves untouched).
-// ||A||_F^2 as one partial sum per block (the host adds them in block order: deterministic)
-__global__ void fro2_kernel(int k, const cplx* A, double* part) {
+// ||A||_F^2 as one partial sum per block (part[b]; the host adds them in block order:
+// deterministic) and the largest column sum of |Re| + |Im| per block (part[gridDim.x + b]),
+// an upper bound of ||A||_1, itself a bound of ||A||_2 for Hermitian A.  One warp per column.
+__global__ void norms_kernel(int k, const cplx* A, double* part) {
   __shared__ double sh[32];
-  double s = 0.0;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)k * k; e += (long)gridDim.x * blockDim.x)
-    s += cabs2(A[e]);
+  const int lane = threadIdx.x & 31;
+  const long warps = (long)gridDim.x * (blockDim.x >> 5);
+  double s = 0.0, cmax = 0.0;
+  for (long col = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5; col < k; col += warps) {
+    double c1 = 0.0;
+    for (int r = lane; r < k; r += 32) {
+      const cplx v = A[r + col * k];
+      s += cabs2(v);
+      c1 += fabs(v.x) + fabs(v.y);
+    }
+    cmax = fmax(cmax, warp_sum(c1));
+  }
   s = block_sum(s, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  if (lane == 0) sh[threadIdx.x >> 5] = cmax;   // block_sum's trailing barrier makes sh free
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) cmax = fmax(cmax, sh[w]);
+    part[blockIdx.x] = s;
+    part[gridDim.x + blockIdx.x] = cmax;
+  }
 }
 
 struct Groups {   // connected components of the strongly coupled pairs (host side)
@@ -915,7 +933,7 @@ void make_groups(int k, const std::vector<int2>& pairs, Groups* g) {
 
 chfsi_status reduced_eig_refined(chfsi_ctx* c, int k, const cplx* G, double* lam, cplx* W, bool* done) {
   *done = false;
-  const int max_sweeps = 40, max_iter = 12, cap = 4096;
+  const int max_sweeps = 24, max_iter = 12, cap = 4096;
   const double tau = 0.05;
   float2* B;
   int* cnt;
@@ -925,7 +943,9 @@ chfsi_status reduced_eig_refined(chfsi_ctx* c, int k, const cplx* G, double* lam
   int *np, *gint;
   int2* pairs;
   TRY(buf(c, "eo_B", (size_t)k * k, &B));
-  TRY(buf(c, "eo_cnt", max_sweeps, &cnt));
+  TRY(buf(c, "eo_cnt", max_sweeps + 1, &cnt));
+  float* nrm;
+  TRY(buf(c, "eo_nrm", k, &nrm));
   TRY(buf(c, "eo_P", (size_t)2 * k * k, &P));
   TRY(buf(c, "eo_T", (size_t)2 * k * k, &T));
   TRY(buf(c, "eo_R", (size_t)k * k, &R));
@@ -937,27 +957,41 @@ chfsi_status reduced_eig_refined(chfsi_ctx* c, int k, const cplx* G, double* lam
   TRY(buf(c, "eo_tmp", (size_t)k * k, &tmp));
   TRY(buf(c, "eo_V", (size_t)k * OA_GROUP_MAX, &V));
   TRY(buf(c, "eo_d", k, &d));
-  TRY(buf(c, "eo_fro", RED_BLOCKS, &fro));
-  TRY(buf(c, "eo_maxb", 2, &maxb));
+  TRY(buf(c, "eo_fro", 2 * RED_BLOCKS, &fro));
+  TRY(buf(c, "eo_maxb", 3, &maxb));
   TRY(buf(c, "eo_np", 1, &np));
   TRY(buf(c, "eo_pairs", cap, &pairs));
   TRY(buf(c, "eo_gint", (size_t)4 * k + 2, &gint));
   cplx* X = P;                       // X and G X side by side: T = X^H [X | G X] is one product
   cplx* GX = P + (size_t)k * k;
-  const unsigned fb = red_blocks((long)k * k);
-  fro2_kernel<<<fb, 256, 0, c->stream>>>(k, G, fro);
+  const unsigned fb = std::min(red_blocks((long)k * k), (unsigned)((k + 7) / 8));   // 8 warps per block
+  norms_kernel<<<fb, 256, 0, c->stream>>>(k, G, fro);
   count_launch();
-  double hpart[RED_BLOCKS];
-  CU(cudaMemcpyAsync(hpart, fro, sizeof(double) * fb, cudaMemcpyDeviceToHost, c->stream));
+  double hpart[2 * RED_BLOCKS];
+  CU(cudaMemcpyAsync(hpart, fro, sizeof(double) * 2 * fb, cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
-  double hfro = 0.0;
-  for (unsigned q = 0; q < fb; ++q) hfro += hpart[q];
+  double hfro = 0.0, hl1 = 0.0;
+  for (unsigned q = 0; q < fb; ++q) {
+    hfro += hpart[q];
+    hl1 = std::max(hl1, hpart[fb + q]);
+  }
   hfro = sqrt(hfro);
-  if (!(hfro > 0.0) || !std::isfinite(hfro)) return CHFSI_OK;
+  if (!(hfro > 0.0) || !std::isfinite(hfro) || !std::isfinite(hl1)) return CHFSI_OK;
   CU(cudaMemsetAsync(c->d_err_qr, 0, sizeof(int), c->stream));
+  // B = G + s I with s = 2 min(||G||_F, column-sum bound) >= 2 ||G||_2: B is positive
+  // definite with its spectrum in [||G||_2, 3 ||G||_2].  The FP32 eigenvector error of a pair
+  // grows like s 2^-24 / |lam_i - lam_j|, so the smaller of the two bounds is taken (for a
+  // Rayleigh quotient matrix close to diagonal the column sums are ~||G||_2, several times
+  // below ||G||_F at k in the hundreds).
+  const double shift = 2.0 * std::min(hfro, hl1);
+  // Rotation threshold 2^-20, raised to sqrt(k) 2^-24 for large k: an FP32 dot product of
+  // length k carries rounding of that order, below which columns cannot be told apart.  A
+  // sweep budget that runs out is not a failure: the refinement starts from whatever the
+  // sweeps reached (pairs the FP32 stage could not separate become groups there).
+  const float tol = (float)std::max(9.5367431640625e-7, sqrt((double)k) * 5.9604644775390625e-8);
+  CU(cudaMemsetAsync(c->d_err_f32, 0, sizeof(int), c->stream));
   int used = 0;
-  CU(os_jacobi_f32(c->stream, k, G, 2.0 * hfro, B, cnt, max_sweeps, 9.5367431640625e-7f /* 2^-20 */, c->d_err_qr,
-                   c->d_sweeps, &used));
+  CU(os_jacobi_f32(c->stream, k, G, shift, B, nrm, cnt, max_sweeps, tol, c->d_err_f32, c->d_sweeps, &used));
   CU(os_columns(c->stream, k, B, X));
   int hsweeps = 0;
   CU(cudaMemcpyAsync(&hsweeps, c->d_sweeps, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -974,17 +1008,19 @@ chfsi_status reduced_eig_refined(chfsi_ctx* c, int k, const cplx* G, double* lam
     st = gemm64(c, gemm_args(k, 2 * k, k, OP_C, X, k, OP_N, P, k, T, k, ONE, ZERO));
     if (st != CHFSI_OK) break;
     CU(oa_analyze(c->stream, k, T, tau, d, R, S, maxb, np, cap, pairs));
-    unsigned long long hb[2];
+    unsigned long long hb[3];
     int hn = 0, herr = 0;
     CU(cudaMemcpyAsync(hb, maxb, sizeof(hb), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaMemcpyAsync(&hn, np, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaMemcpyAsync(&herr, c->d_err_qr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
-    double offmax, rmax;
+    double offmax, rmax, fcorr;
     memcpy(&offmax, &hb[0], sizeof(double));   // squared maxima
     memcpy(&rmax, &hb[1], sizeof(double));
+    memcpy(&fcorr, &hb[2], sizeof(double));
     offmax = sqrt(offmax);
     rmax = sqrt(rmax);
+    fcorr = sqrt(fcorr);
     if (herr != DEV_OK || !std::isfinite(offmax) || !std::isfinite(rmax) || offmax > 1e-2 * hfro) break;
     if (offmax <= 8.0 * eps * hfro && rmax <= 8.0 * eps) {
       conv = true;
@@ -1030,6 +1066,14 @@ chfsi_status reduced_eig_refined(chfsi_ctx* c, int k, const cplx* G, double* lam
     CU(cudaMemcpyAsync(X, XUp, sizeof(cplx) * (size_t)k * k, cudaMemcpyDeviceToDevice, c->stream));
     st = gemm64(c, gemm_args(k, k, k, OP_N, XUp, k, OP_N, F, k, X, k, ONE, ONE));
     if (st != CHFSI_OK) break;
+    // A correction this small (|F| <= 1e-8, no groups) leaves second-order remainders below
+    // FP64 rounding (|F|^2 ||G||): the updated X is orthonormal and diagonalises G to working
+    // accuracy, and this iteration's lam_i = S_ii / (1 - R_ii) are its eigenvalues to
+    // O(|F|^2 |lam_j - lam_i|), so no confirming iteration is needed.
+    if (ngroups == 0 && fcorr <= 1e-8 && rmax <= 1e-8) {
+      conv = true;
+      break;
+    }
   }
   c->spans_off = false;
   c->acc_eig_f32_sweeps += hsweeps;
@@ -1106,14 +1150,40 @@ __global__ void shift_to_f32_kernel(int n, const cplx* T, double sigma, float2* 
   }
 }
 
+__global__ void sub_diag_kernel(int n, cplx* T, double sigma) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    T[i + i * (long)n].x -= sigma;
+}
+
 chfsi_status inertia_check(chfsi_ctx* c, int n, const cplx* Hs, const cplx* Yl, int nl, double lmin, double lmax,
                            double lnext, double hnorm, int* completeness, chfsi_status* status) {
   const double gap = lnext - lmax;
   const double sigma = 0.5 * (lmax + lnext);
   const double tau = (sigma - lmin) + 0.5 * gap;
   const double mnorm = hnorm + fabs(sigma) + tau;
-  if (!(0.5 * gap > 4.0 * n * 5.9604644775390625e-8 * mnorm) || n > CHOL_INV_KMAX) {
+  // up to CHOL_INV_KMAX the factorisation runs in FP32 (one cooperative launch); beyond, in
+  // FP64 by the blocked factorisation, whose rounding allows a far smaller gap
+  const bool f32 = n <= CHOL_INV_KMAX;
+  const double unit = f32 ? 5.9604644775390625e-8 : 1.1102230246251565e-16;
+  if (!(0.5 * gap > 4.0 * n * unit * mnorm)) {
     *completeness = -1;
+    return CHFSI_OK;
+  }
+  if (!f32) {
+    cplx* T;
+    TRY(buf(c, "tmp_nn", (size_t)n * n, &T));
+    CU(cudaMemcpyAsync(T, Hs, sizeof(cplx) * (size_t)n * n, cudaMemcpyDeviceToDevice, c->stream));
+    TRY(gemm64(c, gemm_args(n, n, nl, OP_N, Yl, n, OP_C, Yl, n, T, n, cmk(tau, 0.0), ONE)));
+    sub_diag_kernel<<<(unsigned)std::min((n + 255) / 256, 152), 256, 0, c->stream>>>(n, T, sigma);
+    count_launch();
+    CU(cudaGetLastError());
+    CU(cudaMemsetAsync(c->d_err_qr, 0, sizeof(int), c->stream));
+    TRY(factor_blocked(c, n, T, nullptr, c->d_err_qr));   // factor only, in place
+    int e = 0;
+    TRY(read_word(c, c->d_err_qr, &e));
+    if (e == DEV_ERR_TIMEOUT) return CHFSI_ERR_TIMEOUT;
+    if (e == DEV_OK) *completeness = 2;
+    else *status = CHFSI_ERR_INCOMPLETE;
     return CHFSI_OK;
   }
   cplx* T;
@@ -1734,13 +1804,14 @@ chfsi_status chfsi_create(chfsi_ctx** out, int device, void* cuda_stream, const 
   c->prm = prm;
   c->degree = prm.degree;
   chfsi_status s = setup_device(c);
-  if (s == CHFSI_OK) s = cu(cudaMalloc(&c->d_err, 4 * sizeof(int)), "err");
+  if (s == CHFSI_OK) s = cu(cudaMalloc(&c->d_err, 8 * sizeof(int)), "err");
   if (s == CHFSI_OK) {
     c->d_sweeps = c->d_err + 1;
     c->d_rounds = c->d_err + 2;
     c->d_err_qr = c->d_err + 3;
+    c->d_err_f32 = c->d_err + 4;
     // on the context's stream (which may be non-blocking), then waited for
-    s = cu(cudaMemsetAsync(c->d_err, 0, 4 * sizeof(int), c->stream), "err");
+    s = cu(cudaMemsetAsync(c->d_err, 0, 8 * sizeof(int), c->stream), "err");
     if (s == CHFSI_OK) s = cu(cudaStreamSynchronize(c->stream), "err");
   }
   for (int i = 0; i < 16 && s == CHFSI_OK; ++i) s = cu(cudaEventCreate(&c->ev[i]), "event");

@@ -5,9 +5,9 @@
 // a grid barrier) and a call takes ~500 of them.  Here:
 //
 //  1. FP32 one-sided cyclic Jacobi inside ONE thread-block cluster (hardware cluster barrier
-//     per round, one warp per column pair, FP32 pipe): the columns of B = G + s I, s = 2 ||G||_F
-//     (so B is positive definite with condition <= 3), are made mutually orthogonal by plane
-//     rotations from the right, B J = W.  For Hermitian positive definite B the columns of W
+//     per round, one warp per column pair, FP32 pipe): the columns of B = G + s I,
+//     s = 2 min(||G||_F, max column sum) >= 2 ||G||_2 (so B is positive definite with
+//     condition <= 3), are made mutually orthogonal by plane rotations from the right, B J = W.  For Hermitian positive definite B the columns of W
 //     are multiples of eigenvectors (B j_i = sigma_i j_i), so no rotation accumulator is kept:
 //     x_i = w_i / ||w_i|| (in FP64).
 //  2. FP64 refinement of the eigenvector matrix X (a quadratically convergent iteration of
@@ -53,8 +53,9 @@ struct OsArgs {
   int k, kk, max_sweeps;
   float tol;           // rotate when |x^H y| > tol ||x|| ||y||
   float2* B;           // k x k, column-major (ld k): G + s I on entry, W = B J on exit
-  int* rot_count;      // per sweep, zeroed before the launch
-  int* sweeps;         // out: sweeps run (the last one rotated nothing unless max_sweeps ran out)
+  float* nrm;          // k: squared column norms (scan scratch)
+  int* rot_count;      // max_sweeps + 1: pairs above the threshold at each scan, zeroed before the launch
+  int* sweeps;         // out: rotating sweeps run
   int* err;            // DEV_ERR_NO_CONV when max_sweeps ran out
 };
 
@@ -63,17 +64,106 @@ struct OsArgs {
 // tan = t: t^2 + 2 tau t - 1 = 0, tau = (b - a) / (2 |g|), the smaller root) diagonalises
 // [[a, g], [conj g, b]], so x' = c x - s conj(ph) y and y' = s x + c conj(ph) y are
 // orthogonal.
+//
+// Convergence is decided before every sweep by one scan of all pairs at once (squared column
+// norms first, then every x_p^H x_q against the threshold; no rotation, two cluster barriers):
+// a sweep that would rotate nothing is never run, and a block already within the threshold
+// (a seeded problem's Rayleigh quotient matrix often is) costs one scan.
+__device__ __forceinline__ int os_scan(const OsArgs& g, int gw, int nw, int lane) {
+  const int k = g.k;
+  for (int p = gw; p < k; p += nw) {
+    const float2* bp = g.B + (long)p * k;
+    float a = 0.f;
+    for (int i = lane; i < k; i += 32) {
+      const float2 x = __ldcg(bp + i);
+      a = fmaf(x.x, x.x, fmaf(x.y, x.y, a));
+    }
+    a = warp_sumf(a);
+    if (lane == 0) __stcg(g.nrm + p, a);
+  }
+  cluster_sync_all();
+  // row pair j: columns j and k-1-j with all their partners above them (k - 1 products together)
+  const float tol2 = g.tol * g.tol;
+  const bool cached = k <= 32 * OS_CACHE;
+  int viol = 0;
+  for (int j = gw; j < (k + 1) / 2; j += nw) {
+    for (int h = 0; h < 2; ++h) {
+      const int p = h == 0 ? j : k - 1 - j;
+      if (h == 1 && p == j) break;
+      const float2* bp = g.B + (long)p * k;
+      float2 xs[OS_CACHE];
+      if (cached) {
+#pragma unroll
+        for (int t = 0; t < OS_CACHE; ++t) {
+          const int i = lane + 32 * t;
+          xs[t] = i < k ? __ldcg(bp + i) : make_float2(0.f, 0.f);
+        }
+      }
+      const float a = __ldcg(g.nrm + p);
+      int q = p + 1;
+      if (cached) {
+        // four partners at a time: their loads are in flight together
+        for (; q + 4 <= k; q += 4) {
+          float gr[4] = {0.f, 0.f, 0.f, 0.f}, gi[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int t = 0; t < OS_CACHE; ++t) {
+            const int i = lane + 32 * t;
+            if (i < k) {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const float2 y = __ldcg(g.B + (long)(q + u) * k + i);
+                gr[u] = fmaf(xs[t].x, y.x, fmaf(xs[t].y, y.y, gr[u]));
+                gi[u] = fmaf(xs[t].x, y.y, fmaf(-xs[t].y, y.x, gi[u]));
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float r = warp_sumf(gr[u]), m = warp_sumf(gi[u]);
+            if (fmaf(r, r, m * m) > tol2 * a * __ldcg(g.nrm + q + u)) ++viol;
+          }
+        }
+      }
+      for (; q < k; ++q) {
+        const float2* bq = g.B + (long)q * k;
+        float gr = 0.f, gi = 0.f;
+        if (cached) {
+#pragma unroll
+          for (int t = 0; t < OS_CACHE; ++t) {
+            const int i = lane + 32 * t;
+            const float2 y = i < k ? __ldcg(bq + i) : make_float2(0.f, 0.f);
+            gr = fmaf(xs[t].x, y.x, fmaf(xs[t].y, y.y, gr));
+            gi = fmaf(xs[t].x, y.y, fmaf(-xs[t].y, y.x, gi));
+          }
+        } else {
+          for (int i = lane; i < k; i += 32) {
+            const float2 x = __ldcg(bp + i), y = __ldcg(bq + i);
+            gr = fmaf(x.x, y.x, fmaf(x.y, y.y, gr));
+            gi = fmaf(x.x, y.y, fmaf(-x.y, y.x, gi));
+          }
+        }
+        gr = warp_sumf(gr);
+        gi = warp_sumf(gi);
+        if (fmaf(gr, gr, gi * gi) > tol2 * a * __ldcg(g.nrm + q)) ++viol;
+      }
+    }
+  }
+  return viol;   // per warp (every lane holds it)
+}
+
 __global__ void __launch_bounds__(OS_THREADS, 1) os_jacobi_kernel(OsArgs g) {
-  __shared__ int s_rot;
   const int k = g.k, kk = g.kk, np = kk / 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gw = blockIdx.x * OS_WARPS + warp, nw = gridDim.x * OS_WARPS;   // the grid is one cluster
   const bool cached = k <= 32 * OS_CACHE;
   int sweep = 0;
   bool done = false;
-  for (; sweep < g.max_sweeps && !done; ++sweep) {
-    if (threadIdx.x == 0) s_rot = 0;
-    __syncthreads();
+  for (;; ++sweep) {
+    const int viol = os_scan(g, gw, nw, lane);
+    if (lane == 0 && viol) atomicAdd(&g.rot_count[sweep], viol);
+    cluster_sync_all();
+    done = *(volatile int*)&g.rot_count[sweep] == 0;
+    if (done || sweep == g.max_sweeps) break;
     for (int r = 0; r < kk - 1; ++r) {
       for (int j = gw; j < np; j += nw) {
         int p = slot(j, r, kk), q = slot(kk - 1 - j, r, kk);
@@ -136,94 +226,9 @@ __global__ void __launch_bounds__(OS_THREADS, 1) os_jacobi_kernel(OsArgs g) {
             __stcg(bq + i, make_float2(fmaf(s, x.x, c * wr), fmaf(s, x.y, c * wi)));
           }
         }
-        if (lane == 0) atomicAdd(&s_rot, 1);
       }
       cluster_sync_all();
     }
-    // every CTA adds its count; after the barrier all read the same total
-    if (threadIdx.x == 0 && s_rot) atomicAdd(&g.rot_count[sweep], s_rot);
-    cluster_sync_all();
-    done = *(volatile int*)&g.rot_count[sweep] == 0;
-    __syncthreads();
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *g.sweeps = sweep;
-    if (!done) atomicExch(g.err, DEV_ERR_NO_CONV);
-  }
-}
-
-// Block form of the same sweeps for k up to a few hundred: the columns are cut into 2 NC
-// half-blocks of hb columns (NC = CTAs in the cluster) and a block sweep pairs the half-blocks
-// by the round-robin schedule (2 NC - 1 block rounds).  In a block round every CTA copies its
-// two half-blocks (2 hb columns) into shared memory and sweeps all their column pairs there
-// (2 hb - 1 inner rounds of hb disjoint pairs, one warp per pair, CTA barriers), then writes
-// them back; one cluster barrier per block round instead of one per column round.  A block
-// sweep rotates every column pair at least once; it is repeated until one rotates nothing.
-__global__ void __launch_bounds__(OS_THREADS, 1) os_block_kernel(OsArgs g, int hb) {
-  extern __shared__ float2 cols[];   // 2 hb columns of k
-  __shared__ int s_rot;
-  const int k = g.k, nb = 2 * gridDim.x;   // half-blocks
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int sweep = 0;
-  bool done = false;
-  for (; sweep < g.max_sweeps && !done; ++sweep) {
-    if (threadIdx.x == 0) s_rot = 0;
-    __syncthreads();
-    for (int r = 0; r < nb - 1; ++r) {
-      const int ha = slot(blockIdx.x, r, nb), hbk = slot(nb - 1 - blockIdx.x, r, nb);
-      // local column t -> global column
-      auto gcol = [&](int t) { return t < hb ? ha * hb + t : hbk * hb + (t - hb); };
-      for (long e = threadIdx.x; e < 2L * hb * k; e += blockDim.x) {
-        const int t = (int)(e / k), i = (int)(e % k), gc = gcol(t);
-        cols[e] = gc < k ? __ldcg(g.B + (long)gc * k + i) : make_float2(0.f, 0.f);
-      }
-      __syncthreads();
-      const int m = 2 * hb;   // local columns (even)
-      for (int ir = 0; ir < m - 1; ++ir) {
-        for (int pj = warp; pj < hb; pj += OS_WARPS) {
-          int p = slot(pj, ir, m), q = slot(m - 1 - pj, ir, m);
-          if (p > q) { const int t = p; p = q; q = t; }
-          if (gcol(p) >= k || gcol(q) >= k) continue;
-          float2* x = cols + (long)p * k;
-          float2* y = cols + (long)q * k;
-          float a = 0.f, b = 0.f, gr = 0.f, gi = 0.f;
-          for (int i = lane; i < k; i += 32) {
-            const float2 xv = x[i], yv = y[i];
-            a = fmaf(xv.x, xv.x, fmaf(xv.y, xv.y, a));
-            b = fmaf(yv.x, yv.x, fmaf(yv.y, yv.y, b));
-            gr = fmaf(xv.x, yv.x, fmaf(xv.y, yv.y, gr));
-            gi = fmaf(xv.x, yv.y, fmaf(-xv.y, yv.x, gi));
-          }
-          a = warp_sumf(a);
-          b = warp_sumf(b);
-          gr = warp_sumf(gr);
-          gi = warp_sumf(gi);
-          const float ag = sqrtf(fmaf(gr, gr, gi * gi));
-          if (!(ag > g.tol * sqrtf(a * b))) continue;
-          const float phr = gr / ag, phi = gi / ag;
-          const float tau = (b - a) / (2.f * ag);
-          const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
-          const float c = rsqrtf(fmaf(t, t, 1.f)), sn = t * c;
-          for (int i = lane; i < k; i += 32) {
-            const float2 xv = x[i], yv = y[i];
-            const float wr = fmaf(phr, yv.x, phi * yv.y), wi = fmaf(phr, yv.y, -phi * yv.x);
-            x[i] = make_float2(fmaf(c, xv.x, -sn * wr), fmaf(c, xv.y, -sn * wi));
-            y[i] = make_float2(fmaf(sn, xv.x, c * wr), fmaf(sn, xv.y, c * wi));
-          }
-          if (lane == 0) atomicAdd(&s_rot, 1);
-        }
-        __syncthreads();
-      }
-      for (long e = threadIdx.x; e < 2L * hb * k; e += blockDim.x) {
-        const int t = (int)(e / k), i = (int)(e % k), gc = gcol(t);
-        if (gc < k) __stcg(g.B + (long)gc * k + i, cols[e]);
-      }
-      cluster_sync_all();
-    }
-    if (threadIdx.x == 0 && s_rot) atomicAdd(&g.rot_count[sweep], s_rot);
-    cluster_sync_all();
-    done = *(volatile int*)&g.rot_count[sweep] == 0;
-    __syncthreads();
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *g.sweeps = sweep;
@@ -275,7 +280,7 @@ __global__ void oa_diag_kernel(int k, const cplx* T, double* lam) {
 __global__ void oa_pairs_kernel(int k, const cplx* T, const double* lam, double tau, cplx* R, cplx* S,
                                 unsigned long long* maxbits, int* npairs, int cap, int2* pairs) {
   // maxima reduced in the warp, then the block, then one atomic per block
-  unsigned long long ms = 0, mr = 0;
+  unsigned long long ms = 0, mr = 0, mf = 0;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)k * k; e += (long)gridDim.x * blockDim.x) {
     const int i = (int)(e % k), j = (int)(e / k);
     const cplx x = T[e], xt = T[j + (long)i * k];                  // X^H X entries (i, j) and (j, i)
@@ -295,28 +300,37 @@ __global__ void oa_pairs_kernel(int k, const cplx* T, const double* lam, double 
       if (i < j && sa2 > dl * dl) {
         const int slot_i = atomicAdd(npairs, 1);
         if (slot_i < cap) pairs[slot_i] = make_int2(i, j);
+      } else if (dl != 0.0) {
+        // first-order correction of a weakly coupled pair: F_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i)
+        const double d = lam[j] - lam[i];
+        const cplx f = cmk(sv.x + lam[j] * r.x, sv.y + lam[j] * r.y);
+        mf = max(mf, (unsigned long long)__double_as_longlong(cabs2(f) / (d * d)));
       }
     }
   }
-  __shared__ unsigned long long sh[2][32];
+  __shared__ unsigned long long sh[3][32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     ms = max(ms, __shfl_xor_sync(0xffffffffu, ms, o));
     mr = max(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+    mf = max(mf, __shfl_xor_sync(0xffffffffu, mf, o));
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) {
     sh[0][w] = ms;
     sh[1][w] = mr;
+    sh[2][w] = mf;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
       ms = max(ms, sh[0][q]);
       mr = max(mr, sh[1][q]);
+      mf = max(mf, sh[2][q]);
     }
     if (ms) atomicMax(maxbits, ms);
     if (mr) atomicMax(maxbits + 1, mr);
+    if (mf) atomicMax(maxbits + 2, mf);
   }
 }
 
@@ -492,11 +506,11 @@ unsigned grid_for(long total) {
 
 }  // namespace
 
-cudaError_t os_jacobi_f32(cudaStream_t s, int k, const cplx* G, double shift, float2* B, int* counters, int max_sweeps,
-                          float tol, int* err, int* sweeps, int* cluster_used) {
+cudaError_t os_jacobi_f32(cudaStream_t s, int k, const cplx* G, double shift, float2* B, float* nrm, int* counters,
+                          int max_sweeps, float tol, int* err, int* sweeps, int* cluster_used) {
   os_init_kernel<<<grid_for((long)k * k), 256, 0, s>>>(k, G, shift, B);
   count_launch(1);
-  cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(int) * max_sweeps, s);
+  cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(int) * (max_sweeps + 1), s);
   if (e != cudaSuccess) return e;
   static int nc_ok = 0;   // largest cluster size that launched (16 needs the non-portable opt-in)
   OsArgs a{};
@@ -505,45 +519,10 @@ cudaError_t os_jacobi_f32(cudaStream_t s, int k, const cplx* G, double shift, fl
   a.max_sweeps = max_sweeps;
   a.tol = tol;
   a.B = B;
+  a.nrm = nrm;
   a.rot_count = counters;
   a.sweeps = sweeps;
   a.err = err;
-  // block form when two half-blocks of columns fit in shared memory
-  static int nc_blk_ok = 0;
-  for (int nc : {16, 8}) {
-    if (nc_blk_ok && nc > nc_blk_ok) continue;
-    const int kk = k + (k & 1);
-    const int hb = (kk + 2 * nc - 1) / (2 * nc);
-    const size_t smem = sizeof(float2) * 2 * (size_t)hb * k;
-    if (smem > 200 * 1024 || hb > 2 * OS_WARPS) break;
-    if (nc == 16) cudaFuncSetAttribute(os_block_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaFuncSetAttribute(os_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(nc);
-    cfg.blockDim = dim3(OS_THREADS);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = nc;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, os_block_kernel, &cfg) != cudaSuccess || nclusters < 1) {
-      cudaGetLastError();
-      continue;
-    }
-    e = cudaLaunchKernelEx(&cfg, os_block_kernel, a, hb);
-    count_launch(1);
-    if (e == cudaSuccess) {
-      nc_blk_ok = nc;
-      if (cluster_used) *cluster_used = nc;
-      return cudaSuccess;
-    }
-    cudaGetLastError();
-  }
   for (int nc : {16, 8}) {
     if (nc_ok && nc > nc_ok) continue;
     if (nc == 16) cudaFuncSetAttribute(os_jacobi_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -584,7 +563,7 @@ cudaError_t os_columns(cudaStream_t s, int k, const float2* W, cplx* X) {
 
 cudaError_t oa_analyze(cudaStream_t s, int k, const cplx* T, double tau, double* lam, cplx* R, cplx* S,
                        unsigned long long* maxbits, int* npairs, int cap, int2* pairs) {
-  cudaError_t e = cudaMemsetAsync(maxbits, 0, 2 * sizeof(unsigned long long), s);
+  cudaError_t e = cudaMemsetAsync(maxbits, 0, 3 * sizeof(unsigned long long), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(npairs, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   oa_diag_kernel<<<(k + 255) / 256, 256, 0, s>>>(k, T, lam);

@@ -5,18 +5,21 @@
 
 constexpr int OA_GROUP_MAX = 16;   // largest group of strongly coupled pairs solved exactly
 
-// B = G + shift I (FP32), then one-sided Jacobi on B's columns until no pair rotates
-// (|x^H y| <= tol ||x|| ||y||) or max_sweeps: on return B = W, whose columns are multiples of
-// eigenvectors.  counters: max_sweeps ints (zeroed here); *sweeps the sweeps run; *err
-// DEV_ERR_NO_CONV if max_sweeps ran out.  *cluster_used: CTAs in the cluster.
-cudaError_t os_jacobi_f32(cudaStream_t s, int k, const cplx* G, double shift, float2* B, int* counters, int max_sweeps,
-                          float tol, int* err, int* sweeps, int* cluster_used);
+// B = G + shift I (FP32), then one-sided Jacobi on B's columns until no pair is above the
+// threshold (|x^H y| <= tol ||x|| ||y||, checked by a scan before each sweep) or max_sweeps
+// sweeps ran: on return B = W, whose columns are multiples of eigenvectors.  nrm: k floats
+// of scratch; counters: max_sweeps + 1 ints (zeroed here); *sweeps the rotating sweeps run;
+// *err DEV_ERR_NO_CONV if max_sweeps ran out.  *cluster_used: CTAs in the cluster.
+cudaError_t os_jacobi_f32(cudaStream_t s, int k, const cplx* G, double shift, float2* B, float* nrm, int* counters,
+                          int max_sweeps, float tol, int* err, int* sweeps, int* cluster_used);
 // X = the columns of W normalised (FP64).
 cudaError_t os_columns(cudaStream_t s, int k, const float2* W, cplx* X);
 // From T = X^H [X | G X] (k x 2k, ld k): lam_i = S_ii / (1 - R_ii), R = I - herm(X^H X),
 // S = herm(X^H G X) (k x k each), maxbits[0] = bits of max_{i != j} |S_ij|^2, maxbits[1] =
-// bits of max |R_ij|^2, and the strongly coupled pairs (|S_ij| > tau |lam_j - lam_i|, i < j): *npairs
-// of them (the first `cap` stored in pairs).
+// bits of max |R_ij|^2, maxbits[2] = bits of max |S_ij + lam_j R_ij|^2 / (lam_j - lam_i)^2 over
+// the weakly coupled pairs (the squared size of the coming first-order correction), and the
+// strongly coupled pairs (|S_ij| > tau |lam_j - lam_i|, i < j): *npairs of them (the first
+// `cap` stored in pairs).
 cudaError_t oa_analyze(cudaStream_t s, int k, const cplx* T, double tau, double* lam, cplx* R, cplx* S,
                        unsigned long long* maxbits, int* npairs, int cap, int2* pairs);
 // Exact FP64 diagonalisation of each group's block of S (group g: members idx[off[g] ..
