@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 #include "filter_tc.cuh"
@@ -117,6 +118,15 @@ __device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity) {
     if (mbar_try(bar, parity)) return true;
   return false;
 }
+
+// Programmatic dependent launch: the step launches overlap their prologue (barriers, TMEM,
+// the first stages' A tiles, which no earlier step writes) with the end of the previous step.
+// griddepcontrol.wait returns once the preceding grid has completed and its writes are
+// visible (at once without a programmatic predecessor); launch_dependents, issued only after
+// that wait, lets the next step's CTAs be scheduled, so a grid never runs ahead of a grid two
+// launches back.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
   asm volatile(
@@ -258,9 +268,25 @@ __device__ __forceinline__ void step_body(const CUtensorMap* tmA, const CUtensor
 
   if (warp == 0) {
     if (lane == 0) {
-      // producer: A slice s at rows s*mtiles*BM + m0, B slice t at rows t*npad + n0
-      int issued = 0;
-      for (int kb = 0; kb < g.kblocks; ++kb) {
+      // producer: A slice s at rows s*mtiles*BM + m0, B slice t at rows t*npad + n0.  The
+      // first stages (empty at start) get their A tiles before the wait for the previous step,
+      // their B tiles (that step's output) after it.
+      const int pre = g.kblocks < STAGES ? g.kblocks : STAGES;
+      for (int kb = 0; kb < pre; ++kb) {
+        const uint32_t st = base + kb * STAGE_BYTES;
+        mbar_expect_tx(full(kb), STAGE_BYTES);
+        for (int q = 0; q < NSLICE; ++q)
+          tma_load_2d(st + q * A_TILE, tmA, full(kb), kb * BK, q * g.mtiles * BM + m0);
+      }
+      pdl_wait();
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      pdl_trigger();
+      for (int kb = 0; kb < pre; ++kb)
+        for (int q = 0; q < NSLICE; ++q)
+          tma_load_2d(base + kb * STAGE_BYTES + NSLICE * A_TILE + q * B_TILE, tmB, full(kb), kb * BK,
+                      (int)(q * g.npad) + n0);
+      int issued = pre;
+      for (int kb = pre; kb < g.kblocks; ++kb) {
         const int s = kb % STAGES;
         const uint32_t ph = (kb / STAGES) & 1;
         if (!mbar_wait(empty(s), ph ^ 1, g.err)) break;
@@ -318,7 +344,9 @@ __device__ __forceinline__ void step_body(const CUtensorMap* tmA, const CUtensor
       umma_commit(accum);        // arrives when every product issued above has completed
     }
   } else {
-    // epilogue: warps 2..5 -> TMEM lane quarter (warp % 4)
+    // epilogue: warps 2..5 -> TMEM lane quarter (warp % 4).  It reads the previous steps'
+    // output and overwrites the buffer the previous step read: after that step has completed.
+    pdl_wait();
     const int q = warp & 3;
     const int row = m0 + q * 32 + lane;
     bool ok = mbar_wait(accum, 0, g.err);
@@ -426,6 +454,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_filter_group_kernel(const Grou
   }
   __syncthreads();
   step_body<BN>(&d[gi].mapA, &d[gi].mapB, g, t % d[gi].mtiles, t / d[gi].mtiles);
+}
+
+// A recurrence step launch that may start while the previous step finishes (programmatic
+// dependent launch; the kernels order their dependent accesses with griddepcontrol.wait).
+template <typename... Params, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(Params...), dim3 grid, int smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(NTHREADS);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 // Slices of H' (column-major, Hermitian) as the A operand: A_s[r][2c] = s_s(Re H'[r,c]),
@@ -821,11 +866,12 @@ chfsi_status tc_filter_run(TcFilter* f, cudaStream_t s, int n, const cplx* H, cp
     const int BNv = VAR_BN[v];
     dim3 grid((unsigned)g.mtiles, (unsigned)((2L * cnt[j] + BNv - 1) / BNv));
     if (v == 0)
-      tc_filter_step_kernel<32><<<grid, NTHREADS, Tile<32>::SMEM_BYTES, s>>>(f->mapA, f->mapB[0][(j - 1) & 1], g);
+      CHFSI_CUDA_TRY(launch_pdl(tc_filter_step_kernel<32>, grid, Tile<32>::SMEM_BYTES, s, f->mapA,
+                                f->mapB[0][(j - 1) & 1], g));
     else
-      tc_filter_step_kernel<64><<<grid, NTHREADS, Tile<64>::SMEM_BYTES, s>>>(f->mapA, f->mapB[1][(j - 1) & 1], g);
+      CHFSI_CUDA_TRY(launch_pdl(tc_filter_step_kernel<64>, grid, Tile<64>::SMEM_BYTES, s, f->mapA,
+                                f->mapB[1][(j - 1) & 1], g));
     count_launch(1);
-    CHFSI_CUDA_TRY(cudaGetLastError());
     if (trial) {
       CHFSI_CUDA_TRY(cudaEventRecord(tb, s));
       f->trials.push_back({key, v, ta, tb});
@@ -965,11 +1011,10 @@ chfsi_status tc_filter_run_batch(TcBatch* b, cudaStream_t s, const TcJob* jobs, 
       const GroupDesc* dj = b->d + step_begin[j - 1];
       const int ng = step_count[j - 1];
       if (step_v[j - 1] == 0)
-        tc_filter_group_kernel<32><<<step_grid[j - 1], NTHREADS, Tile<32>::SMEM_BYTES, s>>>(dj, ng);
+        CHFSI_CUDA_TRY(launch_pdl(tc_filter_group_kernel<32>, dim3(step_grid[j - 1]), Tile<32>::SMEM_BYTES, s, dj, ng));
       else
-        tc_filter_group_kernel<64><<<step_grid[j - 1], NTHREADS, Tile<64>::SMEM_BYTES, s>>>(dj, ng);
+        CHFSI_CUDA_TRY(launch_pdl(tc_filter_group_kernel<64>, dim3(step_grid[j - 1]), Tile<64>::SMEM_BYTES, s, dj, ng));
       count_launch(1);
-      CHFSI_CUDA_TRY(cudaGetLastError());
       if (ta) {
         CHFSI_CUDA_TRY(cudaEventRecord(tb, s));
         b->trial_ev.push_back(ta);
@@ -999,30 +1044,28 @@ chfsi_status tc_filter_run_batch(TcBatch* b, cudaStream_t s, const TcJob* jobs, 
       cudaStreamEndCapture(s, &g2);
       if (g2) cudaGraphDestroy(g2);
     }
-    if (lst != CHFSI_OK || ce != cudaSuccess) {
+    if (lst != CHFSI_OK) {
       if (graph) cudaGraphDestroy(graph);
-      if (lst != CHFSI_OK) return lst;
-      return chfsi_cuda_error(ce, "cudaStreamEndCapture");
+      return lst;
     }
-    bool updated = false;
-    if (b->exec) {
+    // nothing ran during the capture: if the graph cannot be made, launch the steps directly
+    bool ready = ce == cudaSuccess && graph != nullptr;
+    if (ready && b->exec) {
       cudaGraphExecUpdateResultInfo info;
-      updated = cudaGraphExecUpdate(b->exec, graph, &info) == cudaSuccess;
-      if (!updated) {
+      if (cudaGraphExecUpdate(b->exec, graph, &info) != cudaSuccess) {
         cudaGetLastError();
         cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
       }
     }
-    if (!updated) {
-      cudaError_t ie = cudaGraphInstantiate(&b->exec, graph, 0);
-      if (ie != cudaSuccess) {
-        cudaGraphDestroy(graph);
-        return chfsi_cuda_error(ie, "cudaGraphInstantiate");
-      }
+    if (ready && !b->exec && cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess) {
+      cudaGetLastError();
+      b->exec = nullptr;
+      ready = false;
     }
-    cudaGraphDestroy(graph);
-    CHFSI_CUDA_TRY(cudaGraphLaunch(b->exec, s));
+    if (graph) cudaGraphDestroy(graph);
+    if (ready) CHFSI_CUDA_TRY(cudaGraphLaunch(b->exec, s));
+    else captured = false;
   }
   if (!captured) {
     cudaGetLastError();

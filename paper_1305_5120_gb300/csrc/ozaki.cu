@@ -101,6 +101,13 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// Bounded wait without the early exit on a raised error word: used after a failure, to let
+// work already issued (copies into this CTA's shared memory, products) complete.
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity) {
+  for (long i = 0; i < WAIT_LIMIT; ++i)
+    if (mbar_try(bar, parity)) return true;
+  return false;
+}
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
   for (long i = 0; i < WAIT_LIMIT; ++i) {
     if (mbar_try(bar, parity)) return true;
@@ -211,6 +218,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
+      int issued = 0;
       for (int i = 0; i < nkb; ++i) {
         const int s = i % STAGES;
         const uint32_t ph = (i / STAGES) & 1;
@@ -222,7 +230,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         bulk_load(st, g.A + ((long)blockIdx.x * g.kblocks + kb) * (SLICES * BM * BK), SLICES * A_TILE, full(s));
         bulk_load(st + SLICES * A_TILE, g.B + ((long)blockIdx.y * g.kblocks + kb) * (SLICES * BN * BK),
                   SLICES * B_TILE, full(s));
+        issued = i + 1;
       }
+      // After a failure the MMA issuer may have abandoned stages whose copies are still in
+      // flight into this CTA's shared memory: wait until each issued stage has landed (the
+      // latest phase of each stage is the one checked) before the CTA may exit.
+      if (*(volatile int*)g.err != DEV_OK)
+        for (int i = std::max(0, issued - STAGES); i < issued; ++i) mbar_drain(full(i % STAGES), (i / STAGES) & 1);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -314,8 +328,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (*(volatile int*)g.err != DEV_OK) __nanosleep(200000);
   if (warp == 1) {
+    // after a failure the products may still be running: the accumulator barrier (committed
+    // after the last issued MMA) arrives when they have completed (bounded), and only then is
+    // the TMEM returned
+    if (*(volatile int*)g.err != DEV_OK && lane == 0) mbar_drain(accum, 0);
+    __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
   }
