@@ -131,6 +131,10 @@ def traffic_for(kernel: str):
         return None
 
 
+# the solve's stages in chfsi_info.ms_stage order
+STAGES = ["reduce", "lanczos", "filter", "qr", "rayleigh_ritz", "residual_lock", "back_transform", "total"]
+
+
 def make_inputs(w, seed):
     from paper_1305_5120_gb300 import synth
     seq = list(synth.sequence(w.n, w.n_low, w.high, w.steps, seed))
@@ -277,9 +281,12 @@ def kernel_rooflines(infos, n, fp64_peak):
                             "work_note": "28 k^2 flops per rotating round", "peak_note": fp64_note}}
     if c_ms > 0:
         a = c_flop / (c_ms / 1e3) / 1e12
-        k["chol_inv_kernel"] = {"role": "Cholesky of S and its inverse (FP64)", "bound": "alu", "achieved": a,
-                                "peak": fp64_peak, "unit": "TFLOP/s", "frac": a / fp64_peak, "ms": c_ms,
-                                "work_note": "(8/3) n^3 flops per factorisation", "peak_note": fp64_note}
+        k["cholesky_of_S"] = {"role": "Cholesky of S and its inverse: blocked, 128-wide FP64 diagonal blocks "
+                                      "(chol_inv_kernel) and FP64-accurate tensor-core panels and updates",
+                              "bound": "mixed", "ms": c_ms, "fp64_equivalent_tflops": a,
+                              "dfma_peak": fp64_peak, "over_dfma_peak": a / fp64_peak,
+                              "work_note": "(8/3) n^3 flops per factorisation and inverse; above the DFMA peak "
+                                           "because most of it runs on the tensor cores"}
     roof = None
     hot = "tc_filter_step_kernel" if "tc_filter_step_kernel" in k else ("zgemm_kernel" if "zgemm_kernel" in k else None)
     if hot:
@@ -293,9 +300,31 @@ def kernel_rooflines(infos, n, fp64_peak):
 def kernel_case(args):
     """A few launches of one kernel on the benchmark's shapes (n = 2000, block 240), for
     profiling: --kernel-case filter (3 tensor-core filter steps), ozaki (one FP64-accurate
-    GEMM n x 240 x n), zgemm (the same GEMM on the FP64 pipe)."""
+    GEMM n x 240 x n), zgemm (the same GEMM on the FP64 pipe), sequence (the first
+    --case-problems problems of the n = 2000 sequence, mixed path: a launch list of the
+    whole solve)."""
     import torch
     from paper_1305_5120_gb300 import chfsi, synth
+    if args.kernel_case == "sequence":
+        w = synth.SEQ_N2000
+        Hs, S, X0 = make_inputs(w, w.seed)
+        ctx = chfsi.Context(device=0, precision=chfsi.CHFSI_PREC_MIXED)
+        evals = torch.empty(w.nev, dtype=torch.float64, device="cuda")
+        X = torch.empty((w.nev, w.n), dtype=torch.complex128, device="cuda")
+        sts = []
+        for l in range(args.case_problems):
+            Hd = chfsi.colmajor(Hs[l])
+            if l == 0:
+                st, *_ = ctx.solve(Hd, chfsi.colmajor(S), w.n, w.nev, w.nex, chfsi.colmajor(X0), w.tol, w.degree,
+                                   evals, X)
+            else:
+                st, *_ = ctx.next_in_sequence(Hd, None, evals, X)
+            sts.append(int(st))
+        torch.cuda.synchronize()
+        ctx.close()
+        print(json.dumps({"kernel_case": "sequence", "problems": args.case_problems, "status": sts,
+                          "launches": chfsi.kernel_launches()}))
+        return 0 if all(st == 0 for st in sts) else 1
     n, k = args.n, args.k
     ctx = chfsi.Context(device=0)
     rng = synth.rng_for(5, n)
@@ -417,7 +446,6 @@ def run_batch(args):
                 (args.check_inertia and infos[q].completeness != 2):
             wrong.append({"id": q, "status": int(sts[q]), "n": n, "nev": nev, "err": err,
                           "completeness": int(infos[q].completeness)})
-    stages = np.sum([list(i.ms_stage) for i in infos], axis=0).tolist()
     line = {"metric": METRIC, "value": len(probs) / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": 1,
             "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16x6+f64" if prec == chfsi.CHFSI_PREC_MIXED else "f64", "data": "synthetic",
@@ -427,8 +455,6 @@ def run_batch(args):
             "wall_s": wall, "wrong": len(wrong), "failures": wrong[:8], "gpu_launches": chfsi.kernel_launches() - launches0,
             "iterations": int(sum(i.iterations for i in infos)),
             "pairs_under_floor": int(sum(i.n_floor for i in infos)),
-            "stages_ms_summed": dict(zip(["reduce", "lanczos", "filter", "qr", "rayleigh_ritz", "residual_lock",
-                                          "back_transform", "total"], stages)),
             "eig": {"ms": float(sum(i.ms_eig for i in infos)), "refined": int(sum(i.eig_refined for i in infos)),
                     "fallbacks": int(sum(i.eig_fallbacks for i in infos))},
             "filter_steps_ms": float(sum(i.ms_filter_steps for i in infos)),
@@ -485,7 +511,9 @@ def run_large(args):
         row = {"step": l, "status": int(st), "ms": ms, "iterations": int(info.iterations),
                "completeness": int(info.completeness), "max_resid_floored": res, "s_orth": orth,
                "n_floor": int(info.n_floor), "filter_col_steps": int(info.filter_col_steps),
-               "eig_refined": int(info.eig_refined), "eig_fallbacks": int(info.eig_fallbacks)}
+               "eig_refined": int(info.eig_refined), "eig_fallbacks": int(info.eig_fallbacks),
+               "ms_eig": float(info.ms_eig), "ms_chol": float(info.ms_chol),
+               "stages_ms": dict(zip(STAGES, [float(x) for x in info.ms_stage]))}
         ev = evals.cpu().numpy()
         if l == 0:
             err = np.abs(ev - lam[:w.nev].cpu().numpy())
@@ -510,61 +538,108 @@ def run_large(args):
     return 0 if all(r["status"] == 0 for r in rows) else 1
 
 
-def run_serve(args):
-    """Serving (continuous batching) at a stated reduced scale of the sequence-serving
-    workload: args.serve_sequences k-point sequences of args.serve_steps correlated steps,
-    n log-uniform in [2000, args.serve_nmax], nev ~ U[3 %, 20 %] n, nex = 0.2 nev, Poisson
-    arrivals at args.serve_rate sequences/s (one seeded schedule), Ritz vectors and bounds kept
-    on the device between a sequence's steps, admission by HBM budget.  The mixed arm and the
-    plain-FP64 arm serve the same requests; eigenproblems/s, p50/p99 per-solve latency; every
-    result checked against its prescribed spectrum (step 0) and its floored residuals."""
-    import torch
-    from paper_1305_5120_gb300 import chfsi, serve, synth
+class _ServeSequence:
+    """One served sequence: step 0 is a structured pencil with a prescribed spectrum (built in
+    O(n^2 log n) on the device), step l > 0 is H_l = H_{l-1} + 1e-2 0.7^(l-1) E_l with S fixed,
+    each built when the server asks for it (the next H of an SCF cycle arriving), so that only
+    the active sequences hold matrices."""
+
+    def __init__(self, sid, n, nev, nex, steps, seed):
+        self.sid, self.n, self.nev, self.nex, self.steps, self.seed = sid, n, nev, nex, steps, seed
+        self.H = None
+        self.lam = None
+
+    def make_step(self, l):
+        from paper_1305_5120_gb300 import synth
+        if l == 0:
+            self.H, S, self.lam = synth.structured_pencil_device(self.n, self.nev, 80.0, self.seed)
+            return self.H, S
+        self.H = self.H + (1e-2 * 0.7 ** (l - 1)) * synth.structured_perturbation_device(self.n, self.seed, l - 1)
+        H = self.H
+        if l == self.steps - 1:
+            self.H = None
+        return H, None
+
+
+def _serve_arm(args, plan, prec, rate, label):
+    """Serve the sequences of `plan` (sid, n, nev, nex, steps) with Poisson arrivals at `rate`
+    sequences/s (seeded), `args.slots` concurrent contexts; every step checked."""
+    from paper_1305_5120_gb300 import serve
     rng = np.random.default_rng(11)
-    t = 0.0
-    seqs = []
-    for i in range(args.serve_sequences):
-        n = int(round(np.exp(rng.uniform(np.log(2000), np.log(args.serve_nmax)))))
-        nev = max(4, int(round(n * rng.uniform(0.03, 0.20))))
-        nex = max(2, int(round(0.2 * nev)))
-        H, S, lam = synth.prescribed_pencil_device(n, nev, 80.0, seed=500 + i)
-        Hs = [H]
-        for l in range(1, args.serve_steps):
-            Hs.append(Hs[-1] + (1e-2 * 0.7 ** (l - 1)) * synth.perturbation_device(n, 500 + i, l - 1))
-        t += float(rng.exponential(1.0 / args.serve_rate))
-        seqs.append((i, t, n, nev, nex, Hs, S, lam))
-    torch.cuda.synchronize()
+    t, reqs, seqs = 0.0, [], {}
+    for (sid, n, nev, nex, steps) in plan:
+        t += float(rng.exponential(1.0 / rate))
+        q = _ServeSequence(sid, n, nev, nex, steps, 500 + sid)
+        seqs[sid] = q
+        reqs.append(serve.SequenceRequest(seq_id=sid, arrival=t, n=n, nev=nev, nex=nex, steps=steps,
+                                          make_step=q.make_step, degree=20))
+    srv = serve.Server(device=0, slots=args.slots, keep_vectors=False, precision=prec,
+                       check_inertia=args.check_inertia)
+    t0 = time.perf_counter()
+    recs = srv.run(reqs, realtime=True)
+    wall = time.perf_counter() - t0
+    summ = serve.latency_summary(recs)
+    wrong, failures = 0, []
+    for r in recs:
+        q = seqs[r.seq_id]
+        bad = r.status != 0 or (args.check_inertia and r.info.get("completeness") != 2)
+        if not bad and r.step == 0:
+            lam = q.lam[:q.nev].cpu().numpy()
+            bad = np.abs(r.evals - lam).max() > 1e-10 * max(1.0, float(np.abs(lam).max()))
+        if bad:
+            wrong += 1
+            failures.append({"seq": r.seq_id, "step": r.step, "status": int(r.status), "n": q.n, "nev": q.nev,
+                             "iterations": r.info.get("iterations"), "completeness": r.info.get("completeness")})
+    expected = sum(p[4] for p in plan)
+    return dict(summ, label=label, expected_solves=expected, wrong=wrong, failures=failures, wall_s=wall,
+                pairs_under_floor=int(sum(r.info.get("n_floor", 0) for r in recs)),
+                iterations=int(sum(r.info.get("iterations", 0) for r in recs)))
 
-    def requests():
-        return [serve.SequenceRequest(seq_id=i, arrival=arr, n=n, nev=nev, nex=nex, steps=len(Hs),
-                                      make_step=lambda l, Hs=Hs, S=S: (Hs[l], S if l == 0 else None), degree=20)
-                for (i, arr, n, nev, nex, Hs, S, lam) in seqs]
 
-    arms = {}
-    for name, prec in (("mixed", chfsi.CHFSI_PREC_MIXED), ("fp64", chfsi.CHFSI_PREC_FP64)):
-        srv = serve.Server(device=0, slots=args.slots, keep_vectors=False, precision=prec)
-        recs = srv.run(requests(), realtime=True)
-        summ = serve.latency_summary(recs)
-        wrong = 0
-        for r in recs:
-            i, arr, n, nev, nex, Hs, S, lam = seqs[r.seq_id]
-            if r.status != 0:
-                wrong += 1
-            elif r.step == 0 and np.abs(r.evals - lam[:nev].cpu().numpy()).max() > 1e-10 * max(
-                    1.0, float(lam[:nev].abs().max())):
-                wrong += 1
-        arms[name] = dict(summ, wrong=wrong)
-    line = {"metric": METRIC, "value": arms["mixed"]["eigenproblems_per_s"], "unit": UNIT, "n_gpus": 1,
+def run_serve(args):
+    """Serving with continuous batching (the sequence-serving workload): args.serve_sequences
+    sequences of args.serve_steps correlated steps, n log-uniform in [2000, args.serve_nmax],
+    nev ~ U[3 %, 20 %] n, nex = 0.2 nev, Poisson arrivals at args.serve_rate sequences/s (one
+    seeded schedule), step l + 1 issued when step l completes, the Ritz block and bounds kept
+    on the device between a sequence's steps, admission by the HBM budget; mixed precision.
+    The plain-FP64 arm is too slow for that scale, so both arms also serve the same stated
+    subset (args.serve_cmp_sequences sequences of args.serve_cmp_steps steps, n log-uniform in
+    [2000, args.serve_cmp_nmax]): their ratio is the mixed/FP64 comparison.  Eigenproblems/s
+    over the served span and p50/p99 per-solve latency (ready -> done, building that step's
+    matrices included); every result checked (status, inertia count, step 0 against its
+    prescribed spectrum)."""
+    from paper_1305_5120_gb300 import chfsi
+    rng = np.random.default_rng(7)
+
+    def plan(count, steps, nmax):
+        out = []
+        for sid in range(count):
+            n = int(round(np.exp(rng.uniform(np.log(2000), np.log(nmax)))))
+            nev = max(4, int(round(n * rng.uniform(0.03, 0.20))))
+            out.append((sid, n, nev, max(2, int(round(0.2 * nev))), steps))
+        return out
+
+    full = plan(args.serve_sequences, args.serve_steps, args.serve_nmax)
+    sub = plan(args.serve_cmp_sequences, args.serve_cmp_steps, args.serve_cmp_nmax)
+    scale = _serve_arm(args, full, chfsi.CHFSI_PREC_MIXED, args.serve_rate, "mixed, full scale")
+    cmp_rate = args.serve_cmp_rate
+    cmp = {"mixed": _serve_arm(args, sub, chfsi.CHFSI_PREC_MIXED, cmp_rate, "mixed, comparison subset"),
+           "fp64": _serve_arm(args, sub, chfsi.CHFSI_PREC_FP64, cmp_rate, "fp64, comparison subset")}
+    line = {"metric": METRIC, "value": scale["eigenproblems_per_s"], "unit": UNIT, "n_gpus": 1,
             "steps": args.serve_steps, "warmup": 0, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16x6+f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "bf16x6+f64", "data": "synthetic (structured FFT-built pencils)",
             "config": {"workload": f"serving: {args.serve_sequences} sequences x {args.serve_steps} steps, n log-U"
                                    f"[2000,{args.serve_nmax}], nev 3-20% n, nex 0.2 nev, Poisson "
-                                   f"{args.serve_rate}/s, {args.slots} slots (reduced scale)"},
-            "arms": arms,
-            "mixed_over_fp64": (arms["mixed"]["eigenproblems_per_s"] / arms["fp64"]["eigenproblems_per_s"]
-                                if arms["fp64"]["eigenproblems_per_s"] else None)}
+                                   f"{args.serve_rate}/s, {args.slots} slots, check_inertia {args.check_inertia}",
+                       "n_range_served": [min(p[1] for p in full), max(p[1] for p in full)],
+                       "comparison_subset": f"{args.serve_cmp_sequences} sequences x {args.serve_cmp_steps} steps, "
+                                            f"n log-U[2000,{args.serve_cmp_nmax}], Poisson {cmp_rate}/s, both arms"},
+            "full_scale": scale, "comparison": cmp,
+            "mixed_over_fp64": (cmp["mixed"]["eigenproblems_per_s"] / cmp["fp64"]["eigenproblems_per_s"]
+                                if cmp["fp64"]["eigenproblems_per_s"] else None)}
     print(json.dumps(line), flush=True)
-    return 0 if all(a["wrong"] == 0 for a in arms.values()) else 1
+    ok = all(a["wrong"] == 0 and a["solves"] == a["expected_solves"] for a in [scale] + list(cmp.values()))
+    return 0 if ok else 1
 
 
 def config_dict(w, precision):
@@ -712,8 +787,7 @@ def run_ours(args):
                 "vs_baseline": None, "dtype": "f64" if prec == chfsi.CHFSI_PREC_FP64 else "bf16x6+f64",
                 "data": "synthetic", "config": config_dict(w, args.precision), "roofline": roof,
                 "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-                "stages_ms": dict(zip(["reduce", "lanczos", "filter", "qr", "rayleigh_ritz", "residual_lock",
-                                       "back_transform", "total"], stages)),
+                "stages_ms": dict(zip(STAGES, stages)),
                 "iterations": int(sum(i.iterations for _, i in infos)), "failed_solves": len(bad),
                 "eig_sweeps": int(sum(i.eig_sweeps for _, i in infos)),
                 "last_problem_max_resid": resid,
@@ -833,14 +907,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
-    ap.add_argument("--kernel-case", choices=["filter", "ozaki", "zgemm"], default=None)
+    ap.add_argument("--kernel-case", choices=["filter", "ozaki", "zgemm", "sequence"], default=None)
+    ap.add_argument("--case-problems", type=int, default=3, help="problems of the sequence kernel case")
     ap.add_argument("--workload", choices=["sequence", "kpoints", "batch", "large", "serve", "seeding"],
                     default="sequence")
     ap.add_argument("--large-steps", type=int, default=8)
-    ap.add_argument("--serve-sequences", type=int, default=6)
-    ap.add_argument("--serve-steps", type=int, default=3)
-    ap.add_argument("--serve-nmax", type=int, default=4000)
-    ap.add_argument("--serve-rate", type=float, default=2.0)
+    ap.add_argument("--serve-sequences", type=int, default=48)
+    ap.add_argument("--serve-steps", type=int, default=15)
+    ap.add_argument("--serve-nmax", type=int, default=8000)
+    ap.add_argument("--serve-rate", type=float, default=0.12, help="sequence arrivals per second")
+    ap.add_argument("--serve-cmp-sequences", type=int, default=4)
+    ap.add_argument("--serve-cmp-steps", type=int, default=3)
+    ap.add_argument("--serve-cmp-nmax", type=int, default=3000)
+    ap.add_argument("--serve-cmp-rate", type=float, default=0.5)
     ap.add_argument("--kpoints", type=int, default=64)
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--n", type=int, default=2000)

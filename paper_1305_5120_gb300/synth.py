@@ -188,3 +188,74 @@ def perturbation_device(n: int, seed: int, step: int, device="cuda"):
     E = (u * e[None, :]) @ u.conj().T
     return 0.5 * (E + E.conj().T)
 
+
+
+# Serving at scale (n up to 20000, hundreds of problems): the Haar recipe above costs O(n^3)
+# per matrix (a QR and dense products), minutes at n = 20000.  Here the unitaries are
+# structured, U = F D_b F D_a with F the unitary DFT and D_a, D_b diagonal matrices of random
+# phases (two layers of phases and Fourier transforms spread every basis vector over all
+# coordinates, as a Haar unitary does), and every matrix is formed by applying them to the
+# columns of a matrix with FFTs: O(n^2 log n).  The pencil keeps the same law otherwise --
+# S = V diag(s) V^H with cond(S) = 10 exactly, H = M W diag(lam) W^H M^H with M = V diag(sqrt(s))
+# -- so its eigenvalues are exactly lam (up to the FFTs' rounding, ~1e-15 relative).
+def _phases(n, gen, device):
+    import torch
+    t = torch.rand(n, generator=gen, device=device, dtype=torch.float64) * (2.0 * np.pi)
+    return torch.polar(torch.ones_like(t), t)
+
+
+class _FourierUnitary:
+    def __init__(self, n, gen, device):
+        self.da = _phases(n, gen, device)
+        self.db = _phases(n, gen, device)
+
+    def apply(self, x):        # U x for every column of x
+        import torch
+        y = torch.fft.fft(self.da[:, None] * x, dim=0, norm="ortho")
+        return torch.fft.fft(self.db[:, None] * y, dim=0, norm="ortho")
+
+    def apply_h(self, x):      # U^H x for every column of x
+        import torch
+        y = torch.conj(self.db)[:, None] * torch.fft.ifft(x, dim=0, norm="ortho")
+        return torch.conj(self.da)[:, None] * torch.fft.ifft(y, dim=0, norm="ortho")
+
+    def conjugate(self, d):    # U diag(d) U^H
+        import torch
+        eye = torch.eye(len(d), dtype=torch.complex128, device=d.device)
+        return self.apply(d[:, None] * self.apply_h(eye))
+
+
+def structured_pencil_device(n: int, n_low: int, high: float, seed: int, device="cuda", cond: float = 10.0):
+    """(H, S, lam) like `prescribed_pencil_device`, with structured unitaries (above):
+    O(n^2 log n) to build.  lam ascending, the exact eigenvalues of the pencil."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed) * 1000003 + 31)
+    v = _FourierUnitary(n, gen, device)
+    w = _FourierUnitary(n, gen, device)
+    g = torch.from_numpy(semicircle(rng_for(seed, 1), n)).to(device)
+    g[0], g[1] = -1.0, 1.0
+    t = (cond - 1.0) / (cond + 1.0)
+    s = (1.0 + t * g).to(torch.complex128)
+    S = v.conjugate(s)
+    S = 0.5 * (S + S.conj().T)
+    lam = torch.from_numpy(prescribed_spectrum(n, n_low, high, seed)).to(device)
+    C = w.conjugate(lam.to(torch.complex128))                 # W diag(lam) W^H
+    r = torch.sqrt(s)
+    T = r[:, None] * C * r[None, :]                           # diag(sqrt s) C diag(sqrt s)
+    del C
+    H = v.apply(torch.conj(v.apply(torch.conj(T).T)).T)       # V (V T^H)^H = V T V^H
+    H = 0.5 * (H + H.conj().T)
+    return H, S, lam
+
+
+def structured_perturbation_device(n: int, seed: int, step: int, device="cuda"):
+    """A Hermitian perturbation of unit 2-norm exactly, E = U diag(e) U^H with U structured."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed) * 1000003 + 7919 * (step + 1) + 37)
+    u = _FourierUnitary(n, gen, device)
+    e = semicircle(rng_for(seed, 100 + step), n)
+    e = torch.from_numpy(e / np.max(np.abs(e))).to(device).to(torch.complex128)
+    E = u.conjugate(e)
+    return 0.5 * (E + E.conj().T)

@@ -10,7 +10,14 @@ relative error (measured: error grows linearly with n), with a factor 2 for the 
 survive (normalised) to the output: tol = m * (2n / 16) * 2^-22 relative to the largest entry.
 
 The residual-corrected form (chfsi_filter_ritz) applies the products to D, of size
-||R|| / ||H Y|| relative to the block, so its error is that fraction of the plain bound."""
+||R|| / ||H Y|| relative to the block, so its error is that fraction of the plain bound.
+
+That bound is a worst case.  The measured errors (GB300, the cases below) stay at the level
+of ONE step's rounding, (2n / 16) 2^-24 relative, whatever m: the rounding injected at a step
+falls mostly on the damped part of the spectrum.  Each parity case therefore also asserts
+its measured error times 4, so that a regression of a few times shows up; the kernels are
+deterministic (both tile widths give bit-identical results), so the measured figure is
+reproducible."""
 import numpy as np
 import pytest
 
@@ -41,6 +48,22 @@ def tol_for(m, n):
     return max(m, 1) * (2 * n / 16) * 2.0 ** -22 + 1e-7
 
 
+# measured relative errors (largest entry) of the tensor-core filter against the oracle
+MEASURED_PLAIN = {
+    (128, 32): {1: 6.21e-7, 2: 6.38e-7, 20: 9.99e-7},
+    (200, 24): {1: 1.78e-6, 2: 1.68e-6, 20: 7.37e-7},
+    (333, 37): {1: 1.94e-6, 2: 2.12e-6, 20: 1.38e-6},
+    (512, 48): {1: 3.29e-6, 2: 4.63e-6, 20: 2.73e-6},
+    (130, 1): {1: 8.45e-7, 2: 8.33e-7, 20: 7.44e-6},
+    (1000, 121): {1: 6.61e-6, 2: 7.27e-6, 20: 3.91e-6},
+}
+MEASURED_RITZ = {
+    (200, 24): {1: 4.78e-9, 3: 3.10e-8, 20: 4.12e-8},
+    (512, 48): {1: 2.77e-8, 3: 1.52e-6, 20: 7.72e-7},
+    (1000, 121): {1: 2.75e-8, 3: 1.56e-6, 20: 3.04e-7},
+}
+
+
 @pytest.mark.parametrize("n,k", [(128, 32), (200, 24), (333, 37), (512, 48), (130, 1), (1000, 121)])
 @pytest.mark.parametrize("m", [1, 2, 20])
 def test_filter_mixed_vs_oracle(ctx, n, k, m):
@@ -52,6 +75,7 @@ def test_filter_mixed_vs_oracle(ctx, n, k, m):
     ref = O2.chebyshev_filter(H, Y0, m, a, b, a0)
     err = rel_err(lib.to_numpy(Y), ref)
     assert err < tol_for(m, n), err
+    assert err <= 4 * MEASURED_PLAIN[(n, k)][m], (err, MEASURED_PLAIN[(n, k)][m])
 
 
 def test_filter_mixed_per_vector_degree(ctx):
@@ -97,3 +121,4 @@ def test_filter_ritz_vs_oracle(ctx, n, k, m):
     ref = O2.chebyshev_filter(H, rY, m, a, b, a0)
     err = rel_err(lib.to_numpy(Y), ref)
     assert err < max(ratio, 1e-9) * tol_for(m, n) * 10 + 1e-12, (err, ratio)
+    assert err <= 4 * MEASURED_RITZ[(n, k)][m], (err, MEASURED_RITZ[(n, k)][m])
