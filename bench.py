@@ -780,6 +780,14 @@ def run_ours(args):
                "sample": "Cholesky + reduction + Lanczos + one outer iteration of problem 1 (FP64 oracle, "
                          "numpy BLAS threads = all cores); rate = 20/(t_chol + 20*(t_red+t_lz+t_iter)), "
                          "an upper bound", "parts": parts}
+        # how loose the bound is: the same rate at the outer-iteration count per problem this
+        # run's solves took (the oracle runs the same algorithm)
+        its = sum(i.iterations for _, i in infos) / max(1, len(infos))
+        pt = parts
+        cpu["estimate_at_measured_iterations"] = {
+            "iterations_per_problem": its,
+            "value": w.steps / (pt["t_cholesky_s"] + w.steps * (pt["t_reduce_s"] + pt["t_lanczos_s"] +
+                                                                 its * pt["t_iteration_s"]))}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -356,9 +356,19 @@ __device__ __forceinline__ int exp_of(double x) {   // smallest e with |x| < 2^e
 // (rows = false), op(X) being R x C: 32 x 32 tiles read along the contiguous dimension,
 // reduced with shared and global atomicMax (order-independent).  out[] starts at a large
 // negative sentinel (all-zero rows keep it).
-__global__ void exp_tile_kernel(int R, int C, const cplx* X, long ld, int op, bool rows, int* out) {
+struct ExpJob {
+  int R, C;
+  const cplx* X;
+  long ld;
+  int op;
+  bool rows;
+  int* out;
+  unsigned gx, gy;   // this job's grid
+};
+__device__ __forceinline__ void exp_tile(int R, int C, const cplx* X, long ld, int op, bool rows, int* out, int bx,
+                                         int by) {
   __shared__ int m[32];
-  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const int r0 = by * 32, c0 = bx * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   if (threadIdx.x < 32) m[threadIdx.x] = -100000;
   __syncthreads();
@@ -379,6 +389,12 @@ __global__ void exp_tile_kernel(int R, int C, const cplx* X, long ld, int op, bo
     const long idx = (rows ? r0 : c0) + threadIdx.x;
     if (m[threadIdx.x] > -100000 && idx < (rows ? R : C)) atomicMax(out + idx, m[threadIdx.x]);
   }
+}
+// Both operands' exponents in one launch: blockIdx.z picks the job (A's rows, B's columns).
+__global__ void exp_tile_kernel(ExpJob a, ExpJob b) {
+  const ExpJob& j = blockIdx.z == 0 ? a : b;
+  if (blockIdx.x >= j.gx || blockIdx.y >= j.gy) return;
+  exp_tile(j.R, j.C, j.X, j.ld, j.op, j.rows, j.out, blockIdx.x, blockIdx.y);
 }
 
 // Digits of x / 2^e (|x| < 2^e):  x = 2^e 2^-6 sum_s 2^(-5 s) d_s with |d_0| <= 64 and
@@ -424,10 +440,9 @@ __device__ __forceinline__ long tiled_off(long r, long k, int s, long kblocks) {
 
 // A digits: slice s, row r, columns 2c (Re) and 2c+1 (Im) of the real embedding; the tile is
 // staged through shared memory so that both the read (op-dependent) and the write coalesce.
-__global__ void slice_a_kernel(int M, int K, const cplx* A, long lda, int op, const int* rowexp, long mpad, long kpad,
-                               __nv_bfloat16* out) {
-  __shared__ cplx t[32][33];
-  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+__device__ __forceinline__ void slice_a(int M, int K, const cplx* A, long lda, int op, const int* rowexp, long mpad,
+                                        long kpad, __nv_bfloat16* out, cplx (*t)[33], int bx, int by) {
+  const int r0 = by * 32, c0 = bx * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
   for (int i = ty; i < 32; i += 8) {
     // element (r0 + a, c0 + b); read along the contiguous dimension
@@ -456,10 +471,9 @@ __global__ void slice_a_kernel(int M, int K, const cplx* A, long lda, int op, co
 }
 
 // B digits: op(B) is K x N; real B^T rows 2j = (Re b, -Im b), 2j+1 = (Im b, Re b) over k.
-__global__ void slice_b_kernel(int K, int N, const cplx* B, long ldb, int op, const int* colexp, long npad, long kpad,
-                               __nv_bfloat16* out) {
-  __shared__ cplx t[32][33];
-  const int j0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+__device__ __forceinline__ void slice_b(int K, int N, const cplx* B, long ldb, int op, const int* colexp, long npad,
+                                        long kpad, __nv_bfloat16* out, cplx (*t)[33], int bx, int by) {
+  const int j0 = by * 32, k0 = bx * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int i = ty; i < 32; i += 8) {
     int a, b;   // a: k offset, b: j offset
@@ -484,6 +498,28 @@ __global__ void slice_b_kernel(int K, int N, const cplx* B, long ldb, int op, co
       *(__nv_bfloat162*)(out + tiled_off<BN>(2 * j, 2 * kk, s, kpad / BK)) = p0;
       *(__nv_bfloat162*)(out + tiled_off<BN>(2 * j + 1, 2 * kk, s, kpad / BK)) = p1;
     }
+  }
+}
+
+struct SliceArgs {
+  int M, N, K;
+  const cplx *A, *B;
+  long lda, ldb;
+  int opA, opB;
+  const int *rowexp, *colexp;
+  long mpad, npad, kpad;
+  __nv_bfloat16 *outA, *outB;
+  unsigned gxa, gya, gxb, gyb;
+};
+// Both operands' digit tiles in one launch: blockIdx.z = 0 slices A, 1 slices B.
+__global__ void slice_kernel(SliceArgs g) {
+  __shared__ cplx t[32][33];
+  if (blockIdx.z == 0) {
+    if (blockIdx.x >= g.gxa || blockIdx.y >= g.gya) return;
+    slice_a(g.M, g.K, g.A, g.lda, g.opA, g.rowexp, g.mpad, g.kpad, g.outA, t, blockIdx.x, blockIdx.y);
+  } else {
+    if (blockIdx.x >= g.gxb || blockIdx.y >= g.gyb) return;
+    slice_b(g.K, g.N, g.B, g.ldb, g.opB, g.colexp, g.npad, g.kpad, g.outB, t, blockIdx.x, blockIdx.y);
   }
 }
 
@@ -564,19 +600,36 @@ cudaError_t ozaki_gemm(OzakiGemm* o, const GemmArgs& g, cudaStream_t s, int* err
   // exponents: rows of op(A), columns of op(B) (sentinel 0x80808080 = very negative)
   if ((e = cudaMemsetAsync(o->exps, 0x80, sizeof(int) * (M + N), s)) != cudaSuccess) return e;
   {
-    dim3 gA((unsigned)((K + 31) / 32), (unsigned)((M + 31) / 32));
-    exp_tile_kernel<<<gA, 256, 0, s>>>((int)M, (int)K, g.A, g.lda, g.opA, true, rowexp);
-    count_launch(1);
-    dim3 gB((unsigned)((N + 31) / 32), (unsigned)((K + 31) / 32));
-    exp_tile_kernel<<<gB, 256, 0, s>>>((int)K, (int)N, g.B, g.ldb, g.opB, false, colexp);
+    ExpJob ja{(int)M, (int)K, g.A, g.lda, g.opA, true, rowexp, (unsigned)((K + 31) / 32), (unsigned)((M + 31) / 32)};
+    ExpJob jb{(int)K, (int)N, g.B, g.ldb, g.opB, false, colexp, (unsigned)((N + 31) / 32), (unsigned)((K + 31) / 32)};
+    dim3 grid(std::max(ja.gx, jb.gx), std::max(ja.gy, jb.gy), 2);
+    exp_tile_kernel<<<grid, 256, 0, s>>>(ja, jb);
     count_launch(1);
   }
   {
-    dim3 ga((unsigned)((kpad / 2 + 31) / 32), (unsigned)(mpad / 32));
-    slice_a_kernel<<<ga, 256, 0, s>>>((int)M, (int)K, g.A, g.lda, g.opA, rowexp, mpad, kpad, o->A);
-    count_launch(1);
-    dim3 gb((unsigned)((kpad / 2 + 31) / 32), (unsigned)((npad / 2 + 31) / 32));
-    slice_b_kernel<<<gb, 256, 0, s>>>((int)K, (int)N, g.B, g.ldb, g.opB, colexp, npad, kpad, o->B);
+    SliceArgs sa{};
+    sa.M = (int)M;
+    sa.N = (int)N;
+    sa.K = (int)K;
+    sa.A = g.A;
+    sa.B = g.B;
+    sa.lda = g.lda;
+    sa.ldb = g.ldb;
+    sa.opA = g.opA;
+    sa.opB = g.opB;
+    sa.rowexp = rowexp;
+    sa.colexp = colexp;
+    sa.mpad = mpad;
+    sa.npad = npad;
+    sa.kpad = kpad;
+    sa.outA = o->A;
+    sa.outB = o->B;
+    sa.gxa = (unsigned)((kpad / 2 + 31) / 32);
+    sa.gya = (unsigned)(mpad / 32);
+    sa.gxb = (unsigned)((kpad / 2 + 31) / 32);
+    sa.gyb = (unsigned)((npad / 2 + 31) / 32);
+    dim3 grid(std::max(sa.gxa, sa.gxb), std::max(sa.gya, sa.gyb), 2);
+    slice_kernel<<<grid, 256, 0, s>>>(sa);
     count_launch(1);
   }
   const int kblocks = (int)(kpad / BK);
