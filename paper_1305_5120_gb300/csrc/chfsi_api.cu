@@ -1001,6 +1001,7 @@ chfsi_status reduced_eig_refined(chfsi_ctx* c, int k, const cplx* G, double* lam
   c->spans_off = true;   // the products below belong to the eigensolver's span
   chfsi_status st = CHFSI_OK;
   bool conv = false;
+  const char* why = "iterations";
   int it = 0;
   for (; it < max_iter; ++it) {
     st = gemm64(c, gemm_args(k, k, k, OP_N, G, k, OP_N, X, k, GX, k, ONE, ZERO));
@@ -1021,19 +1022,28 @@ chfsi_status reduced_eig_refined(chfsi_ctx* c, int k, const cplx* G, double* lam
     offmax = sqrt(offmax);
     rmax = sqrt(rmax);
     fcorr = sqrt(fcorr);
-    if (herr != DEV_OK || !std::isfinite(offmax) || !std::isfinite(rmax) || offmax > 1e-2 * hfro) break;
+    if (herr != DEV_OK || !std::isfinite(offmax) || !std::isfinite(rmax) || offmax > 1e-2 * hfro) {
+      why = "growth";
+      break;
+    }
     if (offmax <= 8.0 * eps * hfro && rmax <= 8.0 * eps) {
       conv = true;
       break;
     }
-    if (hn > cap) break;
+    if (hn > cap) {
+      why = "pairs";
+      break;
+    }
     hp.resize(hn);
     if (hn > 0) {
       CU(cudaMemcpyAsync(hp.data(), pairs, sizeof(int2) * hn, cudaMemcpyDeviceToHost, c->stream));
       CU(cudaStreamSynchronize(c->stream));
     }
     make_groups(k, hp, &gr);
-    if (gr.largest > OA_GROUP_MAX) break;
+    if (gr.largest > OA_GROUP_MAX) {
+      why = "group";
+      break;
+    }
     const int ngroups = (int)gr.voff.size();
     cplx* XUp = XU;
     if (ngroups > 0) {
@@ -1079,6 +1089,9 @@ chfsi_status reduced_eig_refined(chfsi_ctx* c, int k, const cplx* G, double* lam
   c->acc_eig_f32_sweeps += hsweeps;
   c->acc_eig_iters += it + (conv ? 1 : 0);
   if (st != CHFSI_OK) return st;
+  if (!conv && getenv("CHFSI_DEBUG_EIG"))   // diagnostics: why the refinement handed over
+    fprintf(stderr, "chfsi: reduced eigensolver fallback k=%d reason=%s iteration=%d fp32_sweeps=%d\n", k,
+            why, it, hsweeps);
   if (!conv) {
     ++c->acc_eig_fallbacks;
     return CHFSI_OK;
