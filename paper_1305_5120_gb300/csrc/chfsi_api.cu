@@ -1089,9 +1089,9 @@ chfsi_status reduced_eig_refined(chfsi_ctx* c, int k, const cplx* G, double* lam
   c->acc_eig_f32_sweeps += hsweeps;
   c->acc_eig_iters += it + (conv ? 1 : 0);
   if (st != CHFSI_OK) return st;
-  if (!conv && getenv("CHFSI_DEBUG_EIG"))   // diagnostics: why the refinement handed over
-    fprintf(stderr, "chfsi: reduced eigensolver fallback k=%d reason=%s iteration=%d fp32_sweeps=%d\n", k,
-            why, it, hsweeps);
+  if (getenv("CHFSI_DEBUG_EIG"))   // diagnostics: sweeps, iterations and why the refinement handed over
+    fprintf(stderr, "chfsi: reduced eigensolver k=%d fp32_sweeps=%d iterations=%d groups_max=%d %s%s\n", k, hsweeps,
+            it + (conv ? 1 : 0), gr.largest, conv ? "converged" : "fallback reason=", conv ? "" : why);
   if (!conv) {
     ++c->acc_eig_fallbacks;
     return CHFSI_OK;
