@@ -27,6 +27,8 @@
 
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "eigen.cuh"
 
 void count_launch(unsigned long long n);
@@ -234,6 +236,119 @@ __global__ void __launch_bounds__(OS_THREADS, 1) os_jacobi_kernel(OsArgs g) {
     *g.sweeps = sweep;
     if (!done) atomicExch(g.err, DEV_ERR_NO_CONV);
   }
+}
+
+// The same sweeps with the columns resident in the cluster's shared memory (k up to a few
+// hundred): worker j (warp j % W of CTA j / W) owns the two positions j and kk-1-j of the
+// round-robin schedule and keeps their columns in its CTA's shared memory.  In a round it
+// rotates its pair in place, then moves its two columns to the positions they occupy in the
+// next round (position x + 1 -> x, position 1 -> kk - 1, position 0 fixed): into a
+// neighbour's slot of the other buffer, in the same CTA or through distributed shared memory;
+// one cluster barrier per round and no global-memory round trip.  After a whole sweep every
+// column is back at its own position.  A sweep that rotates nothing ends the iteration (a
+// rotation-free sweep costs kk - 1 barriers here).
+__global__ void __launch_bounds__(OS_THREADS, 1) os_dsmem_kernel(OsArgs g, int W) {
+  extern __shared__ float2 sm[];   // [2 buffers][W workers][2 slots][k]
+  __shared__ int s_rot;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int k = g.k, kk = g.kk, np = kk / 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rank = (int)cl.block_rank();
+  const int j = rank * W + warp;
+  const bool active = j < np;
+  auto slotp = [&](int buf, int w, int h) { return sm + (((long)buf * W + w) * 2 + h) * k; };
+  auto remote = [&](int buf, int t, int h) { return cl.map_shared_rank(slotp(buf, t % W, h), t / W); };
+  if (active) {
+    for (int h = 0; h < 2; ++h) {
+      const int c = h == 0 ? j : kk - 1 - j;
+      float2* d = slotp(0, warp, h);
+      for (int i = lane; i < k; i += 32) d[i] = c < k ? __ldcg(g.B + (long)c * k + i) : make_float2(0.f, 0.f);
+    }
+  }
+  if (threadIdx.x == 0) s_rot = 0;
+  cluster_sync_all();
+  int cur = 0, sweep = 0;
+  bool done = false;
+  for (; sweep < g.max_sweeps && !done; ++sweep) {
+    for (int r = 0; r < kk - 1; ++r) {
+      if (active) {
+        int p = slot(j, r, kk), q = slot(kk - 1 - j, r, kk);
+        float2* xp = slotp(cur, warp, 0);
+        float2* xq = slotp(cur, warp, 1);
+        if (p > q) {
+          const int t = p; p = q; q = t;
+          float2* u = xp; xp = xq; xq = u;
+        }
+        if (q < k) {
+          float a = 0.f, b = 0.f, gr = 0.f, gi = 0.f;
+          for (int i = lane; i < k; i += 32) {
+            const float2 x = xp[i], y = xq[i];
+            a = fmaf(x.x, x.x, fmaf(x.y, x.y, a));
+            b = fmaf(y.x, y.x, fmaf(y.y, y.y, b));
+            gr = fmaf(x.x, y.x, fmaf(x.y, y.y, gr));    // conj(x) y
+            gi = fmaf(x.x, y.y, fmaf(-x.y, y.x, gi));
+          }
+          a = warp_sumf(a);
+          b = warp_sumf(b);
+          gr = warp_sumf(gr);
+          gi = warp_sumf(gi);
+          const float ag = sqrtf(fmaf(gr, gr, gi * gi));
+          if (ag > g.tol * sqrtf(a * b)) {   // warp-uniform
+            const float phr = gr / ag, phi = gi / ag;
+            const float tau = (b - a) / (2.f * ag);
+            const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
+            const float c = rsqrtf(fmaf(t, t, 1.f)), sn = t * c;
+            for (int i = lane; i < k; i += 32) {
+              const float2 x = xp[i], y = xq[i];
+              const float wr = fmaf(phr, y.x, phi * y.y), wi = fmaf(phr, y.y, -phi * y.x);   // conj(ph) y
+              xp[i] = make_float2(fmaf(c, x.x, -sn * wr), fmaf(c, x.y, -sn * wi));
+              xq[i] = make_float2(fmaf(sn, x.x, c * wr), fmaf(sn, x.y, c * wi));
+            }
+            if (lane == 0) atomicAdd(&s_rot, 1);
+          }
+        }
+        // move to the next round's positions (each target slot receives exactly one column)
+        const float2* f = slotp(cur, warp, 0);
+        const float2* sc = slotp(cur, warp, 1);
+        float2* df;
+        float2* ds;
+        if (np == 1) {
+          df = slotp(cur ^ 1, warp, 0);
+          ds = slotp(cur ^ 1, warp, 1);
+        } else {
+          df = j == 0 ? slotp(cur ^ 1, warp, 0) : (j == 1 ? remote(cur ^ 1, 0, 1) : remote(cur ^ 1, j - 1, 0));
+          ds = j < np - 1 ? remote(cur ^ 1, j + 1, 1) : slotp(cur ^ 1, warp, 0);
+        }
+        for (int i = lane; i < k; i += 32) {
+          df[i] = f[i];
+          ds[i] = sc[i];
+        }
+      }
+      cluster_sync_all();
+      cur ^= 1;
+    }
+    // every CTA adds its count; after the barrier all read the same total
+    if (threadIdx.x == 0 && s_rot) atomicAdd(&g.rot_count[sweep], s_rot);
+    cluster_sync_all();
+    done = *(volatile int*)&g.rot_count[sweep] == 0;
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+  }
+  // after whole sweeps every column is at its own position: worker j holds columns j, kk-1-j
+  if (active) {
+    for (int h = 0; h < 2; ++h) {
+      const int c = h == 0 ? j : kk - 1 - j;
+      if (c >= k) continue;
+      const float2* src = slotp(cur, warp, h);
+      for (int i = lane; i < k; i += 32) __stcg(g.B + (long)c * k + i, src[i]);
+    }
+  }
+  if (rank == 0 && threadIdx.x == 0) {
+    *g.sweeps = sweep;
+    if (!done) atomicExch(g.err, DEV_ERR_NO_CONV);
+  }
+  cluster_sync_all();   // no CTA leaves while a peer could still address its shared memory
 }
 
 // B = G + s I in FP32 (rounded to nearest)
@@ -523,6 +638,42 @@ cudaError_t os_jacobi_f32(cudaStream_t s, int k, const cplx* G, double shift, fl
   a.rot_count = counters;
   a.sweeps = sweeps;
   a.err = err;
+  // columns resident in the cluster's shared memory when two buffers of every worker's two
+  // columns fit (k up to ~450 on 16 CTAs)
+  static int nc_ds_ok = 0;
+  for (int nc : {16, 8}) {
+    if (nc_ds_ok && nc > nc_ds_ok) continue;
+    const int np = a.kk / 2, W = (np + nc - 1) / nc;
+    const size_t smem = sizeof(float2) * 4 * (size_t)W * k;
+    if (W > OS_WARPS || smem > 200 * 1024) continue;
+    if (nc == 16) cudaFuncSetAttribute(os_dsmem_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(os_dsmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nc);
+    cfg.blockDim = dim3(32 * W);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = nc;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, os_dsmem_kernel, &cfg) != cudaSuccess || nclusters < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    e = cudaLaunchKernelEx(&cfg, os_dsmem_kernel, a, W);
+    count_launch(1);
+    if (e == cudaSuccess) {
+      nc_ds_ok = nc;
+      if (cluster_used) *cluster_used = nc;
+      return cudaSuccess;
+    }
+    cudaGetLastError();
+  }
   for (int nc : {16, 8}) {
     if (nc_ok && nc > nc_ok) continue;
     if (nc == 16) cudaFuncSetAttribute(os_jacobi_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
