@@ -933,7 +933,7 @@ void make_groups(int k, const std::vector<int2>& pairs, Groups* g) {
 
 chfsi_status reduced_eig_refined(chfsi_ctx* c, int k, const cplx* G, double* lam, cplx* W, bool* done) {
   *done = false;
-  const int max_sweeps = 24, max_iter = 12, cap = 4096;
+  const int max_sweeps = 24, max_iter = 24, cap = 4096;
   const double tau = 0.05;
   float2* B;
   int* cnt;

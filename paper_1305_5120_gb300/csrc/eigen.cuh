@@ -3,7 +3,7 @@
 #pragma once
 #include "common.cuh"
 
-constexpr int OA_GROUP_MAX = 16;   // largest group of strongly coupled pairs solved exactly
+constexpr int OA_GROUP_MAX = 32;   // largest group of strongly coupled pairs solved exactly
 
 // B = G + shift I (FP32), then one-sided Jacobi on B's columns until no pair is above the
 // threshold (|x^H y| <= tol ||x|| ||y||, checked by a scan before each sweep) or max_sweeps
