@@ -945,7 +945,7 @@ chfsi_status reduced_eig_refined(chfsi_ctx* c, int k, const cplx* G, double* lam
   TRY(buf(c, "eo_B", (size_t)k * k, &B));
   TRY(buf(c, "eo_cnt", max_sweeps + 1, &cnt));
   float* nrm;
-  TRY(buf(c, "eo_nrm", k, &nrm));
+  TRY(buf(c, "eo_nrm", std::max(k, max_sweeps + 1), &nrm));
   TRY(buf(c, "eo_P", (size_t)2 * k * k, &P));
   TRY(buf(c, "eo_T", (size_t)2 * k * k, &T));
   TRY(buf(c, "eo_R", (size_t)k * k, &R));

@@ -24,6 +24,7 @@
 // Host orchestration (the products, the convergence test and the fallback to the FP64 Jacobi
 // of jacobi.cu) is in chfsi_api.cu.
 #include <math.h>
+#include <stdlib.h>
 
 #include <algorithm>
 
@@ -245,11 +246,16 @@ __global__ void __launch_bounds__(OS_THREADS, 1) os_jacobi_kernel(OsArgs g) {
 // next round (position x + 1 -> x, position 1 -> kk - 1, position 0 fixed): into a
 // neighbour's slot of the other buffer, in the same CTA or through distributed shared memory;
 // one cluster barrier per round and no global-memory round trip.  After a whole sweep every
-// column is back at its own position.  A sweep that rotates nothing ends the iteration (a
-// rotation-free sweep costs kk - 1 barriers here).
+// column is back at its own position.  The iteration ends after a sweep that rotates
+// nothing, or after one whose largest relative coupling |x^H y| / (||x|| ||y||) was at most
+// OS_QUAD: Jacobi converges quadratically, so what remains is of order OS_QUAD^2, about the
+// rotation threshold -- and the FP64 refinement that follows removes any remainder -- so the
+// rotation-free confirming sweep is saved.
+constexpr float OS_QUAD = 1e-3f;
 __global__ void __launch_bounds__(OS_THREADS, 1) os_dsmem_kernel(OsArgs g, int W) {
   extern __shared__ float2 sm[];   // [2 buffers][W workers][2 slots][k]
   __shared__ int s_rot;
+  __shared__ float s_rel;
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int k = g.k, kk = g.kk, np = kk / 2;
@@ -266,7 +272,10 @@ __global__ void __launch_bounds__(OS_THREADS, 1) os_dsmem_kernel(OsArgs g, int W
       for (int i = lane; i < k; i += 32) d[i] = c < k ? __ldcg(g.B + (long)c * k + i) : make_float2(0.f, 0.f);
     }
   }
-  if (threadIdx.x == 0) s_rot = 0;
+  if (threadIdx.x == 0) {
+    s_rot = 0;
+    s_rel = 0.f;
+  }
   cluster_sync_all();
   int cur = 0, sweep = 0;
   bool done = false;
@@ -294,7 +303,8 @@ __global__ void __launch_bounds__(OS_THREADS, 1) os_dsmem_kernel(OsArgs g, int W
           gr = warp_sumf(gr);
           gi = warp_sumf(gi);
           const float ag = sqrtf(fmaf(gr, gr, gi * gi));
-          if (ag > g.tol * sqrtf(a * b)) {   // warp-uniform
+          const float nab = sqrtf(a * b);
+          if (ag > g.tol * nab) {   // warp-uniform
             const float phr = gr / ag, phi = gi / ag;
             const float tau = (b - a) / (2.f * ag);
             const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
@@ -305,7 +315,11 @@ __global__ void __launch_bounds__(OS_THREADS, 1) os_dsmem_kernel(OsArgs g, int W
               xp[i] = make_float2(fmaf(c, x.x, -sn * wr), fmaf(c, x.y, -sn * wi));
               xq[i] = make_float2(fmaf(sn, x.x, c * wr), fmaf(sn, x.y, c * wi));
             }
-            if (lane == 0) atomicAdd(&s_rot, 1);
+            if (lane == 0) {
+              atomicAdd(&s_rot, 1);
+              // non-negative floats order like their bit patterns
+              atomicMax((int*)&s_rel, __float_as_int(fminf(ag / nab, 1.f)));
+            }
           }
         }
         // move to the next round's positions (each target slot receives exactly one column)
@@ -328,11 +342,18 @@ __global__ void __launch_bounds__(OS_THREADS, 1) os_dsmem_kernel(OsArgs g, int W
       cluster_sync_all();
       cur ^= 1;
     }
-    // every CTA adds its count; after the barrier all read the same total
-    if (threadIdx.x == 0 && s_rot) atomicAdd(&g.rot_count[sweep], s_rot);
+    // every CTA adds its count and its largest coupling; after the barrier all read the totals
+    if (threadIdx.x == 0 && s_rot) {
+      atomicAdd(&g.rot_count[sweep], s_rot);
+      atomicMax((int*)g.nrm + sweep, __float_as_int(s_rel));
+    }
     cluster_sync_all();
-    done = *(volatile int*)&g.rot_count[sweep] == 0;
-    if (threadIdx.x == 0) s_rot = 0;
+    done = *(volatile int*)&g.rot_count[sweep] == 0 ||
+           __int_as_float(*((volatile int*)g.nrm + sweep)) <= OS_QUAD;
+    if (threadIdx.x == 0) {
+      s_rot = 0;
+      s_rel = 0.f;
+    }
     __syncthreads();
   }
   // after whole sweeps every column is at its own position: worker j holds columns j, kk-1-j
@@ -641,8 +662,15 @@ cudaError_t os_jacobi_f32(cudaStream_t s, int k, const cplx* G, double shift, fl
   // columns resident in the cluster's shared memory when two buffers of every worker's two
   // columns fit (k up to ~450 on 16 CTAs)
   static int nc_ds_ok = 0;
+  static const int nc_env = [] {
+    const char* v = getenv("CHFSI_OS_CLUSTER");   // 8 or 16: the cluster size (default: 16 when allowed)
+    return v ? atoi(v) : 0;
+  }();
+  e = cudaMemsetAsync(nrm, 0, sizeof(float) * (max_sweeps + 1), s);   // per-sweep largest coupling
+  if (e != cudaSuccess) return e;
   for (int nc : {16, 8}) {
     if (nc_ds_ok && nc > nc_ds_ok) continue;
+    if (nc_env && nc != nc_env) continue;
     const int np = a.kk / 2, W = (np + nc - 1) / nc;
     const size_t smem = sizeof(float2) * 4 * (size_t)W * k;
     if (W > OS_WARPS || smem > 200 * 1024) continue;

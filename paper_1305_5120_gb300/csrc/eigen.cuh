@@ -6,10 +6,12 @@
 constexpr int OA_GROUP_MAX = 32;   // largest group of strongly coupled pairs solved exactly
 
 // B = G + shift I (FP32), then one-sided Jacobi on B's columns until no pair is above the
-// threshold (|x^H y| <= tol ||x|| ||y||, checked by a scan before each sweep) or max_sweeps
-// sweeps ran: on return B = W, whose columns are multiples of eigenvectors.  nrm: k floats
-// of scratch; counters: max_sweeps + 1 ints (zeroed here); *sweeps the rotating sweeps run;
-// *err DEV_ERR_NO_CONV if max_sweeps ran out.  *cluster_used: CTAs in the cluster.
+// threshold (|x^H y| <= tol ||x|| ||y||) or, with the columns in the cluster's shared memory
+// (k up to ~450), until a sweep's largest coupling is of the order sqrt(threshold); at most
+// max_sweeps sweeps.  On return B = W, whose columns are multiples of eigenvectors.  nrm:
+// max(k, max_sweeps + 1) floats of scratch; counters: max_sweeps + 1 ints (zeroed here);
+// *sweeps the sweeps run; *err DEV_ERR_NO_CONV if max_sweeps ran out.  *cluster_used: CTAs in
+// the cluster (CHFSI_OS_CLUSTER = 8 or 16 picks it; by default 16 where the device allows it).
 cudaError_t os_jacobi_f32(cudaStream_t s, int k, const cplx* G, double shift, float2* B, float* nrm, int* counters,
                           int max_sweeps, float tol, int* err, int* sweeps, int* cluster_used);
 // X = the columns of W normalised (FP64).
