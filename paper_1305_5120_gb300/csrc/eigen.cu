@@ -46,6 +46,28 @@ __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// mbarriers in shared memory, signalled from other CTAs of the cluster
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_cluster(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+constexpr long OS_WAIT_LIMIT = 1L << 22;
+
 __device__ __forceinline__ float warp_sumf(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -245,17 +267,24 @@ __global__ void __launch_bounds__(OS_THREADS, 1) os_jacobi_kernel(OsArgs g) {
 // rotates its pair in place, then moves its two columns to the positions they occupy in the
 // next round (position x + 1 -> x, position 1 -> kk - 1, position 0 fixed): into a
 // neighbour's slot of the other buffer, in the same CTA or through distributed shared memory;
-// one cluster barrier per round and no global-memory round trip.  After a whole sweep every
-// column is back at its own position.  The iteration ends after a sweep that rotates
+// no global-memory round trip.  A worker depends only on the two workers whose columns it
+// receives, so instead of a cluster-wide barrier per round each worker has one mbarrier per
+// buffer that completes when both of its incoming columns have been written (the senders
+// store through distributed shared memory, then arrive with release semantics); waits are
+// bounded.  After a whole sweep every column is back at its own position; the rotation count
+// of a sweep is gathered with one cluster barrier.  The iteration ends after a sweep that rotates
 // nothing, or after one whose largest relative coupling |x^H y| / (||x|| ||y||) was at most
 // OS_QUAD: Jacobi converges quadratically, so what remains is of order OS_QUAD^2, about the
 // rotation threshold -- and the FP64 refinement that follows removes any remainder -- so the
 // rotation-free confirming sweep is saved.
 constexpr float OS_QUAD = 1e-3f;
 __global__ void __launch_bounds__(OS_THREADS, 1) os_dsmem_kernel(OsArgs g, int W) {
-  extern __shared__ float2 sm[];   // [2 buffers][W workers][2 slots][k]
+  extern __shared__ uint64_t dyn[];   // mbarriers [2 buffers][W workers], then the columns
+  uint64_t* bars = dyn;
+  float2* sm = (float2*)(dyn + 2 * W);   // [2 buffers][W workers][2 slots][k]
   __shared__ int s_rot;
   __shared__ float s_rel;
+  __shared__ int s_timeout;
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int k = g.k, kk = g.kk, np = kk / 2;
@@ -265,6 +294,14 @@ __global__ void __launch_bounds__(OS_THREADS, 1) os_dsmem_kernel(OsArgs g, int W
   const bool active = j < np;
   auto slotp = [&](int buf, int w, int h) { return sm + (((long)buf * W + w) * 2 + h) * k; };
   auto remote = [&](int buf, int t, int h) { return cl.map_shared_rank(slotp(buf, t % W, h), t / W); };
+  // worker t's barrier for buffer `buf`, as a cluster address: it completes a phase when both
+  // of t's slots of that buffer have been written (two arrivals)
+  auto bar_of = [&](int buf, int t) { return cluster_addr(smem_addr(bars + buf * W + t % W), t / W); };
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2 * W; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(smem_addr(bars + b)));
+    s_timeout = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   if (active) {
     for (int h = 0; h < 2; ++h) {
       const int c = h == 0 ? j : kk - 1 - j;
@@ -278,10 +315,25 @@ __global__ void __launch_bounds__(OS_THREADS, 1) os_dsmem_kernel(OsArgs g, int W
   }
   cluster_sync_all();
   int cur = 0, sweep = 0;
+  long rg = 0;   // rounds run so far (over all sweeps)
   bool done = false;
   for (; sweep < g.max_sweeps && !done; ++sweep) {
-    for (int r = 0; r < kk - 1; ++r) {
+    for (int r = 0; r < kk - 1; ++r, ++rg) {
       if (active) {
+        // this round's two columns were written by the neighbours at the end of the last one
+        if (rg > 0) {
+          if (lane == 0 && !*(volatile int*)&s_timeout) {
+            const uint32_t bar = smem_addr(bars + cur * W + warp);
+            const uint32_t par = (uint32_t)((rg - 1) >> 1) & 1u;
+            long it = 0;
+            while (!mbar_try_cluster(bar, par) && ++it < OS_WAIT_LIMIT) {}
+            if (it >= OS_WAIT_LIMIT) {   // bounded: record and stop waiting (the refinement rejects the result)
+              s_timeout = 1;
+              atomicExch(g.err, DEV_ERR_TIMEOUT);
+            }
+          }
+          __syncwarp();
+        }
         int p = slot(j, r, kk), q = slot(kk - 1 - j, r, kk);
         float2* xp = slotp(cur, warp, 0);
         float2* xq = slotp(cur, warp, 1);
@@ -327,10 +379,14 @@ __global__ void __launch_bounds__(OS_THREADS, 1) os_dsmem_kernel(OsArgs g, int W
         const float2* sc = slotp(cur, warp, 1);
         float2* df;
         float2* ds;
+        int tf, ts;   // receiving workers
         if (np == 1) {
           df = slotp(cur ^ 1, warp, 0);
           ds = slotp(cur ^ 1, warp, 1);
+          tf = ts = j;
         } else {
+          tf = j == 0 ? 0 : (j == 1 ? 0 : j - 1);
+          ts = j < np - 1 ? j + 1 : j;
           df = j == 0 ? slotp(cur ^ 1, warp, 0) : (j == 1 ? remote(cur ^ 1, 0, 1) : remote(cur ^ 1, j - 1, 0));
           ds = j < np - 1 ? remote(cur ^ 1, j + 1, 1) : slotp(cur ^ 1, warp, 0);
         }
@@ -338,8 +394,14 @@ __global__ void __launch_bounds__(OS_THREADS, 1) os_dsmem_kernel(OsArgs g, int W
           df[i] = f[i];
           ds[i] = sc[i];
         }
+        // the copies are visible to the receivers before their barriers are signalled
+        asm volatile("fence.acq_rel.cluster;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive_cluster(bar_of(cur ^ 1, tf));
+          mbar_arrive_cluster(bar_of(cur ^ 1, ts));
+        }
       }
-      cluster_sync_all();
       cur ^= 1;
     }
     // every CTA adds its count and its largest coupling; after the barrier all read the totals
@@ -672,7 +734,7 @@ cudaError_t os_jacobi_f32(cudaStream_t s, int k, const cplx* G, double shift, fl
     if (nc_ds_ok && nc > nc_ds_ok) continue;
     if (nc_env && nc != nc_env) continue;
     const int np = a.kk / 2, W = (np + nc - 1) / nc;
-    const size_t smem = sizeof(float2) * 4 * (size_t)W * k;
+    const size_t smem = sizeof(uint64_t) * 2 * (size_t)W + sizeof(float2) * 4 * (size_t)W * k;
     if (W > OS_WARPS || smem > 200 * 1024) continue;
     if (nc == 16) cudaFuncSetAttribute(os_dsmem_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaFuncSetAttribute(os_dsmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
