@@ -274,10 +274,10 @@ __global__ void __launch_bounds__(OS_THREADS, 1) os_jacobi_kernel(OsArgs g) {
 // bounded.  After a whole sweep every column is back at its own position; the rotation count
 // of a sweep is gathered with one cluster barrier.  The iteration ends after a sweep that rotates
 // nothing, or after one whose largest relative coupling |x^H y| / (||x|| ||y||) was at most
-// OS_QUAD: Jacobi converges quadratically, so what remains is of order OS_QUAD^2, about the
+// OS_QUAD: Jacobi converges quadratically, so what remains is of order OS_QUAD^2, below the
 // rotation threshold -- and the FP64 refinement that follows removes any remainder -- so the
 // rotation-free confirming sweep is saved.
-constexpr float OS_QUAD = 1e-3f;
+constexpr float OS_QUAD = 1e-4f;
 __global__ void __launch_bounds__(OS_THREADS, 1) os_dsmem_kernel(OsArgs g, int W) {
   extern __shared__ uint64_t dyn[];   // mbarriers [2 buffers][W workers], then the columns
   uint64_t* bars = dyn;

@@ -7,7 +7,7 @@ constexpr int OA_GROUP_MAX = 32;   // largest group of strongly coupled pairs so
 
 // B = G + shift I (FP32), then one-sided Jacobi on B's columns until no pair is above the
 // threshold (|x^H y| <= tol ||x|| ||y||) or, with the columns in the cluster's shared memory
-// (k up to ~450), until a sweep's largest coupling is of the order sqrt(threshold); at most
+// (k up to ~450), until a sweep's largest coupling is below 1e-4; at most
 // max_sweeps sweeps.  On return B = W, whose columns are multiples of eigenvectors.  nrm:
 // max(k, max_sweeps + 1) floats of scratch; counters: max_sweeps + 1 ints (zeroed here);
 // *sweeps the sweeps run; *err DEV_ERR_NO_CONV if max_sweeps ran out.  *cluster_used: CTAs in
