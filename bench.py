@@ -717,26 +717,40 @@ def run_ours(args):
     stages = np.sum([list(i.ms_stage) for _, i in infos], axis=0).tolist()
 
     # end to end through the public API with host buffers: per problem H2D of H_l (pinned),
-    # solve, D2H of eigenvalues and eigenvectors; S uploaded once per sequence
+    # solve, D2H of eigenvalues and eigenvectors; S uploaded once per sequence.  The upload
+    # of H_{l+1} runs on a second stream while problem l is solved (double-buffered device
+    # copy, as an SCF code would prefetch its next matrix); every copy lies inside the timed
+    # region.
     e2e = None
     if not args.no_e2e:
         Hh = [torch.from_numpy(np.ascontiguousarray(H.T)).pin_memory() for H in Hs]
         Sh = torch.from_numpy(np.ascontiguousarray(S.T)).pin_memory()
-        Hd = torch.empty_like(dev[0])
+        Hd = [torch.empty_like(dev[0]), torch.empty_like(dev[0])]
         Sd2 = torch.empty_like(S_d)
         ev_h = torch.empty(nev, dtype=torch.float64).pin_memory()
         X_h = torch.empty((nev, n), dtype=torch.complex128).pin_memory()
+        up = torch.cuda.Stream()
+        ev_up = [torch.cuda.Event(), torch.cuda.Event()]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         e0.record(stream)
+        up.wait_event(e0)
         for _ in range(args.steps):
+            with torch.cuda.stream(up):
+                Hd[0].copy_(Hh[0], non_blocking=True)
+                ev_up[0].record(up)
             Sd2.copy_(Sh, non_blocking=True)
             for l in range(w.steps):
-                Hd.copy_(Hh[l], non_blocking=True)
+                b = l & 1
+                if l + 1 < w.steps:   # the other buffer's last reader (problem l - 1) has returned
+                    with torch.cuda.stream(up):
+                        Hd[1 - b].copy_(Hh[l + 1], non_blocking=True)
+                        ev_up[1 - b].record(up)
+                stream.wait_event(ev_up[b])
                 if l == 0:
-                    ctx.solve(Hd, Sd2, n, nev, nex, X0_d, w.tol, w.degree, evals, X)
+                    ctx.solve(Hd[b], Sd2, n, nev, nex, X0_d, w.tol, w.degree, evals, X)
                 else:
-                    ctx.next_in_sequence(Hd, None, evals, X)
+                    ctx.next_in_sequence(Hd[b], None, evals, X)
                 ev_h.copy_(evals, non_blocking=True)
                 X_h.copy_(X, non_blocking=True)
         e1.record(stream)
@@ -745,7 +759,9 @@ def run_ours(args):
         h2d = (Hh[0].numel() * 16) * w.steps + Sh.numel() * 16
         d2h = (nev * 8 + nev * n * 16) * w.steps
         e2e = {"value": problems / (ms_e2e / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "wall_s": time.perf_counter() - t0}
+               "d2h_bytes_per_step": d2h, "wall_s": time.perf_counter() - t0,
+               "last_problem_evals_match_device_run": float(np.abs(ev_h.numpy() - lam).max()),
+               "note": "upload of the next H overlapped with the current solve (second stream)"}
 
     # the plain-FP64 arm on the same sequence (every product on the DFMA pipe): one sequence
     # after one warm-up problem, CUDA events on the same stream
