@@ -36,6 +36,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <utility>
 
 #include "ozaki.cuh"
 
@@ -158,6 +159,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Programmatic dependent launch between the stages of one product (slicing -> products ->
+// split-K sum): a kernel's launch and prologue overlap the end of the kernel before it.
+// griddepcontrol.wait returns once the preceding grid has completed and its writes are
+// visible (at once without a programmatic predecessor); launch_dependents is issued only
+// after that wait, so no grid runs ahead of one two launches back.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // 2^x as a double: the exponent field directly in the normal range, ldexp outside it
 __device__ __forceinline__ double pow2(int x) {
   if (x >= -1022 && x <= 1023) return __longlong_as_double((long long)(x + 1023) << 52);
@@ -215,6 +224,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *(volatile uint32_t*)tmem_slot;
+  pdl_wait();   // the digit tiles, exponents and C come from earlier launches
+  pdl_trigger();
 
   if (warp == 0) {
     if (lane == 0) {
@@ -392,6 +403,7 @@ __device__ __forceinline__ void exp_tile(int R, int C, const cplx* X, long ld, i
 }
 // Both operands' exponents in one launch: blockIdx.z picks the job (A's rows, B's columns).
 __global__ void exp_tile_kernel(ExpJob a, ExpJob b) {
+  pdl_trigger();   // launched in order after the sentinel fill: the slicing may be scheduled now
   const ExpJob& j = blockIdx.z == 0 ? a : b;
   if (blockIdx.x >= j.gx || blockIdx.y >= j.gy) return;
   exp_tile(j.R, j.C, j.X, j.ld, j.op, j.rows, j.out, blockIdx.x, blockIdx.y);
@@ -514,6 +526,8 @@ struct SliceArgs {
 // Both operands' digit tiles in one launch: blockIdx.z = 0 slices A, 1 slices B.
 __global__ void slice_kernel(SliceArgs g) {
   __shared__ cplx t[32][33];
+  pdl_wait();
+  pdl_trigger();
   if (blockIdx.z == 0) {
     if (blockIdx.x >= g.gxa || blockIdx.y >= g.gya) return;
     slice_a(g.M, g.K, g.A, g.lda, g.opA, g.rowexp, g.mpad, g.kpad, g.outA, t, blockIdx.x, blockIdx.y);
@@ -525,6 +539,8 @@ __global__ void slice_kernel(SliceArgs g) {
 
 __global__ void oz_reduce_kernel(int M, int N, int splits, const cplx* partial, cplx* C, long ldc, cplx alpha,
                                  cplx beta) {
+  pdl_wait();
+  pdl_trigger();
   const long total = (long)M * N;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
     const long r = e % M, c = e / M;
@@ -537,6 +553,22 @@ __global__ void oz_reduce_kernel(int M, int N, int splits, const cplx* partial, 
 }
 
 long round_up(long x, long m) { return (x + m - 1) / m * m; }
+
+// a launch that may start while the previous kernel on the stream finishes
+template <typename... Params, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 }  // namespace
 
 struct OzakiGemm {
@@ -629,7 +661,7 @@ cudaError_t ozaki_gemm(OzakiGemm* o, const GemmArgs& g, cudaStream_t s, int* err
     sa.gxb = (unsigned)((kpad / 2 + 31) / 32);
     sa.gyb = (unsigned)((npad / 2 + 31) / 32);
     dim3 grid(std::max(sa.gxa, sa.gxb), std::max(sa.gya, sa.gyb), 2);
-    slice_kernel<<<grid, 256, 0, s>>>(sa);
+    if ((e = launch_pdl(slice_kernel, grid, dim3(256), 0, s, sa)) != cudaSuccess) return e;
     count_launch(1);
   }
   const int kblocks = (int)(kpad / BK);
@@ -678,13 +710,13 @@ cudaError_t ozaki_gemm(OzakiGemm* o, const GemmArgs& g, cudaStream_t s, int* err
     a.partial = o->partial;
   }
   dim3 grid((unsigned)(mpad / BM), (unsigned)(npad / BN), (unsigned)splits);
-  ozaki_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(a);
+  if ((e = launch_pdl(ozaki_kernel, grid, dim3(NTHREADS), SMEM_BYTES, s, a)) != cudaSuccess) return e;
   count_launch(1);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (splits > 1) {
     const long total = M * N;
-    oz_reduce_kernel<<<(unsigned)std::min<long>((total + 255) / 256, 4096), 256, 0, s>>>(
-        (int)M, (int)N, splits, o->partial, g.C, g.ldc, g.alpha, g.beta);
+    if ((e = launch_pdl(oz_reduce_kernel, dim3((unsigned)std::min<long>((total + 255) / 256, 4096)), dim3(256), 0, s,
+                        (int)M, (int)N, splits, (const cplx*)o->partial, g.C, g.ldc, g.alpha, g.beta)) != cudaSuccess)
+      return e;
     count_launch(1);
   }
   return cudaGetLastError();
