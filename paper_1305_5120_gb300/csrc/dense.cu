@@ -1,8 +1,6 @@
 // Blocked Cholesky (reduction of S to L L^H, Section 3), triangular inverse (for the
 // two-sided transform H' = L^{-1} H L^{-H} and the back-transform x = L^{-H} y), and the
 // small column kernels around Algorithm 1 (residual norms, locking gathers, random start).
-#include <cooperative_groups.h>
-
 #include "dense.cuh"
 
 namespace {
@@ -607,197 +605,6 @@ size_t chol_inv_work_bytes(int k) {
 cudaError_t chol_inv_small(cudaStream_t s, int k, cplx* A, cplx* X, void* work, int* err) {
   return chol_inv_launch<double>(s, k, A, X, work, err);
 }
-namespace {
-// FP32 Cholesky + inverse of a small matrix (k <= 256) inside ONE thread-block cluster: CTA r
-// owns the 32-wide block column r of L and of X = L^{-1} in its shared memory.  Block step
-// jb: CTA jb factors its diagonal block (32 pivots), inverts it (D_jb = L_jb,jb^{-1}, kept as
-// the diagonal block of X) and forms its panel L_i,jb = A_i,jb D_jb^H; one cluster barrier;
-// every later CTA c stages the rows it needs of that panel from CTA jb's shared memory and
-// updates its own block column, A_i,c -= L_i,jb L_c,jb^H.  Then CTA c forms its block column
-// of X by block forward substitution, X_ib,c = -D_ib sum_{q=c}^{ib-1} L_ib,q X_q,c, reading
-// the finished L blocks and D_ib of the other CTAs.  One cluster barrier per block step and
-// no grid-wide synchronisation (the cooperative kernel needs three grid barriers per block
-// step and a separate inverse phase).
-constexpr int CL_NB = 32, CL_KMAX = 256, CL_THREADS = 256;
-__device__ __forceinline__ void cl_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__global__ void __launch_bounds__(CL_THREADS, 1) chol_inv_cluster_kernel(int k, float2* A, float2* X, int* err) {
-  extern __shared__ float2 csm[];
-  namespace cg = cooperative_groups;
-  cg::cluster_group cl = cg::this_cluster();
-  constexpr int LD = CL_NB + 1;
-  float2* Lc = csm;                      // [k][LD]: rows of my block column of L
-  float2* Xc = csm + (size_t)k * LD;     // [k][LD]: rows of my block column of X
-  float2* St = Xc + (size_t)k * LD;      // [k][LD]: staged rows of another CTA's block column
-  __shared__ float s_inv;
-  __shared__ int s_bad;
-  const int nb = (k + CL_NB - 1) / CL_NB;
-  const int r = (int)cl.block_rank();
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = CL_THREADS / 32;
-  const int c0 = r * CL_NB, w = r < nb ? min(CL_NB, k - c0) : 0;
-  if (tid == 0) s_bad = 0;
-  for (int e = tid; e < k * CL_NB; e += CL_THREADS) {
-    const int i = e % k, q = e / k;
-    Lc[i * LD + q] = (q < w && i >= c0) ? A[i + (long)(c0 + q) * k] : make_float2(0.f, 0.f);
-    Xc[i * LD + q] = make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  for (int jb = 0; jb < nb; ++jb) {
-    if (r == jb) {
-      // diagonal block: 32 pivots
-      for (int p = 0; p < w; ++p) {
-        if (tid == 0) {
-          const float d = Lc[(c0 + p) * LD + p].x;
-          const bool ok = d > 0.f && isfinite(d);
-          const float inv = ok ? rsqrtf(d) : 1.f;
-          if (!ok) s_bad = 1;
-          Lc[(c0 + p) * LD + p] = make_float2(ok ? d * inv : 1.f, 0.f);
-          s_inv = inv;
-        }
-        __syncthreads();
-        for (int i = p + 1 + tid; i < w; i += CL_THREADS) {
-          const float2 v = Lc[(c0 + i) * LD + p];
-          Lc[(c0 + i) * LD + p] = make_float2(v.x * s_inv, v.y * s_inv);
-        }
-        __syncthreads();
-        const int m = w - p - 1;
-        for (int e = tid; e < m * m; e += CL_THREADS) {
-          const int i = p + 1 + e % m, q = p + 1 + e / m;
-          if (q > i) continue;
-          const float2 a = Lc[(c0 + i) * LD + p], b = Lc[(c0 + q) * LD + p], t = Lc[(c0 + i) * LD + q];
-          Lc[(c0 + i) * LD + q] = make_float2(t.x - (a.x * b.x + a.y * b.y), t.y - (a.y * b.x - a.x * b.y));
-        }
-        __syncthreads();
-      }
-      // D = L_jj^{-1} by forward substitution, one thread per column
-      if (tid < w) {
-        const int c = tid;
-        for (int i = c; i < w; ++i) {
-          float sr = (i == c) ? 1.f : 0.f, si = 0.f;
-          for (int q = c; q < i; ++q) {
-            const float2 l = Lc[(c0 + i) * LD + q], x = Xc[(c0 + q) * LD + c];
-            sr -= l.x * x.x - l.y * x.y;
-            si -= l.x * x.y + l.y * x.x;
-          }
-          const float d = Lc[(c0 + i) * LD + i].x;
-          Xc[(c0 + i) * LD + c] = make_float2(sr / d, si / d);
-        }
-      }
-      __syncthreads();
-      // panel: L_i = A_i D^H for rows below the block, one warp per row
-      for (int i = c0 + w + warp; i < k; i += nwarps) {
-        const float2 a = lane < w ? Lc[i * LD + lane] : make_float2(0.f, 0.f);
-        float sr = 0.f, si = 0.f;
-        for (int p = 0; p < w; ++p) {
-          const float ar = __shfl_sync(0xffffffffu, a.x, p), ai = __shfl_sync(0xffffffffu, a.y, p);
-          if (lane < w && p <= lane) {
-            const float2 dv = Xc[(c0 + lane) * LD + p];   // D[lane][p]; a_p conj(D[lane][p])
-            sr += ar * dv.x + ai * dv.y;
-            si += ai * dv.x - ar * dv.y;
-          }
-        }
-        __syncwarp();
-        if (lane < w) Lc[i * LD + lane] = make_float2(sr, si);
-      }
-    }
-    cl_sync();
-    if (r > jb && r < nb) {
-      // stage rows [c0, k) of block column jb from its CTA, then update my block column
-      const float2* Lr = cl.map_shared_rank(Lc, jb);
-      const int wj = min(CL_NB, k - jb * CL_NB);
-      for (int e = tid; e < (k - c0) * CL_NB; e += CL_THREADS) {
-        const int i = c0 + e / CL_NB, q = e % CL_NB;
-        if (q < wj) St[i * LD + q] = Lr[i * LD + q];
-      }
-      __syncthreads();
-      for (int e = tid; e < (k - c0) * w; e += CL_THREADS) {
-        const int i = c0 + e / w, q = e % w;
-        if (c0 + q > i) continue;   // lower triangle of the diagonal block
-        float sr = 0.f, si = 0.f;
-        for (int p = 0; p < wj; ++p) {   // L_i,jb[p] conj(L_(c0+q),jb[p])
-          const float2 a = St[i * LD + p], b = St[(c0 + q) * LD + p];
-          sr += a.x * b.x + a.y * b.y;
-          si += a.y * b.x - a.x * b.y;
-        }
-        const float2 t = Lc[i * LD + q];
-        Lc[i * LD + q] = make_float2(t.x - sr, t.y - si);
-      }
-      __syncthreads();
-    }
-  }
-  // every L block and every D are final: my block column of X
-  if (r < nb) {
-    for (int ib = r + 1; ib < nb; ++ib) {
-      const int i0 = ib * CL_NB, wi = min(CL_NB, k - i0);
-      // T = sum_{q=r}^{ib-1} L_ib,q X_q,r   (rows i0.. of St hold T)
-      for (int e = tid; e < wi * w; e += CL_THREADS) {
-        const int ii = e / w, cc = e % w;
-        float sr = 0.f, si = 0.f;
-        for (int q = r; q < ib; ++q) {
-          const float2* Lq = cl.map_shared_rank(Lc, q);
-          const int wq = min(CL_NB, k - q * CL_NB);
-          for (int p = 0; p < wq; ++p) {
-            const float2 l = Lq[(i0 + ii) * LD + p], x = Xc[(q * CL_NB + p) * LD + cc];
-            sr += l.x * x.x - l.y * x.y;
-            si += l.x * x.y + l.y * x.x;
-          }
-        }
-        St[(i0 + ii) * LD + cc] = make_float2(sr, si);
-      }
-      __syncthreads();
-      // X_ib,r = -D_ib T
-      const float2* Xi = cl.map_shared_rank(Xc, ib);
-      for (int e = tid; e < wi * w; e += CL_THREADS) {
-        const int ii = e / w, cc = e % w;
-        float sr = 0.f, si = 0.f;
-        for (int p = 0; p <= ii; ++p) {
-          const float2 d = Xi[(i0 + ii) * LD + p], t = St[(i0 + p) * LD + cc];
-          sr += d.x * t.x - d.y * t.y;
-          si += d.x * t.y + d.y * t.x;
-        }
-        Xc[(i0 + ii) * LD + cc] = make_float2(-sr, -si);
-      }
-      __syncthreads();
-    }
-    // outputs: L (lower, upper zero) in A, X
-    for (int e = tid; e < k * w; e += CL_THREADS) {
-      const int i = e % k, q = e / k;
-      A[i + (long)(c0 + q) * k] = i >= c0 + q ? Lc[i * LD + q] : make_float2(0.f, 0.f);
-      X[i + (long)(c0 + q) * k] = i >= c0 + q ? Xc[i * LD + q] : make_float2(0.f, 0.f);
-    }
-  }
-  if (tid == 0 && s_bad) atomicExch(err, DEV_ERR_NOT_HPD);
-  cl_sync();   // no CTA leaves while a peer could still read its shared memory
-}
-}  // namespace
-
 cudaError_t chol_inv_small_f32(cudaStream_t s, int k, float2* A, float2* X, void* work, int* err) {
-  // small k with the inverse wanted: one cluster of 8 CTAs, everything in shared memory
-  if (X && k >= 1 && k <= CL_KMAX) {
-    static int attr = 0;
-    const size_t smem = sizeof(float2) * 3 * (size_t)k * (CL_NB + 1);
-    if (!attr) {
-      cudaFuncSetAttribute(chol_inv_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(float2) * 3 * (size_t)CL_KMAX * (CL_NB + 1)));
-      attr = 1;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(8);
-    cfg.blockDim = dim3(CL_THREADS);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 8;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, chol_inv_cluster_kernel, k, A, X, err);
-    count_launch();
-    if (e == cudaSuccess) return cudaSuccess;
-    cudaGetLastError();   // cluster launch refused: the cooperative kernel below
-  }
   return chol_inv_launch<float>(s, k, A, X, work, err);
 }

@@ -37,6 +37,5 @@ constexpr int CHOL_INV_KMAX = 8192;
 size_t chol_inv_work_bytes(int k);
 cudaError_t chol_inv_small(cudaStream_t s, int k, cplx* A, cplx* X, void* work, int* err);
 // The same factorisation in FP32 (complex64 A and X), for well-conditioned Gram matrices whose
-// factor only needs FP32 accuracy; work: chol_inv_work_bytes(k).  With X and k <= 256 it runs
-// in one thread-block cluster with everything in shared memory (the work array unused).
+// factor only needs FP32 accuracy; work: chol_inv_work_bytes(k).
 cudaError_t chol_inv_small_f32(cudaStream_t s, int k, float2* A, float2* X, void* work, int* err);
