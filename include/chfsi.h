@@ -94,9 +94,9 @@ typedef struct {
   double ms_gemm_tc;       /* device time of the FP64-accurate tensor-core GEMMs (all stages) */
   double gemm_tc_flop;     /* their algorithmic work: 8 M N K_eff real flops per complex product */
   double ms_eig;           /* device time of the reduced eigensolver (Rayleigh-Ritz) */
-  int eig_sweeps;          /* Jacobi sweeps that rotated, summed over the call */
-  long long eig_rounds;    /* Jacobi rounds that rotated (each updates the whole k x k matrix and
-                              its eigenvector accumulator), summed over the call */
+  int eig_sweeps;          /* FP64 Jacobi sweeps that rotated (FP64 mode and fallbacks), summed */
+  long long eig_rounds;    /* FP64 Jacobi rounds that rotated (each updates the whole k x k matrix
+                              and its eigenvector accumulator), summed over the call */
   double eig_flop;         /* their algorithmic FP64 work: 28 k^2 real flops per rotating round */
   int n_floor;             /* returned pairs whose residual was tested against the absolute floor
                               (|lambda| < 1e-4 ||H'||: Res = ||H'y - lam y|| / (1e-4 ||H'||)) */
@@ -242,7 +242,12 @@ chfsi_status chfsi_orthonormalize(chfsi_ctx *c, int n, int nl, const void *Ylock
  * Y <- Y W, Z <- H' Y.  Y: n x k orthonormal in, Ritz vectors out; lam[k]; Z: n x k out. */
 chfsi_status chfsi_rayleigh_ritz(chfsi_ctx *c, int n, int k, const void *Hs, void *Y, double *lam, void *Z);
 
-/* a7 alone. All eigenpairs of the k x k Hermitian G (parallel Jacobi): lam ascending, W. */
+/* a7 alone. All eigenpairs of the k x k Hermitian G: lam ascending, W.  Mixed precision with
+ * k >= 32: FP32 one-sided Jacobi in one thread-block cluster, refined to FP64 accuracy by
+ * FP64-accurate tensor-core products, with the parallel FP64 Jacobi as fallback; FP64
+ * precision: the parallel FP64 Jacobi.  Diagnostics: CHFSI_DEBUG_EIG=1 prints every call's
+ * sweeps, iterations and any fallback reason to stderr; CHFSI_OS_CLUSTER=8|16 picks the
+ * cluster size of the FP32 stage. */
 chfsi_status chfsi_reduced_eig(chfsi_ctx *c, int k, const void *G, double *lam, void *W);
 
 /* Allocation-free form of chfsi_reduced_eig, for callers that cannot allocate device memory
