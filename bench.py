@@ -300,7 +300,8 @@ def kernel_rooflines(infos, n, fp64_peak):
 def kernel_case(args):
     """A few launches of one kernel on the benchmark's shapes (n = 2000, block 240), for
     profiling: --kernel-case filter (3 tensor-core filter steps), ozaki (one FP64-accurate
-    GEMM n x 240 x n), zgemm (the same GEMM on the FP64 pipe), sequence (the first
+    GEMM n x 240 x n), zgemm (the same GEMM on the FP64 pipe), eig (the reduced eigenproblem
+    of a Rayleigh-Ritz step, k = 240), sequence (the first
     --case-problems problems of the n = 2000 sequence, mixed path: a launch list of the
     whole solve)."""
     import torch
@@ -334,6 +335,25 @@ def kernel_case(args):
     torch.cuda.synchronize()
     if args.kernel_case == "filter":
         ctx.filter(n, k, Hd, Y, 3, 2.0, 80.0, -1.0, chfsi.CHFSI_PREC_MIXED)
+    elif args.kernel_case == "eig":
+        # the reduced eigenproblem of a Rayleigh-Ritz step: k x k Hermitian with the benchmark's
+        # spectrum shape (200 wanted eigenvalues in [-1, 0], the rest in [0.5, 80]), dense
+        # eigenvectors; solved twice by the mixed-precision path (FP32 sweeps + FP64 refinement)
+        lam = synth.prescribed_spectrum(k, min(k - 1, 200), 80.0, 5)
+        q = synth.haar_unitary(k, synth.rng_for(5, 7))
+        G = chfsi.colmajor(synth.hermitian_part((q * lam[None, :]) @ q.conj().T))
+        ev = torch.empty(k, dtype=torch.float64, device="cuda")
+        W = torch.empty((k, k), dtype=torch.complex128, device="cuda")
+        ctx.close()
+        ctx = chfsi.Context(device=0, precision=chfsi.CHFSI_PREC_MIXED)
+        for _ in range(2):
+            ctx.reduced_eig(k, G, ev, W)
+        torch.cuda.synchronize()
+        err = float(np.abs(ev.cpu().numpy() - lam).max())
+        ctx.close()
+        print(json.dumps({"kernel_case": "eig", "k": k, "max_eigenvalue_error": err,
+                          "launches": chfsi.kernel_launches()}))
+        return 0 if err < 1e-12 * 80 else 1
     else:
         prec = chfsi.CHFSI_PREC_MIXED if args.kernel_case == "ozaki" else chfsi.CHFSI_PREC_FP64
         C = torch.empty_like(Y)
@@ -931,7 +951,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
-    ap.add_argument("--kernel-case", choices=["filter", "ozaki", "zgemm", "sequence"], default=None)
+    ap.add_argument("--kernel-case", choices=["filter", "ozaki", "zgemm", "sequence", "eig"], default=None)
     ap.add_argument("--case-problems", type=int, default=3, help="problems of the sequence kernel case")
     ap.add_argument("--workload", choices=["sequence", "kpoints", "batch", "large", "serve", "seeding"],
                     default="sequence")
