@@ -1023,7 +1023,7 @@ chfsi_status reduced_eig_refined(chfsi_ctx* c, int k, const cplx* G, double* lam
     rmax = sqrt(rmax);
     fcorr = sqrt(fcorr);
     if (herr != DEV_OK || !std::isfinite(offmax) || !std::isfinite(rmax) || offmax > 1e-2 * hfro) {
-      why = "growth";
+      why = herr != DEV_OK ? "device status (a group solve or a product)" : "growth";
       break;
     }
     if (offmax <= 8.0 * eps * hfro && rmax <= 8.0 * eps) {

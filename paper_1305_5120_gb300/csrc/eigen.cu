@@ -394,10 +394,11 @@ __global__ void __launch_bounds__(OS_THREADS, 1) os_dsmem_kernel(OsArgs g, int W
           df[i] = f[i];
           ds[i] = sc[i];
         }
-        // the copies are visible to the receivers before their barriers are signalled
-        asm volatile("fence.acq_rel.cluster;" ::: "memory");
+        // the copies are visible to the receivers before their barriers are signalled: the
+        // warp barrier orders every lane's stores before lane 0's cluster-scope release
         __syncwarp();
         if (lane == 0) {
+          asm volatile("fence.acq_rel.cluster;" ::: "memory");
           mbar_arrive_cluster(bar_of(cur ^ 1, tf));
           mbar_arrive_cluster(bar_of(cur ^ 1, ts));
         }
@@ -559,7 +560,8 @@ __global__ void __launch_bounds__(256) oa_group_kernel(int k, const cplx* S, con
     s_fro = sqrt(f);
   }
   __syncthreads();
-  const double thresh = 2.220446049250313e-16 * s_fro;
+  // rounding of the rotations leaves off-diagonal entries of order c u ||A||_F
+  const double thresh = (double)c * 2.220446049250313e-16 * s_fro;
   bool converged = false;
   for (int sweep = 0; sweep < 30 && !converged; ++sweep) {
     if (threadIdx.x == 0) s_any = 0;
