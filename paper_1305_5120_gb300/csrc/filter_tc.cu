@@ -81,11 +81,6 @@ struct StepArgs {
   const float2* R;               // corrected recurrence: R = H Yhat - Yhat diag(lam) (n x ncols), else NULL
   const float* fcol;             // per column fa_j p_{j-1}(lam_col); NULL for the plain recurrence
   int* err;
-  // stream-K partition (sk = 1): tiles mtiles x ntiles, pieces' partial sums in ws (per CTA:
-  // 3 levels x BN columns x BM rows, FP32), a piece published when flags[cta] == epoch
-  int sk, ntiles, epoch;
-  float* ws;
-  int* flags;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -231,94 +226,39 @@ __device__ __forceinline__ float2 join_slices(const uint32_t w[3]) {
   return make_float2(re, -nim);
 }
 
-// A piece of work of one CTA: K blocks [k0, k1) of the output tile (mtile, ntile).  An owner
-// (k1 = kblocks) finishes the tile: it adds the partial sums of the tile's other pieces (the
-// CTAs listed in contrib, at most two) and runs the recurrence epilogue; a contributor writes
-// its three level accumulators to its slot of the workspace and raises its flag.
-struct Seg {
-  int mtile, ntile, k0, k1;
-  bool owner;
-  int ncontrib, contrib[2];
-};
-
-// Stream-K partition of a step (the single-problem launch when its tiles do not fill the
-// SMs): the tiles x K blocks units are cut into gridDim.x contiguous equal ranges, so every
-// CTA does the same work; a range covers the end of one tile and the start of the next.
-// The contributor piece is processed first and published before any wait, and an owner only
-// waits for lower-numbered CTAs, so the waits cannot form a cycle.
-__device__ __forceinline__ int stream_k_segments(const StepArgs& g, Seg* segs) {
-  const long KB = g.kblocks, T = (long)g.mtiles * g.ntiles, U = T * KB, G = gridDim.x;
-  auto range = [&](long c, long* s0, long* e0) {
-    *s0 = c * U / G;
-    *e0 = (c + 1) * U / G;
-  };
-  long s0, e0;
-  range(blockIdx.x, &s0, &e0);
-  int n = 0;
-  Seg tmp[2];
-  for (long t = s0 / KB; t * KB < e0 && n < 2; ++t) {
-    Seg sg;
-    sg.mtile = (int)(t % g.mtiles);
-    sg.ntile = (int)(t / g.mtiles);
-    sg.k0 = (int)((s0 > t * KB ? s0 : t * KB) - t * KB);
-    sg.k1 = (int)((e0 < (t + 1) * KB ? e0 : (t + 1) * KB) - t * KB);
-    sg.owner = sg.k1 == KB;
-    sg.ncontrib = 0;
-    if (sg.owner && sg.k0 > 0) {
-      // the pieces before this one belong to the CTAs just below
-      for (long c = (long)blockIdx.x - 1; c >= 0 && sg.ncontrib < 2; --c) {
-        long cs, ce;
-        range(c, &cs, &ce);
-        if (ce <= t * KB) break;
-        sg.contrib[sg.ncontrib++] = (int)c;
-        if (cs <= t * KB) break;
-      }
-    }
-    tmp[n++] = sg;
-  }
-  // contributor piece first
-  if (n == 2 && !tmp[1].owner) {
-    segs[0] = tmp[1];
-    segs[1] = tmp[0];
-  } else {
-    for (int i = 0; i < n; ++i) segs[i] = tmp[i];
-  }
-  return n;
-}
-
 template <int BN>
-__device__ __forceinline__ void step_body(const CUtensorMap* tmA, const CUtensorMap* tmB, const StepArgs& g,
-                                          const Seg* segs, int nseg) {
+__device__ __forceinline__ void step_body(const CUtensorMap* tmA, const CUtensorMap* tmB, const StepArgs& g, int mtile,
+                                          int ntile) {
   constexpr int STAGES = Tile<BN>::STAGES;
   constexpr int B_TILE = Tile<BN>::B_TILE;
   constexpr int STAGE_BYTES = Tile<BN>::STAGE_BYTES;
-  constexpr int TMEM_COLS = Tile<BN>::TMEM_COLS;   // one accumulator set; piece i uses set i
+  constexpr int TMEM_COLS = Tile<BN>::TMEM_COLS;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* base_ptr = smem_raw + (base - raw);
-  const uint32_t bars = base + STAGES * STAGE_BYTES;          // full[S], empty[S], accum[2]
+  const uint32_t bars = base + STAGES * STAGE_BYTES;          // full[S], empty[S], accum
   uint64_t* bar_ptr = (uint64_t*)(base_ptr + STAGES * STAGE_BYTES);
-  uint32_t* tmem_slot = (uint32_t*)(bar_ptr + 2 * STAGES + 2);
+  uint32_t* tmem_slot = (uint32_t*)(bar_ptr + 2 * STAGES + 1);
   auto full = [&](int s) { return bars + 8u * s; };
   auto empty = [&](int s) { return bars + 8u * (STAGES + s); };
-  auto accum = [&](int i) { return bars + 8u * (2 * STAGES + i); };
-  const uint32_t tcols = nseg > 1 ? 2 * TMEM_COLS : TMEM_COLS;
+  const uint32_t accum = bars + 8u * (2 * STAGES);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = mtile * BM;
+  const int n0 = ntile * BN;   // real column offset
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full(s), 1);
       mbar_init(empty(s), 1);
     }
-    mbar_init(accum(0), 1);
-    mbar_init(accum(1), 1);
+    mbar_init(accum, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(tcols));
+                 "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -328,218 +268,144 @@ __device__ __forceinline__ void step_body(const CUtensorMap* tmA, const CUtensor
 
   if (warp == 0) {
     if (lane == 0) {
-      // producer: A slice s at rows s*mtiles*BM + m0, B slice t at rows t*npad + n0, piece
-      // after piece through one ring.  The first stages (empty at start) get their A tiles
-      // before the wait for the previous step, their B tiles (that step's output) after it.
-      const int pre = min(STAGES, segs[0].k1 - segs[0].k0);
-      {
-        const int m0 = segs[0].mtile * BM;
-        for (int i = 0; i < pre; ++i) {
-          const int kb = segs[0].k0 + i;
-          const uint32_t st = base + i * STAGE_BYTES;
-          mbar_expect_tx(full(i), STAGE_BYTES);
-          for (int q = 0; q < NSLICE; ++q)
-            tma_load_2d(st + q * A_TILE, tmA, full(i), kb * BK, q * g.mtiles * BM + m0);
-        }
+      // producer: A slice s at rows s*mtiles*BM + m0, B slice t at rows t*npad + n0.  The
+      // first stages (empty at start) get their A tiles before the wait for the previous step,
+      // their B tiles (that step's output) after it.
+      const int pre = g.kblocks < STAGES ? g.kblocks : STAGES;
+      for (int kb = 0; kb < pre; ++kb) {
+        const uint32_t st = base + kb * STAGE_BYTES;
+        mbar_expect_tx(full(kb), STAGE_BYTES);
+        for (int q = 0; q < NSLICE; ++q)
+          tma_load_2d(st + q * A_TILE, tmA, full(kb), kb * BK, q * g.mtiles * BM + m0);
       }
       pdl_wait();
       asm volatile("fence.proxy.async.global;" ::: "memory");
       pdl_trigger();
-      {
-        const int n0 = segs[0].ntile * BN;
-        for (int i = 0; i < pre; ++i)
-          for (int q = 0; q < NSLICE; ++q)
-            tma_load_2d(base + i * STAGE_BYTES + NSLICE * A_TILE + q * B_TILE, tmB, full(i), (segs[0].k0 + i) * BK,
-                        (int)(q * g.npad) + n0);
-      }
-      int it = 0, issued = pre;
-      bool stop = false;
-      for (int sgi = 0; sgi < nseg && !stop; ++sgi) {
-        const int m0 = segs[sgi].mtile * BM, n0 = segs[sgi].ntile * BN;
-        for (int kb = segs[sgi].k0; kb < segs[sgi].k1; ++kb, ++it) {
-          if (it < pre) continue;
-          const int s = it % STAGES;
-          const uint32_t ph = (it / STAGES) & 1;
-          if (!mbar_wait(empty(s), ph ^ 1, g.err)) {
-            stop = true;
-            break;
-          }
-          mbar_expect_tx(full(s), STAGE_BYTES);
-          const uint32_t st = base + s * STAGE_BYTES;
-          for (int q = 0; q < NSLICE; ++q)
-            tma_load_2d(st + q * A_TILE, tmA, full(s), kb * BK, q * g.mtiles * BM + m0);
-          for (int q = 0; q < NSLICE; ++q)
-            tma_load_2d(st + NSLICE * A_TILE + q * B_TILE, tmB, full(s), kb * BK, (int)(q * g.npad) + n0);
-          issued = it + 1;
-        }
+      for (int kb = 0; kb < pre; ++kb)
+        for (int q = 0; q < NSLICE; ++q)
+          tma_load_2d(base + kb * STAGE_BYTES + NSLICE * A_TILE + q * B_TILE, tmB, full(kb), kb * BK,
+                      (int)(q * g.npad) + n0);
+      int issued = pre;
+      for (int kb = pre; kb < g.kblocks; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (!mbar_wait(empty(s), ph ^ 1, g.err)) break;
+        mbar_expect_tx(full(s), STAGE_BYTES);
+        const uint32_t st = base + s * STAGE_BYTES;
+        for (int q = 0; q < NSLICE; ++q)
+          tma_load_2d(st + q * A_TILE, tmA, full(s), kb * BK, q * g.mtiles * BM + m0);
+        for (int q = 0; q < NSLICE; ++q)
+          tma_load_2d(st + NSLICE * A_TILE + q * B_TILE, tmB, full(s), kb * BK, (int)(q * g.npad) + n0);
+        issued = kb + 1;
       }
       // After a failure the consumer may have abandoned stages whose copies are still in
       // flight into this CTA's shared memory: wait until each issued stage has landed (each
       // stage's latest phase is the one checked) before the CTA may exit.
       if (*(volatile int*)g.err != DEV_OK)
-        for (int i = max(0, issued - STAGES); i < issued; ++i) mbar_drain(full(i % STAGES), (i / STAGES) & 1);
+        for (int kb = std::max(0, issued - STAGES); kb < issued; ++kb)
+          mbar_drain(full(kb % STAGES), (kb / STAGES) & 1);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // MMA issuer.  The three B slice tiles of a stage lie one after another (slice t at rows
       // BN t of one K-major operand) and level L = s + t accumulates in TMEM columns [BN L,
-      // BN L + BN) of the piece's set, so the products of A slice s with B slices 0 .. 2 - s
-      // are one MMA of N = BN (3 - s) into columns [BN s, 3 BN) (split at N = 256): three to
-      // four instructions per 16-wide K step for the six slice products.  Each level has its
-      // own accumulator, so the per-instruction truncation of the FP32 accumulation acts on
-      // every level at that level's scale.
-      int it = 0;
-      bool stop = false;
-      for (int sgi = 0; sgi < nseg; ++sgi) {
-        const uint32_t tacc = tmem + (uint32_t)(sgi * TMEM_COLS);
-        for (int kb = segs[sgi].k0; kb < segs[sgi].k1 && !stop; ++kb, ++it) {
-          const int s = it % STAGES;
-          const uint32_t ph = (it / STAGES) & 1;
-          if (!mbar_wait(full(s), ph, g.err)) {
-            stop = true;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t st = base + s * STAGE_BYTES;
-          // base descriptors once per stage; slices and K steps are start-address offsets
-          const uint64_t da0 = umma_desc(st), db0 = umma_desc(st + NSLICE * A_TILE);
-          const uint32_t later = kb != segs[sgi].k0;
+      // BN L + BN), so the products of A slice s with B slices 0 .. 2 - s are one MMA of
+      // N = BN (3 - s) into columns [BN s, 3 BN) (split at N = 256): three to four instructions
+      // per 16-wide K step for the six slice products.  Each level has its own accumulator, so
+      // the per-instruction truncation of the FP32 accumulation acts on every level at that
+      // level's scale.
+      for (int kb = 0; kb < g.kblocks; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (!mbar_wait(full(s), ph, g.err)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st = base + s * STAGE_BYTES;
+        // base descriptors once per stage; slices and K steps are start-address offsets
+        const uint64_t da0 = umma_desc(st), db0 = umma_desc(st + NSLICE * A_TILE);
+        const uint32_t later = kb != 0;
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
+        for (int kk = 0; kk < BK / 16; ++kk) {
 #pragma unroll
-            for (int sa = 0; sa < NSLICE; ++sa) {
-              const uint64_t da = da0 + (uint64_t)((sa * A_TILE + kk * 32) >> 4);
-              const uint32_t acc = (kk != 0 || sa != 0) ? 1u : later;
-              constexpr int NMAX = 256;
+          for (int sa = 0; sa < NSLICE; ++sa) {
+            const uint64_t da = da0 + (uint64_t)((sa * A_TILE + kk * 32) >> 4);
+            const uint32_t acc = (kk != 0 || sa != 0) ? 1u : later;
+            constexpr int NMAX = 256;
 #pragma unroll
-              for (int off = 0; off < BN * (NSLICE - sa); off += NMAX) {
-                const int nn = BN * (NSLICE - sa) - off < NMAX ? BN * (NSLICE - sa) - off : NMAX;
-                // B rows [off, off + nn) of the stage: 128 bytes per K-major row
-                const uint64_t db = db0 + (uint64_t)((off * 128 + kk * 32) >> 4);
-                umma_bf16(tacc + (uint32_t)(sa * BN + off), da, db, idesc(nn), acc);
-              }
+            for (int off = 0; off < BN * (NSLICE - sa); off += NMAX) {
+              const int nn = BN * (NSLICE - sa) - off < NMAX ? BN * (NSLICE - sa) - off : NMAX;
+              // B rows [off, off + nn) of the stage: 128 bytes per K-major row
+              const uint64_t db = db0 + (uint64_t)((off * 128 + kk * 32) >> 4);
+              umma_bf16(tmem + (uint32_t)(sa * BN + off), da, db, idesc(nn), acc);
             }
           }
-          umma_commit(empty(s));   // frees the stage once these MMAs have read it
         }
-        umma_commit(accum(sgi));   // arrives when every product issued above has completed
+        umma_commit(empty(s));   // frees the stage once these MMAs have read it
       }
+      umma_commit(accum);        // arrives when every product issued above has completed
     }
   } else {
     // epilogue: warps 2..5 -> TMEM lane quarter (warp % 4).  It reads the previous steps'
     // output and overwrites the buffer the previous step read: after that step has completed.
     pdl_wait();
     const int q = warp & 3;
-    const int rt = q * 32 + lane;   // row within the tile
-    for (int sgi = 0; sgi < nseg; ++sgi) {
-      const Seg& sg = segs[sgi];
-      const int m0 = sg.mtile * BM, n0 = sg.ntile * BN;
-      const int row = m0 + rt;
-      bool ok = mbar_wait(accum(sgi), 0, g.err);
-      ok = __all_sync(0xffffffffu, ok && *(volatile int*)g.err == DEV_OK);   // warp-uniform
-      __syncwarp();
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t taddr = tmem + (uint32_t)(sgi * TMEM_COLS) + ((uint32_t)(q * 32) << 16);
-      if (!sg.owner) {
-        // contributor: the three level accumulators to this CTA's workspace slot, then the flag
-        float* ws = g.ws + (long)blockIdx.x * 3 * BN * BM;
-        if (ok) {
+    const int row = m0 + q * 32 + lane;
+    bool ok = mbar_wait(accum, 0, g.err);
+    ok = __all_sync(0xffffffffu, ok && *(volatile int*)g.err == DEV_OK);   // warp-uniform
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16);
+      const uint32_t* Bc32 = (const uint32_t*)g.Bcur;
+      uint32_t* Bn32 = (uint32_t*)g.Bnext;
+      const long kw = g.kpad / 2;                 // 32-bit words per B row
+      const long slice_words = g.npad * kw;
+      const bool use_prev = g.fg != 0.0f;
 #pragma unroll 1
-          for (int c0 = 0; c0 < BN; c0 += 16) {
-            float l[3][16];
-            tmem_ld16(taddr + c0, l[0]);
-            tmem_ld16(taddr + BN + c0, l[1]);
-            tmem_ld16(taddr + 2 * BN + c0, l[2]);
+      for (int c0 = 0; c0 < BN; c0 += 16) {   // 16 real columns (8 complex) per pass
+        float l0[16], l1[16], l2[16];
+        tmem_ld16(taddr + c0, l0);
+        tmem_ld16(taddr + BN + c0, l1);
+        tmem_ld16(taddr + 2 * BN + c0, l2);
+        const int jb = (n0 + c0) / 2;
+        if (row < g.n) {
+          // every load of the 8 columns first, then the arithmetic and the stores
+          uint32_t wc[8][3], wp[8][3];
+          float2 rr[8];
 #pragma unroll
-            for (int L = 0; L < 3; ++L)
+          for (int jj = 0; jj < 8; ++jj) {
+            const int j = jb + jj;
+            const long w2j = 2L * j * kw + row;
 #pragma unroll
-              for (int i = 0; i < 16; ++i) ws[((long)L * BN + c0 + i) * BM + rt] = l[L][i];
-          }
-        }
-        __threadfence();
-        asm volatile("bar.sync 1, 128;" ::: "memory");   // the four epilogue warps
-        if (warp == 2 && lane == 0) atomicExch(g.flags + blockIdx.x, g.epoch);
-        continue;
-      }
-      // owner: wait (bounded) for the tile's other pieces
-      if (sg.ncontrib > 0) {
-        if (warp == 2 && lane == 0) {
-          for (int ci = 0; ci < sg.ncontrib; ++ci) {
-            long spin = 0;
-            while (*(volatile int*)(g.flags + sg.contrib[ci]) != g.epoch) {
-              if (++spin >= WAIT_LIMIT || *(volatile int*)g.err != DEV_OK) {
-                atomicExch(g.err, DEV_ERR_TIMEOUT);
-                break;
-              }
+            for (int t = 0; t < NSLICE; ++t) {
+              wc[jj][t] = j < g.ncols ? Bc32[t * slice_words + w2j] : 0u;
+              wp[jj][t] = (use_prev && j < g.ncols) ? Bn32[t * slice_words + w2j] : 0u;
             }
+            rr[jj] = (g.R && j < g.ncols) ? g.R[(long)j * g.n + row] : make_float2(0.f, 0.f);
           }
-          __threadfence();
-        }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        ok = __all_sync(0xffffffffu, ok && *(volatile int*)g.err == DEV_OK);
-      }
-      if (ok) {
-        const uint32_t* Bc32 = (const uint32_t*)g.Bcur;
-        uint32_t* Bn32 = (uint32_t*)g.Bnext;
-        const long kw = g.kpad / 2;                 // 32-bit words per B row
-        const long slice_words = g.npad * kw;
-        const bool use_prev = g.fg != 0.0f;
-#pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 16) {   // 16 real columns (8 complex) per pass
-          float l0[16], l1[16], l2[16];
-          tmem_ld16(taddr + c0, l0);
-          tmem_ld16(taddr + BN + c0, l1);
-          tmem_ld16(taddr + 2 * BN + c0, l2);
-          for (int ci = 0; ci < sg.ncontrib; ++ci) {   // the other pieces' partial sums
-            const float* ws = g.ws + (long)sg.contrib[ci] * 3 * BN * BM;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              l0[i] += __ldcg(ws + ((long)0 * BN + c0 + i) * BM + rt);
-              l1[i] += __ldcg(ws + ((long)1 * BN + c0 + i) * BM + rt);
-              l2[i] += __ldcg(ws + ((long)2 * BN + c0 + i) * BM + rt);
+          for (int jj = 0; jj < 8; ++jj) {
+            const int j = jb + jj;
+            if (j >= g.ncols) continue;
+            const float hr = l0[2 * jj] + (l1[2 * jj] + l2[2 * jj]);
+            const float hi = l0[2 * jj + 1] + (l1[2 * jj + 1] + l2[2 * jj + 1]);
+            const float2 y = join_slices(wc[jj]);
+            float ore = fmaf(g.fa, hr, g.fb * y.x);
+            float oim = fmaf(g.fa, hi, g.fb * y.y);
+            if (use_prev) {
+              const float2 p = join_slices(wp[jj]);
+              ore = fmaf(g.fg, p.x, ore);
+              oim = fmaf(g.fg, p.y, oim);
             }
-          }
-          const int jb = (n0 + c0) / 2;
-          if (row < g.n) {
-            // every load of the 8 columns first, then the arithmetic and the stores
-            uint32_t wc[8][3], wp[8][3];
-            float2 rr[8];
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-              const int j = jb + jj;
+            if (g.fcol) {   // residual forcing of the corrected recurrence: + fa p_{j-1}(lam_j) R_j
+              const float f = g.fcol[j];
+              ore = fmaf(f, rr[jj].x, ore);
+              oim = fmaf(f, rr[jj].y, oim);
+            }
+            if (j < g.ncols_next) {
               const long w2j = 2L * j * kw + row;
-#pragma unroll
-              for (int t = 0; t < NSLICE; ++t) {
-                wc[jj][t] = j < g.ncols ? Bc32[t * slice_words + w2j] : 0u;
-                wp[jj][t] = (use_prev && j < g.ncols) ? Bn32[t * slice_words + w2j] : 0u;
-              }
-              rr[jj] = (g.R && j < g.ncols) ? g.R[(long)j * g.n + row] : make_float2(0.f, 0.f);
-            }
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-              const int j = jb + jj;
-              if (j >= g.ncols) continue;
-              const float hr = l0[2 * jj] + (l1[2 * jj] + l2[2 * jj]);
-              const float hi = l0[2 * jj + 1] + (l1[2 * jj + 1] + l2[2 * jj + 1]);
-              const float2 y = join_slices(wc[jj]);
-              float ore = fmaf(g.fa, hr, g.fb * y.x);
-              float oim = fmaf(g.fa, hi, g.fb * y.y);
-              if (use_prev) {
-                const float2 p = join_slices(wp[jj]);
-                ore = fmaf(g.fg, p.x, ore);
-                oim = fmaf(g.fg, p.y, oim);
-              }
-              if (g.fcol) {   // residual forcing of the corrected recurrence: + fa p_{j-1}(lam_j) R_j
-                const float f = g.fcol[j];
-                ore = fmaf(f, rr[jj].x, ore);
-                oim = fmaf(f, rr[jj].y, oim);
-              }
-              if (j < g.ncols_next) {
-                const long w2j = 2L * j * kw + row;
-                store_slices(Bn32, slice_words, w2j, w2j + kw, ore, oim);
-              } else {
-                g.Yfinal[(long)j * g.n + row] = cmk(to_f64(ore), to_f64(oim));
-              }
+              store_slices(Bn32, slice_words, w2j, w2j + kw, ore, oim);
+            } else {
+              g.Yfinal[(long)j * g.n + row] = cmk(to_f64(ore), to_f64(oim));
             }
           }
         }
@@ -549,13 +415,12 @@ __device__ __forceinline__ void step_body(const CUtensorMap* tmA, const CUtensor
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
-    // after a failure the products may still be running: each piece's accumulator barrier
-    // arrives when they have completed (bounded), and only then is the TMEM returned
-    if (*(volatile int*)g.err != DEV_OK && lane == 0)
-      for (int i = 0; i < nseg; ++i) mbar_drain(accum(i), 0);
+    // after a failure the products may still be running: the accumulator barrier arrives when
+    // they have completed (bounded), and only then is the TMEM returned
+    if (*(volatile int*)g.err != DEV_OK && lane == 0) mbar_drain(accum, 0);
     __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
   }
 }
 
@@ -564,20 +429,7 @@ template <int BN>
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_filter_step_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                           StepArgs g) {
-  Seg segs[2];
-  int nseg = 1;
-  if (g.sk) {
-    nseg = stream_k_segments(g, segs);
-    if (nseg == 0) return;   // uniform over the CTA, before any barrier or TMEM allocation
-  } else {
-    segs[0].mtile = blockIdx.x;
-    segs[0].ntile = blockIdx.y;
-    segs[0].k0 = 0;
-    segs[0].k1 = g.kblocks;
-    segs[0].owner = true;
-    segs[0].ncontrib = 0;
-  }
-  step_body<BN>(&tmA, &tmB, g, segs, nseg);
+  step_body<BN>(&tmA, &tmB, g, blockIdx.x, blockIdx.y);
 }
 
 // Many problems in one launch (one recurrence step of every problem of a batch): a device
@@ -601,14 +453,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_filter_group_kernel(const Grou
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&d[gi].mapB) : "memory");
   }
   __syncthreads();
-  Seg sg;
-  sg.mtile = t % d[gi].mtiles;
-  sg.ntile = t / d[gi].mtiles;
-  sg.k0 = 0;
-  sg.k1 = g.kblocks;
-  sg.owner = true;
-  sg.ncontrib = 0;
-  step_body<BN>(&d[gi].mapA, &d[gi].mapB, g, &sg, 1);
+  step_body<BN>(&d[gi].mapA, &d[gi].mapB, g, t % d[gi].mtiles, t / d[gi].mtiles);
 }
 
 // A recurrence step launch that may start while the previous step finishes (programmatic
@@ -758,18 +603,13 @@ struct TcFilter {
   };
   std::vector<Trial> trials;
   std::vector<cudaEvent_t> ev_pool;
-  // stream-K workspace (one slot of partial sums per CTA) and publication flags
-  float* sk_ws = nullptr;
-  int* sk_flags = nullptr;
-  int sk_epoch = 0, sms = 0;
 };
 
 namespace {
 // ---- autotuner of the tile width --------------------------------------------------------
 // The two widths compute every output element in the same order (the same K loop, one
 // element per accumulator column), so they give bit-identical results and the choice can
-// follow measured time alone.  (Shapes that take the stream-K partition are not tuned: they
-// always run at width 64, so their results do not depend on a timing either.)  Per launch shape (row tiles, columns) each width is timed on
+// follow measured time alone.  Per launch shape (row tiles, columns) each width is timed on
 // its first use (CUDA events on the launching stream, read at the next synchronisation) and
 // the faster one is kept for the rest of the process.
 constexpr int NVAR = 2;
@@ -868,8 +708,6 @@ void tc_filter_free(TcFilter* f) {
   cudaFree(f->pm);
   cudaFree(f->deg);
   cudaFree(f->err);
-  cudaFree(f->sk_ws);
-  cudaFree(f->sk_flags);
   for (int i = 0; i < 2; ++i)
     if (f->ev[i]) cudaEventDestroy(f->ev[i]);
   for (auto& t : f->trials) {
@@ -992,34 +830,6 @@ static StepArgs step_args(TcFilter* f, int n, cplx* Y, const int* cnt, int mmax,
   return g;
 }
 
-// Stream-K for a single-problem step of width 64 whose tiles leave SMs idle: every SM gets an
-// equal share of the tiles x K blocks, each share at least half a tile (so a tile has at most
-// three pieces and a CTA at most two).  The partition depends only on the shape and the SM
-// count, so the results are reproducible; they differ from the one-piece-per-tile launch in
-// the FP32 rounding of the summation order only.
-static bool stream_k_eligible(TcFilter* f, int mtiles, int ntiles, int kblocks) {
-  if (getenv("CHFSI_FILTER_WIDTH") && atoi(getenv("CHFSI_FILTER_WIDTH")) == 32) return false;
-  if (f->sms == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&f->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-      cudaGetLastError();
-      f->sms = -1;
-    }
-  }
-  if (f->sms <= 0) return false;
-  const long T = (long)mtiles * ntiles, U = T * kblocks;
-  return T < f->sms && U / f->sms >= (kblocks + 1) / 2;
-}
-static chfsi_status stream_k_workspace(TcFilter* f, cudaStream_t s) {
-  if (f->sk_ws) return CHFSI_OK;
-  CHFSI_CUDA_TRY(cudaMalloc(&f->sk_ws, sizeof(float) * (size_t)f->sms * 3 * 64 * BM));
-  CHFSI_CUDA_TRY(cudaMalloc(&f->sk_flags, sizeof(int) * (size_t)f->sms));
-  CHFSI_CUDA_TRY(cudaMemsetAsync(f->sk_flags, 0, sizeof(int) * (size_t)f->sms, s));
-  f->sk_epoch = 0;
-  return CHFSI_OK;
-}
-
 static chfsi_status tc_epilogue_launch(TcFilter* f, cudaStream_t s, int n, cplx* Y, int k, const TcRefine* ref) {
   if (ref) {
     const unsigned cgrid = (unsigned)std::min<long>((n + 255) / 256, 16);
@@ -1042,13 +852,11 @@ chfsi_status tc_filter_run(TcFilter* f, cudaStream_t s, int n, const cplx* H, cp
   }
   CHFSI_CUDA_TRY(cudaEventRecord(f->ev[0], s));
   for (int j = ref ? 2 : 1; j <= mmax; ++j) {
-    StepArgs g = step_args(f, n, Y, cnt, mmax, j, fa, fb, fg, ref);
+    const StepArgs g = step_args(f, n, Y, cnt, mmax, j, fa, fb, fg, ref);
     f->col_steps += cnt[j];
     const long long key = ((long long)g.mtiles << 32) | (long long)(2 * cnt[j]);
     bool trial = false;
-    const int nt64 = (int)((2L * cnt[j] + 63) / 64);
-    const bool sk = stream_k_eligible(f, g.mtiles, nt64, g.kblocks);
-    const int v = sk ? 1 : tune_pick(key, &trial);
+    const int v = tune_pick(key, &trial);
     cudaEvent_t ta = nullptr, tb = nullptr;
     if (trial) {
       ta = pool_ev(f);
@@ -1057,15 +865,6 @@ chfsi_status tc_filter_run(TcFilter* f, cudaStream_t s, int n, const cplx* H, cp
     }
     const int BNv = VAR_BN[v];
     dim3 grid((unsigned)g.mtiles, (unsigned)((2L * cnt[j] + BNv - 1) / BNv));
-    if (sk) {
-      TRY_CHFSI(stream_k_workspace(f, s));
-      g.sk = 1;
-      g.ntiles = nt64;
-      g.ws = f->sk_ws;
-      g.flags = f->sk_flags;
-      g.epoch = ++f->sk_epoch;
-      grid = dim3((unsigned)f->sms);
-    }
     if (v == 0)
       CHFSI_CUDA_TRY(launch_pdl(tc_filter_step_kernel<32>, grid, Tile<32>::SMEM_BYTES, s, f->mapA,
                                 f->mapB[0][(j - 1) & 1], g));
