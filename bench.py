@@ -537,7 +537,8 @@ def run_large(args):
         ev = evals.cpu().numpy()
         if l == 0:
             err = np.abs(ev - lam[:w.nev].cpu().numpy())
-            np.savetxt(os.path.join(ROOT, "gpurun_out", "large_step0_eig_errors.txt"), err)
+            if args.large_errors_file:   # every eigenvalue's error, one per line
+                np.savetxt(args.large_errors_file, err)
             row["eig_error_vs_prescribed"] = {"max": float(err.max()), "median": float(np.median(err)),
                                               "p99": float(np.percentile(err, 99)),
                                               "worst_index": int(err.argmax())}
@@ -956,6 +957,8 @@ def main():
     ap.add_argument("--workload", choices=["sequence", "kpoints", "batch", "large", "serve", "seeding"],
                     default="sequence")
     ap.add_argument("--large-steps", type=int, default=8)
+    ap.add_argument("--large-errors-file", default=None,
+                    help="write step 0's error of every eigenvalue against the prescribed spectrum here")
     ap.add_argument("--serve-sequences", type=int, default=48)
     ap.add_argument("--serve-steps", type=int, default=15)
     ap.add_argument("--serve-nmax", type=int, default=8000)
